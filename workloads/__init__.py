@@ -1,0 +1,172 @@
+"""Seeded synthetic inputs shared by the oracle-side tests, the GPU tests and the bench.
+
+This module holds no arithmetic of the lattice Boltzmann method itself: it builds
+initial order-parameter fields (the tanh profiles of the paper's Sec. 4 set-ups),
+region labels for the droplet volumes of Fig. 3b, seeded noise and random
+population states, and the parameter dictionaries of the benchmark workloads.
+Both the CPU oracle and the CUDA library receive exactly these arrays.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, OOPSLA 2014), a
+counter-based generator, so a field is a pure function of (seed, index).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+_M64 = np.uint64(0xFFFFFFFFFFFFFFFF)
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """n consecutive SplitMix64 outputs for the stream starting at ``seed``."""
+    with np.errstate(over="ignore"):
+        k = np.arange(1, n + 1, dtype=np.uint64)
+        z = (np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + k * np.uint64(0x9E3779B97F4A7C15)) & _M64
+        z = ((z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)) & _M64
+        z = ((z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)) & _M64
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(seed: int, shape, lo=0.0, hi=1.0) -> np.ndarray:
+    """Uniform doubles in [lo, hi) from the top 53 bits of SplitMix64."""
+    n = int(np.prod(shape)) if len(shape) else 1
+    u = (splitmix64(seed, n) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return (lo + (hi - lo) * u).reshape(shape)
+
+
+# ---------------------------------------------------------------------------
+# Initial fields (Sec. 4 set-ups)
+# ---------------------------------------------------------------------------
+
+def tanh_disc(nx, ny, cx, cy, R, W, periodic=False):
+    """0.5[1 + tanh(2(R - d)/W)] on node coordinates (i, j); d Euclidean.
+
+    With periodic=True the distance is taken to the nearest periodic image."""
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    dx = x - cx
+    dy = y - cy
+    if periodic:
+        dx = dx - nx * np.round(dx / nx)
+        dy = dy - ny * np.round(dy / ny)
+    d = np.sqrt(dx * dx + dy * dy)
+    return 0.5 * (1.0 + np.tanh(2.0 * (R - d) / W))
+
+
+def droplets_field(nx, ny, drops, W, periodic=False):
+    """Sum of tanh discs, as in the two-droplet set-up of Sec. 4.1."""
+    phi = np.zeros((ny, nx))
+    for (cx, cy, R) in drops:
+        phi += tanh_disc(nx, ny, cx, cy, R, W, periodic)
+    return phi
+
+
+def nearest_surface_labels(nx, ny, drops, periodic=True):
+    """Region of each node: the droplet whose surface is nearest (|x-c|-R minimal)."""
+    x = np.arange(nx, dtype=np.float64)[None, :]
+    y = np.arange(ny, dtype=np.float64)[:, None]
+    best = np.full((ny, nx), np.inf)
+    lab = np.zeros((ny, nx), dtype=np.int8)
+    for k, (cx, cy, R) in enumerate(drops):
+        dx = x - cx
+        dy = y - cy
+        if periodic:
+            dx = dx - nx * np.round(dx / nx)
+            dy = dy - ny * np.round(dy / ny)
+        s = np.sqrt(dx * dx + dy * dy) - R
+        sel = s < best
+        best = np.where(sel, s, best)
+        lab = np.where(sel, np.int8(k), lab)
+    return lab
+
+
+def flat_slab(nx, ny, x1, x2, W):
+    """A periodic slab phi(x) = 1 between x1 < x < x2 with two tanh interfaces."""
+    x = np.arange(nx, dtype=np.float64)
+    phi = 0.5 * (np.tanh(2.0 * (x - x1) / W) - np.tanh(2.0 * (x - x2) / W))
+    return np.broadcast_to(phi[None, :], (ny, nx)).copy()
+
+
+# ---------------------------------------------------------------------------
+# Parameter sets
+# ---------------------------------------------------------------------------
+
+def base_case(nx, ny, **kw):
+    c = dict(nx=int(nx), ny=int(ny), flow="coupled", W=4.0, sigma=1e-3,
+             **{"lambda": 0.5}, xi=1e-10, tau_g=0.8, rho_l=1.0, rho_g=1.0,
+             tau_f_l=1.0, tau_f_g=1.0, s_f=[1.0] * 9, s_g=[1.0] * 9,
+             vortex_U=0.0, vortex_T=1.0)
+    c.update(kw)
+    return c
+
+
+def two_droplets(noise=0.0, seed=12345, lam=0.5):
+    """Two stationary droplets in gas: 128x64 periodic, R=12 at (40,32) and
+    R=6 at (96,32), W=4, ratios 1:1, tau_g=0.8, tau_f=1.0, sigma=1e-3, at rest.
+    ``noise`` adds a seeded uniform perturbation in [-noise, noise) to phi0."""
+    nx, ny = 128, 64
+    drops = [(40.0, 32.0, 12.0), (96.0, 32.0, 6.0)]
+    case = base_case(nx, ny, **{"lambda": lam})
+    phi0 = droplets_field(nx, ny, drops, case["W"])
+    if noise:
+        phi0 = phi0 + uniform(seed, (ny, nx), -noise, noise)
+    labels = nearest_surface_labels(nx, ny, drops)
+    return case, phi0, None, labels, drops
+
+
+def single_vortex(n=256, W=3.0, U=0.02, T=16384, lam=0.5, sigma=0.01, tau_g=0.8):
+    """Time-reversed single vortex, phase field only: n x n, disc of radius 0.15n
+    at (0.5n, 0.75n), prescribed velocity with amplitude U and period T steps."""
+    case = base_case(n, n, flow="vortex", W=W, sigma=sigma, tau_g=tau_g,
+                     vortex_U=U, vortex_T=float(T), **{"lambda": lam})
+    phi0 = tanh_disc(n, n, 0.5 * n, 0.75 * n, 0.15 * n, W)
+    return case, phi0, None
+
+
+def random_state(nx, ny, seed, coupled=True, phi_lo=-0.05, phi_hi=1.05):
+    """A random but well-conditioned post-streaming state for parity tests:
+    g_i = w_i * phi_i-ish positive pieces plus noise, f_i small, phi*u small."""
+    w = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    phi = uniform(seed, (ny, nx), phi_lo, phi_hi)
+    g = w[:, None, None] * phi[None] + uniform(seed + 1, (9, ny, nx), -2e-3, 2e-3)
+    f = uniform(seed + 2, (9, ny, nx), -2e-3, 2e-3) if coupled else None
+    j = uniform(seed + 3, (2, ny, nx), -1e-3, 1e-3)
+    return f, g, j
+
+
+EDGES = (64, 96, 128, 192, 256, 384, 512)
+
+
+def batched_droplets(ncases=512, seed=2026, W=4.0, sigma=1e-3, tau_g=0.8,
+                     tau_f=1.0, lam=0.5):
+    """Independent 2-D droplet cases: square edge uniform in EDGES, radius
+    uniform in [0.05, 0.3]*edge, centred, translation speed uniform in
+    [0, 0.02] in a uniform random direction, density ratio log-uniform in
+    [1, 10] (rho_g = 1), equal kinematic viscosity (tau_f) in both phases."""
+    r = uniform(seed, (ncases, 5))
+    cases = []
+    for c in range(ncases):
+        edge = EDGES[min(int(r[c, 0] * len(EDGES)), len(EDGES) - 1)]
+        R = (0.05 + 0.25 * r[c, 1]) * edge
+        speed = 0.02 * r[c, 2]
+        ang = 2.0 * math.pi * r[c, 3]
+        ratio = math.exp(math.log(10.0) * r[c, 4])
+        case = base_case(edge, edge, W=W, sigma=sigma, tau_g=tau_g,
+                         rho_l=ratio, rho_g=1.0, tau_f_l=tau_f, tau_f_g=tau_f,
+                         **{"lambda": lam})
+        case["R"] = R
+        case["u0"] = (speed * math.cos(ang), speed * math.sin(ang))
+        cases.append(case)
+    return cases
+
+
+def case_fields(case):
+    """phi0 and u0 (2, ny, nx) of a batched droplet case."""
+    nx, ny = case["nx"], case["ny"]
+    phi0 = tanh_disc(nx, ny, 0.5 * nx, 0.5 * ny, case["R"], case["W"], periodic=True)
+    u0 = np.empty((2, ny, nx))
+    u0[0] = case["u0"][0]
+    u0[1] = case["u0"][1]
+    return phi0, u0
