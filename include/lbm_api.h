@@ -1,0 +1,187 @@
+/*
+ * lbm_api.h -- C ABI of the GB300 library for the coupled, locally
+ * volume-conserving lattice Boltzmann step of Xiong, Wang & Liu,
+ * "Local volume-conserving lattice Boltzmann model for incompressible
+ * multiphase flows" (arXiv 2505.10899).
+ *
+ * One time step couples
+ *   - the interface-capturing MRT-LB for the modified Cahn-Hilliard equation
+ *     (Sec. 3.2, Eqs. 30-37; target PDE Eq. 17), whose source carries the
+ *     level-set sharpening flux (lambda/W)[1 - tanh^2(2 psi/W)] grad(psi)/|grad(psi)|
+ *     (Eq. 32), and
+ *   - the hydrodynamic MRT-LB for incompressible two-phase flow
+ *     (Sec. 3.1, Eqs. 20-29; target PDE Eq. 18) driven by F_s = hbar grad(phi),
+ * with the isotropic gradient/Laplacian stencils of Sec. 3.2 for grad(phi),
+ * lap(phi) and grad(psi), on the D2Q9 lattice of Eq. 19.  Lattice units:
+ * dt = dx = 1, c_s^2 = 1/3.  The grid is periodic in x and y.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: LBM_OK (0) or a negative LBM_ERR_* code.  No C++
+ *     exception crosses the ABI.  lbm_last_error() gives a message for the
+ *     last failing call of the calling thread.
+ *   - Device memory: the library never allocates device memory.  The caller
+ *     passes one device buffer (the workspace) of lbm_workspace_bytes()
+ *     bytes, 256-byte aligned, which must outlive the handle.  All
+ *     simulation state lives there.
+ *   - Host memory: every host array is owned by the caller; the library
+ *     copies in or out during the call and keeps no host pointer.  Host
+ *     fields are always FP64, whatever the device precision.  Layout of a
+ *     2-D field: [y][x], x fastest; of populations: [i][y][x] with i the
+ *     D2Q9 index of Eq. 19; of phi*u: [component][y][x].
+ *   - Streams: every call enqueues its work on the CUDA stream given to
+ *     lbm_init (NULL = legacy default stream).  Calls that return host data
+ *     (lbm_volume, lbm_fields, lbm_get_state, lbm_save, lbm_status)
+ *     synchronise that stream; lbm_step does not.
+ *   - Batches: one handle advances ncases >= 1 independent grids of
+ *     possibly different sizes in the same kernel launches.  Fields that
+ *     define the launch (precision, flow, W, sigma, lambda, xi, tau_g, the
+ *     free MRT rates, vortex_U, vortex_T) must be equal across the batch;
+ *     nx, ny, rho_l, rho_g, tau_f_l, tau_f_g may differ per case.
+ *   - Thread safety: a handle may be used by one host thread at a time.
+ */
+#ifndef LBM_API_H
+#define LBM_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+typedef struct lbm_handle lbm_handle; /* opaque; freed by lbm_destroy */
+
+enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,           /* invalid argument or parameter set */
+  LBM_ERR_CUDA = -2,          /* a CUDA runtime call failed */
+  LBM_ERR_WORKSPACE = -3,     /* workspace missing, too small or misaligned */
+  LBM_ERR_NONFINITE = -4,     /* a NaN/Inf appeared in the macroscopic fields */
+  LBM_ERR_TIMEOUT = -5,       /* reserved: a bounded device wait gave up */
+  LBM_ERR_UNIMPLEMENTED = -6  /* entry point declared but not built */
+};
+
+enum { LBM_F64 = 0, LBM_F32 = 1 };                 /* storage and arithmetic */
+enum { LBM_FLOW_COUPLED = 0, LBM_FLOW_VORTEX = 1 }; /* see lbm_params.flow */
+
+/* Parameters of one case (one periodic grid). */
+typedef struct {
+  int32_t abi_version; /* must be LBM_ABI_VERSION */
+  int32_t nx, ny;      /* nodes in x and y, each >= 1 */
+  int32_t precision;   /* LBM_F64 or LBM_F32 */
+  /* LBM_FLOW_COUPLED: both LB equations, u from Eq. 28.
+   * LBM_FLOW_VORTEX: the phase-field LB alone under the prescribed
+   * time-reversed single vortex of Eqs. 43-44 (Sec. 4.2):
+   *   u = -U sin^2(pi X) sin(2 pi Y) cos(pi t/T),
+   *   v =  U sin^2(pi Y) sin(2 pi X) cos(pi t/T),
+   * X = (x + 1/2)/nx, Y = (y + 1/2)/ny, t the step index; U < 0 gives the
+   * sign printed in Eqs. 43-44. */
+  int32_t flow;
+  int32_t reserved; /* set to 0 */
+  double W;         /* interface width (Eq. 4) */
+  double sigma;     /* surface tension; beta = 12 sigma/W, kappa = 3 sigma W/2 (Sec. 2) */
+  double lambda;    /* penalty constant (Eq. 6; 0.5 in the paper); 0 = classical C-H */
+  double xi;        /* regulariser of psi (Eq. 37; 1e-10 in the paper) */
+  double tau_g;     /* phase-field relaxation time; mobility M = (tau_g - 1/2)/3 (Eq. 34) */
+  double rho_l, rho_g;     /* densities of the phi = 1 and phi = 0 fluids */
+  double tau_f_l, tau_f_g; /* f relaxation times in each bulk; viscosity from Eq. 27 */
+  /* MRT rates of Eq. 26 in the moment order of Eq. 24.  s_f[7], s_f[8] are
+   * replaced by 1/tau_f(phi) and s_g[3], s_g[5] by 1/tau_g (Eqs. 27, 34);
+   * the other entries are free (the paper does not fix them; 1.0 is the
+   * usual choice) and must lie in (0, 2). */
+  double s_f[9], s_g[9];
+  double vortex_U, vortex_T; /* flow == LBM_FLOW_VORTEX only */
+} lbm_params;
+
+/* Device bytes the caller must provide for this batch (0 on bad params). */
+size_t lbm_workspace_bytes(const lbm_params* cases, int32_t ncases);
+
+/* Create a handle and set the initial state of every case (Sec. 4 set-ups):
+ *   phi = h_phi0[c] ([ny][nx], FP64), u = h_u0[c] ([2][ny][nx], FP64; the
+ *   array pointer or an entry may be NULL for a fluid at rest), p = 0;
+ *   hbar0 = Eq. 2 on phi0; g = g_eq(phi0, hbar0, u0) (Eq. 31);
+ *   f = f_eq(p = 0, rho(phi0), u0) (Eq. 22); phi*u at t-1 := phi0 u0.
+ * rho(phi) = rho_g + phi (rho_l - rho_g) and mu(phi) linear likewise;
+ * tau_f(x) = mu/(rho c_s^2) + 1/2 (Eq. 27).  In vortex mode u0 is ignored.
+ * d_workspace: device pointer, >= lbm_workspace_bytes(), 256-byte aligned.
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: LBM_ERR_ARG, LBM_ERR_WORKSPACE, LBM_ERR_CUDA. */
+int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace,
+             size_t ws_bytes, const double* const* h_phi0,
+             const double* const* h_u0, void* stream, lbm_handle** out);
+
+/* Advance every case by nsteps >= 0 coupled time steps (Eqs. 20-37):
+ * stream, phi = sum g (Eq. 35), psi (Eq. 37, phi clipped to [0,1]),
+ * isotropic stencils (Sec. 3.2), hbar (Eq. 2), F = hbar grad phi, u and p
+ * (Eqs. 28-29), MRT collision of f (Eqs. 21-25) and of g (Eqs. 31-33) with
+ * d_t(phi u) by backward difference.  Asynchronous on the handle's stream;
+ * long runs replay a captured CUDA graph.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_CUDA (launch failure; device faults surface at the next
+ * synchronising call). */
+int lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Declare the volume regions of case c: h_labels [ny][nx] with values in
+ * [0, nregions) or -1 (no region); NULL means one region = whole grid.
+ * 1 <= nregions <= 8.  Copies the labels into the workspace. */
+int lbm_set_regions(lbm_handle* h, int32_t c, const int8_t* h_labels,
+                    int32_t nregions);
+
+/* Phase volumes V_r = sum over region r of phi (the droplet volumes of
+ * Fig. 3b) for every case, reduced in FP64 in a fixed order (bitwise
+ * reproducible).  h_out receives lbm_num_regions(h) doubles, case-major.
+ * Synchronises; returns LBM_ERR_NONFINITE if a NaN/Inf was flagged. */
+int lbm_volume(lbm_handle* h, double* h_out);
+
+/* Same reduction, written to device memory d_out (lbm_num_regions doubles)
+ * without synchronising. */
+int lbm_volume_async(lbm_handle* h, double* d_out);
+
+/* Total number of volume regions over all cases. */
+int32_t lbm_num_regions(const lbm_handle* h);
+
+/* Macroscopic fields of case c at the current time, each [ny][nx] FP64:
+ * phi (Eq. 35), u (Eq. 28, or the prescribed velocity), p (Eq. 29, 0 in
+ * vortex mode).  Any pointer may be NULL.  Synchronises. */
+int lbm_fields(lbm_handle* h, int32_t c, double* h_phi, double* h_ux,
+               double* h_uy, double* h_p);
+
+/* Copy the state of case c to the host: the distributions f_i(x,t), g_i(x,t)
+ * after streaming (left-hand sides of Eqs. 20 and 30) as [9][ny][nx] FP64,
+ * phi*u at t-1 as [2][ny][nx], and the step index t.  h_f is ignored in
+ * vortex mode.  Any pointer may be NULL.  Synchronises. */
+int lbm_get_state(lbm_handle* h, int32_t c, double* h_f, double* h_g,
+                  double* h_j, int64_t* t);
+
+/* Overwrite the state of case c (same layout as lbm_get_state; values are
+ * rounded to the device precision) and set the step index of the batch. */
+int lbm_set_state(lbm_handle* h, int32_t c, const double* h_f,
+                  const double* h_g, const double* h_j, int64_t t);
+
+/* Current step index of the batch. */
+int64_t lbm_time(const lbm_handle* h);
+
+/* Checkpoint / resume: the raw device state of the batch (populations in
+ * device precision, phi*u, step index), bitwise.  lbm_save synchronises. */
+size_t lbm_checkpoint_bytes(const lbm_handle* h);
+int lbm_save(lbm_handle* h, void* h_buf, size_t bytes);
+int lbm_load(lbm_handle* h, const void* h_buf, size_t bytes);
+
+/* Synchronise the stream and report device-side error flags:
+ * LBM_OK, LBM_ERR_NONFINITE or LBM_ERR_CUDA.  Clears the flags. */
+int lbm_status(lbm_handle* h);
+
+/* Adjoint of the coupled step (not built): returns LBM_ERR_UNIMPLEMENTED. */
+int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out,
+                     double* h_param_grads);
+
+void lbm_destroy(lbm_handle* h);
+const char* lbm_status_string(int status);
+const char* lbm_last_error(void);
+int32_t lbm_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_API_H */

@@ -1,0 +1,10 @@
+// FP64 instantiation of the device kernels.
+#define LBM_T double
+#include "kern_impl.cuh"
+
+namespace lbmk {
+cudaError_t launch_clock(int64_t* t, int64_t n, cudaStream_t s) {
+  clock_kernel<<<1, 32, 0, s>>>(t, n);
+  return cudaGetLastError();
+}
+}  // namespace lbmk

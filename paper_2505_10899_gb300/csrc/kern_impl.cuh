@@ -1,0 +1,100 @@
+// Explicit instantiation of the launch wrappers for precision LBM_T.
+// Included by kern_f32.cu (LBM_T = float) and kern_f64.cu (LBM_T = double).
+#include "launch.h"
+#include "lbm_aux.cuh"
+#include "lbm_kernels.cuh"
+
+namespace lbmk {
+
+namespace {
+inline int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 65535 * 8) b = 65535 * 8;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <int BX>
+cudaError_t step_bx(const StepArgs<LBM_T>& a, bool coupled, int mode, int n, cudaStream_t s) {
+  if (coupled) {
+    if (mode == kModeStep)
+      step_kernel<LBM_T, BX, true, kModeStep><<<n, BX, 0, s>>>(a);
+    else
+      step_kernel<LBM_T, BX, true, kModeFields><<<n, BX, 0, s>>>(a);
+  } else {
+    if (mode == kModeStep)
+      step_kernel<LBM_T, BX, false, kModeStep><<<n, BX, 0, s>>>(a);
+    else
+      step_kernel<LBM_T, BX, false, kModeFields><<<n, BX, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+}  // namespace
+
+template <>
+cudaError_t launch_step<LBM_T>(const StepArgs<LBM_T>& a, int bx, bool coupled,
+                               int mode, int n_items, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  switch (bx) {
+    case 32: return step_bx<32>(a, coupled, mode, n_items, s);
+    case 64: return step_bx<64>(a, coupled, mode, n_items, s);
+    case 128: return step_bx<128>(a, coupled, mode, n_items, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t launch_init<LBM_T>(const CaseDev<LBM_T>& cd, double beta4, double kappa,
+                               double lambda, double rho_g, double drho,
+                               const double* phi0, const double* u0, int vortex,
+                               double vU, int parity, cudaStream_t s) {
+  const int64_t n = (int64_t)cd.nx * cd.ny;
+  init_kernel<LBM_T><<<grid_for(n, 256), 256, 0, s>>>(cd, beta4, kappa, lambda, rho_g,
+                                                      drho, phi0, u0, vortex, vU, parity);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_plane_import<LBM_T>(LBM_T* dst, const double* src, int i, int nx,
+                                       int ny, cudaStream_t s) {
+  plane_import<LBM_T><<<grid_for((int64_t)nx * ny, 256), 256, 0, s>>>(dst, src, i, nx, ny);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_plane_export<LBM_T>(double* dst, const LBM_T* src, int i, int nx,
+                                       int ny, cudaStream_t s) {
+  plane_export<LBM_T><<<grid_for((int64_t)nx * ny, 256), 256, 0, s>>>(dst, src, i, nx, ny);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_copy_to_T<LBM_T>(LBM_T* dst, const double* src, int64_t n, cudaStream_t s) {
+  copy_to_T<LBM_T><<<grid_for(n, 256), 256, 0, s>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_copy_to_f64<LBM_T>(double* dst, const LBM_T* src, int64_t n, cudaStream_t s) {
+  copy_to_f64<LBM_T><<<grid_for(n, 256), 256, 0, s>>>(dst, src, n);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_volume<LBM_T>(const CaseDev<LBM_T>* cases, int ncases,
+                                 const Item* items, int n_items, int bx, int parity,
+                                 double* part, double* out, cudaStream_t s) {
+  if (n_items <= 0) return cudaSuccess;
+  switch (bx) {
+    case 32: volume_partial<LBM_T, 32><<<n_items, 32, 0, s>>>(cases, items, parity, part); break;
+    case 64: volume_partial<LBM_T, 64><<<n_items, 64, 0, s>>>(cases, items, parity, part); break;
+    case 128: volume_partial<LBM_T, 128><<<n_items, 128, 0, s>>>(cases, items, parity, part); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int warps = 4;
+  volume_final<LBM_T><<<(ncases + warps - 1) / warps, 32 * warps, 0, s>>>(cases, ncases, part, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmk

@@ -1,0 +1,42 @@
+// Host-side launch wrappers of the device kernels (one translation unit per
+// precision instantiates them).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm_layout.h"
+
+namespace lbmk {
+
+// Supported strip widths (threads per CTA of the step kernel).
+inline bool valid_bx(int bx) { return bx == 32 || bx == 64 || bx == 128; }
+
+template <typename T>
+cudaError_t launch_step(const StepArgs<T>& a, int bx, bool coupled, int mode,
+                        int n_items, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_init(const CaseDev<T>& cd, double beta4, double kappa,
+                        double lambda, double rho_g, double drho,
+                        const double* phi0, const double* u0, int vortex,
+                        double vU, int parity, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_plane_import(T* dst_plane, const double* src, int i, int nx,
+                                int ny, cudaStream_t s);
+template <typename T>
+cudaError_t launch_plane_export(double* dst, const T* src_plane, int i, int nx,
+                                int ny, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_to_T(T* dst, const double* src, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_copy_to_f64(double* dst, const T* src, int64_t n, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_volume(const CaseDev<T>* cases, int ncases,
+                          const Item* items, int n_items, int bx, int parity,
+                          double* part, double* out, cudaStream_t s);
+
+cudaError_t launch_clock(int64_t* t, int64_t n, cudaStream_t s);
+
+}  // namespace lbmk

@@ -1,0 +1,824 @@
+// Host runtime behind the C ABI of include/lbm_api.h: parameter checks,
+// workspace carving, work-item tiling, CUDA-graph replay of the step loop,
+// state import/export, checkpointing and error reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm_api.h"
+#include "launch.h"
+#include "lbm_layout.h"
+
+using lbmk::CaseDev;
+using lbmk::Item;
+using lbmk::Phys;
+using lbmk::StepArgs;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define LBM_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess)                                                    \
+      return fail(LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kGraphSteps = 64;  // steps per captured graph (even)
+
+size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
+
+// Inverse squared norms of the rows of M (Eq. 24): M^-1 = M^T diag(D).
+const double kD[9] = {1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 6, 1.0 / 12,
+                      1.0 / 6, 1.0 / 12, 1.0 / 4,  1.0 / 4};
+
+struct Layout {
+  size_t hdr = 0, cases = 0, items = 0, part = 0, vol = 0, staging = 0;
+  std::vector<size_t> f, g, J, lab;  // per-case offsets (f: 2 buffers back to back)
+  std::vector<int64_t> plane;
+  size_t total = 0;
+};
+
+struct Tiling {
+  int bx = 128;
+  int rows = 32;
+};
+
+}  // namespace
+
+struct lbm_handle {
+  int ncases = 0;
+  int precision = LBM_F32;
+  int flow = LBM_FLOW_COUPLED;
+  std::vector<lbm_params> params;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream for graph capture
+  Layout L;
+  Tiling tile;
+  std::vector<Item> items;
+  std::vector<int> item_begin, item_end, vol_base, nregions;
+  int total_regions = 0;
+  int64_t t = 0;   // step index
+  int parity = 0;  // source buffer
+  Phys<float> pf{};
+  Phys<double> pd{};
+  std::vector<CaseDev<float>> cf;
+  std::vector<CaseDev<double>> cd;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_parity = -1;
+  // device pointers
+  int32_t* flags = nullptr;
+  int64_t* t_dev = nullptr;
+  Item* items_dev = nullptr;
+  void* cases_dev = nullptr;
+  double* part = nullptr;
+  double* vol = nullptr;
+  double* staging = nullptr;
+  int64_t max_plane = 0;
+};
+
+namespace {
+
+bool same(double a, double b) { return a == b || (std::isnan(a) && std::isnan(b)); }
+
+int check_params(const lbm_params* c, int n) {
+  if (!c || n < 1) return fail(LBM_ERR_ARG, "no cases");
+  for (int k = 0; k < n; ++k) {
+    const lbm_params& p = c[k];
+    char buf[160];
+    auto bad = [&](const char* what) {
+      snprintf(buf, sizeof buf, "case %d: %s", k, what);
+      return fail(LBM_ERR_ARG, buf);
+    };
+    if (p.abi_version != LBM_ABI_VERSION) return bad("abi_version mismatch");
+    if (p.nx < 1 || p.ny < 1 || p.nx > (1 << 20) || p.ny > (1 << 20))
+      return bad("nx, ny must lie in [1, 2^20]");
+    if ((int64_t)p.nx * p.ny > (int64_t(1) << 34)) return bad("grid too large");
+    if (p.precision != LBM_F64 && p.precision != LBM_F32) return bad("precision");
+    if (p.flow != LBM_FLOW_COUPLED && p.flow != LBM_FLOW_VORTEX) return bad("flow");
+    if (!(p.W > 0) || !std::isfinite(p.W)) return bad("W must be > 0");
+    if (!std::isfinite(p.sigma) || !std::isfinite(p.lambda)) return bad("sigma, lambda");
+    if (!(p.xi >= 0) || !std::isfinite(p.xi)) return bad("xi must be >= 0");
+    if (!(p.tau_g > 0.5) || !std::isfinite(p.tau_g)) return bad("tau_g must be > 1/2");
+    if (p.flow == LBM_FLOW_COUPLED) {
+      if (!(p.rho_l > 0) || !(p.rho_g > 0) || !std::isfinite(p.rho_l) || !std::isfinite(p.rho_g))
+        return bad("densities must be > 0");
+      if (!(p.tau_f_l > 0.5) || !(p.tau_f_g > 0.5) || !std::isfinite(p.tau_f_l) ||
+          !std::isfinite(p.tau_f_g))
+        return bad("tau_f must be > 1/2");
+    } else {
+      if (!(p.vortex_T != 0) || !std::isfinite(p.vortex_T) || !std::isfinite(p.vortex_U))
+        return bad("vortex_T must be nonzero");
+    }
+    for (int i = 0; i < 9; ++i) {
+      const bool tied_f = (i == 7 || i == 8), tied_g = (i == 3 || i == 5);
+      if (!tied_f && !(p.s_f[i] > 0 && p.s_f[i] < 2)) return bad("s_f rates must lie in (0,2)");
+      if (!tied_g && !(p.s_g[i] > 0 && p.s_g[i] < 2)) return bad("s_g rates must lie in (0,2)");
+    }
+    if (k > 0) {
+      const lbm_params& q = c[0];
+      bool ok = p.precision == q.precision && p.flow == q.flow && same(p.W, q.W) &&
+                same(p.sigma, q.sigma) && same(p.lambda, q.lambda) && same(p.xi, q.xi) &&
+                same(p.tau_g, q.tau_g) && same(p.vortex_U, q.vortex_U) &&
+                same(p.vortex_T, q.vortex_T);
+      for (int i = 0; i < 9; ++i) ok = ok && same(p.s_f[i], q.s_f[i]) && same(p.s_g[i], q.s_g[i]);
+      if (!ok) return bad("launch-uniform fields differ from case 0");
+    }
+  }
+  return LBM_OK;
+}
+
+size_t elem_size(int precision) { return precision == LBM_F64 ? 8 : 4; }
+
+// Work items: strips of bx columns, runs of `rows` rows.
+std::vector<Item> make_items(const lbm_params* c, int n, const Tiling& t,
+                             std::vector<int>* beg, std::vector<int>* end) {
+  std::vector<Item> it;
+  beg->assign(n, 0);
+  end->assign(n, 0);
+  for (int k = 0; k < n; ++k) {
+    (*beg)[k] = (int)it.size();
+    for (int y0 = 0; y0 < c[k].ny; y0 += t.rows)
+      for (int x0 = 0; x0 < c[k].nx; x0 += t.bx)
+        it.push_back(Item{k, x0, y0, std::min(t.rows, c[k].ny - y0)});
+    (*end)[k] = (int)it.size();
+  }
+  return it;
+}
+
+// Default tiling: wide strips and long runs (few halo re-reads) unless the
+// batch is too small to give every SM several CTAs.
+Tiling choose_tiling(const lbm_params* c, int n) {
+  int min_nx = c[0].nx;
+  int64_t nodes = 0;
+  for (int k = 0; k < n; ++k) {
+    min_nx = std::min(min_nx, c[k].nx);
+    nodes += (int64_t)c[k].nx * c[k].ny;
+  }
+  const int64_t want = 152 * 8;  // CTAs for a full machine
+  Tiling t;
+  t.bx = min_nx >= 128 ? 128 : (min_nx >= 64 ? 64 : 32);
+  for (;;) {
+    int64_t rows = nodes / (t.bx * want);
+    if (rows >= 16 || t.bx == 32) {
+      t.rows = (int)std::max<int64_t>(2, std::min<int64_t>(64, rows));
+      break;
+    }
+    t.bx /= 2;
+  }
+  return t;
+}
+
+Layout make_layout(const lbm_params* c, int n, int n_items, int total_regions) {
+  Layout L;
+  const size_t es = elem_size(c[0].precision);
+  const bool coupled = c[0].flow == LBM_FLOW_COUPLED;
+  size_t off = 0;
+  L.hdr = off;
+  off = align_up(off + 64);
+  L.cases = off;
+  off = align_up(off + (size_t)n * std::max(sizeof(CaseDev<float>), sizeof(CaseDev<double>)));
+  L.items = off;
+  off = align_up(off + (size_t)n_items * sizeof(Item));
+  L.part = off;
+  off = align_up(off + (size_t)n_items * lbmk::kMaxRegions * sizeof(double));
+  L.vol = off;
+  off = align_up(off + (size_t)std::max(total_regions, n * lbmk::kMaxRegions) * sizeof(double));
+  int64_t maxp = 0;
+  for (int k = 0; k < n; ++k) maxp = std::max<int64_t>(maxp, (int64_t)c[k].nx * c[k].ny);
+  L.staging = off;
+  off = align_up(off + (size_t)maxp * 4 * sizeof(double));
+  L.f.resize(n);
+  L.g.resize(n);
+  L.J.resize(n);
+  L.lab.resize(n);
+  L.plane.resize(n);
+  for (int k = 0; k < n; ++k) {
+    const int64_t nn = (int64_t)c[k].nx * c[k].ny;
+    const int64_t plane = (nn + 63) / 64 * 64;
+    L.plane[k] = plane;
+    const size_t pb = (size_t)plane * es;
+    L.g[k] = off;
+    off = align_up(off + 2 * 9 * pb);
+    if (coupled) {
+      L.f[k] = off;
+      off = align_up(off + 2 * 9 * pb);
+    } else {
+      L.f[k] = 0;
+    }
+    L.J[k] = off;
+    off = align_up(off + 2 * pb);
+    L.lab[k] = off;
+    off = align_up(off + (size_t)plane);
+  }
+  L.total = off;
+  return L;
+}
+
+template <typename T>
+Phys<T> make_phys(const lbm_params& p) {
+  Phys<T> ph{};
+  const double beta = 12.0 * p.sigma / p.W, kappa = 1.5 * p.sigma * p.W;  // Sec. 2
+  ph.beta4 = (T)(4.0 * beta);
+  ph.kappa = (T)kappa;
+  ph.lambda = (T)p.lambda;
+  ph.lamW = (T)(p.lambda / p.W);
+  ph.xi = (T)p.xi;
+  ph.tfac = (T)(4.0 / ((1.0 + 2.0 * p.xi) * (1.0 + 2.0 * p.xi)));
+  double sg[9];
+  for (int i = 0; i < 9; ++i) sg[i] = p.s_g[i];
+  sg[3] = sg[5] = 1.0 / p.tau_g;  // Eq. 34
+  for (int i = 0; i < 9; ++i) {
+    ph.fsD[i] = (T)(-p.s_f[i] * kD[i]);
+    ph.fhD[i] = (T)((1.0 - 0.5 * p.s_f[i]) * kD[i]);
+    ph.gsD[i] = (T)(-sg[i] * kD[i]);
+    ph.ghD3[i] = (T)((1.0 - 0.5 * sg[i]) * kD[i] / 3.0);
+  }
+  ph.vU = p.vortex_U;
+  ph.vT = p.vortex_T;
+  return ph;
+}
+
+template <typename T>
+CaseDev<T> make_case(const lbm_handle* h, int k) {
+  const lbm_params& p = h->params[k];
+  const Layout& L = h->L;
+  CaseDev<T> c{};
+  const size_t pb = (size_t)L.plane[k] * sizeof(T);
+  c.g[0] = (T*)(h->ws + L.g[k]);
+  c.g[1] = (T*)(h->ws + L.g[k] + 9 * pb);
+  if (h->flow == LBM_FLOW_COUPLED) {
+    c.f[0] = (T*)(h->ws + L.f[k]);
+    c.f[1] = (T*)(h->ws + L.f[k] + 9 * pb);
+  }
+  c.J = (T*)(h->ws + L.J[k]);
+  c.labels = nullptr;
+  c.plane = L.plane[k];
+  c.nx = p.nx;
+  c.ny = p.ny;
+  const double cs2 = 1.0 / 3.0;
+  const double rho_l = h->flow == LBM_FLOW_COUPLED ? p.rho_l : 1.0;
+  const double rho_g = h->flow == LBM_FLOW_COUPLED ? p.rho_g : 1.0;
+  c.rho_g = (T)rho_g;
+  c.drho = (T)(rho_l - rho_g);
+  const double mu_l = rho_l * cs2 * (p.tau_f_l - 0.5), mu_g = rho_g * cs2 * (p.tau_f_g - 0.5);
+  c.mu_g = (T)mu_g;
+  c.dmu = (T)(mu_l - mu_g);
+  c.var_tau = (p.tau_f_l != p.tau_f_g) ? 1 : 0;
+  const double s7 = 1.0 / p.tau_f_l;  // Eq. 27, uniform tau_f
+  c.sD7 = (T)(-0.25 * s7);
+  c.hD7 = (T)(0.25 * (1.0 - 0.5 * s7));
+  c.nregions = h->nregions[k];
+  c.vol_base = h->vol_base[k];
+  c.item_begin = h->item_begin[k];
+  c.item_end = h->item_end[k];
+  return c;
+}
+
+template <typename T>
+CaseDev<T>& case_of(lbm_handle* h, int c) {
+  if constexpr (sizeof(T) == 4) return h->cf[c]; else return h->cd[c];
+}
+
+int upload_cases(lbm_handle* h) {
+  if (h->precision == LBM_F32) {
+    h->cf.resize(h->ncases);
+    for (int k = 0; k < h->ncases; ++k) {
+      CaseDev<float> c = make_case<float>(h, k);
+      c.labels = h->cf[k].labels;
+      h->cf[k] = c;
+    }
+    LBM_CUDA(cudaMemcpyAsync(h->cases_dev, h->cf.data(), h->cf.size() * sizeof(CaseDev<float>),
+                             cudaMemcpyHostToDevice, h->stream));
+  } else {
+    h->cd.resize(h->ncases);
+    for (int k = 0; k < h->ncases; ++k) {
+      CaseDev<double> c = make_case<double>(h, k);
+      c.labels = h->cd[k].labels;
+      h->cd[k] = c;
+    }
+    LBM_CUDA(cudaMemcpyAsync(h->cases_dev, h->cd.data(), h->cd.size() * sizeof(CaseDev<double>),
+                             cudaMemcpyHostToDevice, h->stream));
+  }
+  // the host vectors must stay alive until the copy ran: synchronise
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+template <typename T>
+StepArgs<T> step_args(const lbm_handle* h, int parity, int64_t t_off) {
+  StepArgs<T> a{};
+  if constexpr (sizeof(T) == 4) a.ph = h->pf; else a.ph = h->pd;
+  a.cases = (const CaseDev<T>*)h->cases_dev;
+  a.items = h->items_dev;
+  a.t_base = h->t_dev;
+  a.t_off = t_off;
+  a.parity = parity;
+  a.flags = h->flags;
+  return a;
+}
+
+// Enqueue `count` consecutive steps starting from source buffer `parity`,
+// then advance the device clock.
+int enqueue_steps(lbm_handle* h, cudaStream_t s, int parity, int count) {
+  const bool coupled = h->flow == LBM_FLOW_COUPLED;
+  const int n = (int)h->items.size();
+  for (int j = 0; j < count; ++j) {
+    const int par = (parity + j) & 1;
+    cudaError_t e;
+    if (h->precision == LBM_F32)
+      e = lbmk::launch_step<float>(step_args<float>(h, par, j), h->tile.bx, coupled,
+                                   lbmk::kModeStep, n, s);
+    else
+      e = lbmk::launch_step<double>(step_args<double>(h, par, j), h->tile.bx, coupled,
+                                    lbmk::kModeStep, n, s);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+  }
+  LBM_CUDA(lbmk::launch_clock(h->t_dev, count, s));
+  return LBM_OK;
+}
+
+void drop_graph(lbm_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  h->graph_parity = -1;
+}
+
+int build_graph(lbm_handle* h) {
+  drop_graph(h);
+  LBM_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  int rc = enqueue_steps(h, h->cap, h->parity, kGraphSteps);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  if (rc != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->gexec = nullptr;
+    return fail(LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  h->graph_parity = h->parity;
+  return LBM_OK;
+}
+
+int check_case(const lbm_handle* h, int c) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (c < 0 || c >= h->ncases) return fail(LBM_ERR_ARG, "case index out of range");
+  return LBM_OK;
+}
+
+int read_flags(lbm_handle* h) {
+  int32_t fl = 0;
+  LBM_CUDA(cudaMemcpyAsync(&fl, h->flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (fl & lbmk::kFlagNonFinite) return fail(LBM_ERR_NONFINITE, "non-finite macroscopic field");
+  return LBM_OK;
+}
+
+template <typename T>
+int do_fields(lbm_handle* h, int c, double* phi, double* ux, double* uy, double* p) {
+  const int64_t n = (int64_t)h->params[c].nx * h->params[c].ny;
+  double* st = h->staging;
+  StepArgs<T> a = step_args<T>(h, h->parity, 0);
+  a.items = h->items_dev + h->item_begin[c];
+  a.out_phi = st;
+  a.out_ux = st + n;
+  a.out_uy = st + 2 * n;
+  a.out_p = st + 3 * n;
+  cudaError_t e = lbmk::launch_step<T>(a, h->tile.bx, h->flow == LBM_FLOW_COUPLED,
+                                       lbmk::kModeFields, h->item_end[c] - h->item_begin[c],
+                                       h->stream);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("fields: ") + cudaGetErrorString(e));
+  double* outs[4] = {phi, ux, uy, p};
+  for (int q = 0; q < 4; ++q)
+    if (outs[q])
+      LBM_CUDA(cudaMemcpyAsync(outs[q], st + q * n, n * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+template <typename T>
+int do_get_state(lbm_handle* h, int c, double* f, double* g, double* j) {
+  const lbm_params& p = h->params[c];
+  const int64_t n = (int64_t)p.nx * p.ny;
+  const CaseDev<T>& cd = case_of<T>(h, c);
+  double* st = h->staging;
+  for (int which = 0; which < 2; ++which) {
+    double* out = which == 0 ? g : f;
+    const T* buf = which == 0 ? cd.g[h->parity] : cd.f[h->parity];
+    if (!out || !buf) continue;
+    for (int i = 0; i < 9; ++i) {
+      cudaError_t e = lbmk::launch_plane_export<T>(st, buf + i * cd.plane, i, p.nx, p.ny, h->stream);
+      if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+      LBM_CUDA(cudaMemcpyAsync(out + i * n, st, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      LBM_CUDA(cudaStreamSynchronize(h->stream));
+    }
+  }
+  if (j) {
+    for (int q = 0; q < 2; ++q) {
+      cudaError_t e = lbmk::launch_copy_to_f64<T>(st, cd.J + q * cd.plane, n, h->stream);
+      if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+      LBM_CUDA(cudaMemcpyAsync(j + q * n, st, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      LBM_CUDA(cudaStreamSynchronize(h->stream));
+    }
+  }
+  return LBM_OK;
+}
+
+template <typename T>
+int do_set_state(lbm_handle* h, int c, const double* f, const double* g, const double* j) {
+  const lbm_params& p = h->params[c];
+  const int64_t n = (int64_t)p.nx * p.ny;
+  const CaseDev<T>& cd = case_of<T>(h, c);
+  double* st = h->staging;
+  for (int which = 0; which < 2; ++which) {
+    const double* in = which == 0 ? g : f;
+    T* buf = which == 0 ? cd.g[h->parity] : cd.f[h->parity];
+    if (!in || !buf) continue;
+    for (int i = 0; i < 9; ++i) {
+      LBM_CUDA(cudaMemcpyAsync(st, in + i * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      cudaError_t e = lbmk::launch_plane_import<T>(buf + i * cd.plane, st, i, p.nx, p.ny, h->stream);
+      if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+      LBM_CUDA(cudaStreamSynchronize(h->stream));
+    }
+  }
+  if (j) {
+    for (int q = 0; q < 2; ++q) {
+      LBM_CUDA(cudaMemcpyAsync(st, j + q * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+      cudaError_t e = lbmk::launch_copy_to_T<T>(cd.J + q * cd.plane, st, n, h->stream);
+      if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+      LBM_CUDA(cudaStreamSynchronize(h->stream));
+    }
+  }
+  return LBM_OK;
+}
+
+int set_clock(lbm_handle* h) {
+  LBM_CUDA(cudaMemcpyAsync(h->t_dev, &h->t, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+struct CkptHeader {
+  char magic[8];
+  int32_t abi, precision, flow, ncases;
+  int64_t t;
+  uint64_t payload;
+  char pad[24];
+};
+
+size_t state_bytes_case(const lbm_handle* h, int k) {
+  const size_t es = elem_size(h->precision);
+  const int64_t n = (int64_t)h->params[k].nx * h->params[k].ny;
+  const int planes = (h->flow == LBM_FLOW_COUPLED ? 18 : 9) + 2;
+  return (size_t)planes * n * es;
+}
+
+}  // namespace
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+int32_t lbm_abi_version(void) { return LBM_ABI_VERSION; }
+
+const char* lbm_last_error(void) { return g_err.c_str(); }
+
+const char* lbm_status_string(int s) {
+  switch (s) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_ARG: return "invalid argument";
+    case LBM_ERR_CUDA: return "CUDA error";
+    case LBM_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case LBM_ERR_NONFINITE: return "non-finite value in the fields";
+    case LBM_ERR_TIMEOUT: return "device wait timed out";
+    case LBM_ERR_UNIMPLEMENTED: return "not implemented";
+    default: return "unknown status";
+  }
+}
+
+size_t lbm_workspace_bytes(const lbm_params* cases, int32_t ncases) {
+  if (check_params(cases, ncases) != LBM_OK) return 0;
+  Tiling t = choose_tiling(cases, ncases);
+  std::vector<int> b, e;
+  std::vector<Item> it = make_items(cases, ncases, t, &b, &e);
+  return make_layout(cases, ncases, (int)it.size(), ncases * lbmk::kMaxRegions).total;
+}
+
+int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t ws_bytes,
+             const double* const* h_phi0, const double* const* h_u0, void* stream,
+             lbm_handle** out) {
+  if (!out) return fail(LBM_ERR_ARG, "out is null");
+  *out = nullptr;
+  int rc = check_params(cases, ncases);
+  if (rc) return rc;
+  if (!h_phi0) return fail(LBM_ERR_ARG, "h_phi0 is null");
+  for (int k = 0; k < ncases; ++k)
+    if (!h_phi0[k]) return fail(LBM_ERR_ARG, "h_phi0[c] is null");
+  if (!d_workspace) return fail(LBM_ERR_WORKSPACE, "workspace is null");
+  if ((uintptr_t)d_workspace % kAlign) return fail(LBM_ERR_WORKSPACE, "workspace not 256-byte aligned");
+
+  lbm_handle* h = new lbm_handle();
+  h->ncases = ncases;
+  h->params.assign(cases, cases + ncases);
+  h->precision = cases[0].precision;
+  h->flow = cases[0].flow;
+  h->stream = (cudaStream_t)stream;
+  h->tile = choose_tiling(cases, ncases);
+  h->items = make_items(cases, ncases, h->tile, &h->item_begin, &h->item_end);
+  h->nregions.assign(ncases, 1);
+  h->vol_base.resize(ncases);
+  for (int k = 0; k < ncases; ++k) h->vol_base[k] = k;
+  h->total_regions = ncases;
+  h->L = make_layout(cases, ncases, (int)h->items.size(), ncases * lbmk::kMaxRegions);
+  if (ws_bytes < h->L.total) {
+    delete h;
+    return fail(LBM_ERR_WORKSPACE, "workspace too small: need " + std::to_string(h->L.total));
+  }
+  h->ws = (char*)d_workspace;
+  h->ws_bytes = ws_bytes;
+  h->flags = (int32_t*)(h->ws + h->L.hdr);
+  h->t_dev = (int64_t*)(h->ws + h->L.hdr + 16);
+  h->cases_dev = h->ws + h->L.cases;
+  h->items_dev = (Item*)(h->ws + h->L.items);
+  h->part = (double*)(h->ws + h->L.part);
+  h->vol = (double*)(h->ws + h->L.vol);
+  h->staging = (double*)(h->ws + h->L.staging);
+  h->pf = make_phys<float>(cases[0]);
+  h->pd = make_phys<double>(cases[0]);
+
+  auto cleanup = [&](int code) {
+    lbm_destroy(h);
+    return code;
+  };
+  if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
+    return cleanup(fail(LBM_ERR_CUDA, "cannot create capture stream"));
+  if (cudaMemsetAsync(h->ws + h->L.hdr, 0, 64, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->items_dev, h->items.data(), h->items.size() * sizeof(Item),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return cleanup(fail(LBM_ERR_CUDA, "header upload failed"));
+  // labels planes: zero (region 0 everywhere) until lbm_set_regions
+  rc = upload_cases(h);
+  if (rc) return cleanup(rc);
+
+  const bool vortex = h->flow == LBM_FLOW_VORTEX;
+  for (int k = 0; k < ncases; ++k) {
+    const lbm_params& p = cases[k];
+    const int64_t n = (int64_t)p.nx * p.ny;
+    double* st = h->staging;
+    if (cudaMemcpyAsync(st, h_phi0[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return cleanup(fail(LBM_ERR_CUDA, "phi0 upload failed"));
+    const double* u0d = nullptr;
+    if (!vortex && h_u0 && h_u0[k]) {
+      if (cudaMemcpyAsync(st + n, h_u0[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return cleanup(fail(LBM_ERR_CUDA, "u0 upload failed"));
+      u0d = st + n;
+    }
+    const double beta4 = 4.0 * (12.0 * p.sigma / p.W), kappa = 1.5 * p.sigma * p.W;
+    const double rho_g = vortex ? 1.0 : p.rho_g, drho = vortex ? 0.0 : p.rho_l - p.rho_g;
+    cudaError_t e;
+    if (h->precision == LBM_F32)
+      e = lbmk::launch_init<float>(h->cf[k], beta4, kappa, p.lambda, rho_g, drho, st, u0d,
+                                   vortex, p.vortex_U, 0, h->stream);
+    else
+      e = lbmk::launch_init<double>(h->cd[k], beta4, kappa, p.lambda, rho_g, drho, st, u0d,
+                                    vortex, p.vortex_U, 0, h->stream);
+    if (e != cudaSuccess) return cleanup(fail(LBM_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e)));
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return cleanup(fail(LBM_ERR_CUDA, "init sync failed"));
+  }
+  *out = h;
+  return LBM_OK;
+}
+
+int lbm_step(lbm_handle* h, int64_t nsteps) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps < 0");
+  while (nsteps > 0) {
+    if (nsteps >= kGraphSteps) {
+      if (!h->gexec || h->graph_parity != h->parity) {
+        if (h->gexec && h->graph_parity != h->parity) {
+          // realign the buffer parity with the captured graph by one step
+          int rc = enqueue_steps(h, h->stream, h->parity, 1);
+          if (rc) return rc;
+          h->parity ^= 1;
+          h->t += 1;
+          nsteps -= 1;
+          continue;
+        }
+        int rc = build_graph(h);
+        if (rc) return rc;
+      }
+      LBM_CUDA(cudaGraphLaunch(h->gexec, h->stream));
+      h->t += kGraphSteps;  // kGraphSteps is even: parity unchanged
+      nsteps -= kGraphSteps;
+    } else {
+      const int cnt = (int)nsteps;
+      int rc = enqueue_steps(h, h->stream, h->parity, cnt);
+      if (rc) return rc;
+      h->parity ^= (cnt & 1);
+      h->t += cnt;
+      nsteps = 0;
+    }
+  }
+  return LBM_OK;
+}
+
+int lbm_set_regions(lbm_handle* h, int32_t c, const int8_t* h_labels, int32_t nregions) {
+  int rc = check_case(h, c);
+  if (rc) return rc;
+  if (nregions < 1 || nregions > lbmk::kMaxRegions)
+    return fail(LBM_ERR_ARG, "nregions must lie in [1, 8]");
+  const int64_t n = (int64_t)h->params[c].nx * h->params[c].ny;
+  const int8_t* dlab = nullptr;
+  if (h_labels) {
+    for (int64_t k = 0; k < n; ++k)
+      if (h_labels[k] >= nregions) return fail(LBM_ERR_ARG, "label >= nregions");
+    int8_t* d = (int8_t*)(h->ws + h->L.lab[c]);
+    LBM_CUDA(cudaMemcpyAsync(d, h_labels, n, cudaMemcpyHostToDevice, h->stream));
+    dlab = d;
+  }
+  h->nregions[c] = nregions;
+  int base = 0;
+  for (int k = 0; k < h->ncases; ++k) {
+    h->vol_base[k] = base;
+    base += h->nregions[k];
+  }
+  h->total_regions = base;
+  if (h->precision == LBM_F32) h->cf[c].labels = dlab;
+  else h->cd[c].labels = dlab;
+  return upload_cases(h);
+}
+
+int32_t lbm_num_regions(const lbm_handle* h) { return h ? h->total_regions : 0; }
+
+int lbm_volume_async(lbm_handle* h, double* d_out) {
+  if (!h || !d_out) return fail(LBM_ERR_ARG, "null argument");
+  cudaError_t e;
+  const int n = (int)h->items.size();
+  if (h->precision == LBM_F32)
+    e = lbmk::launch_volume<float>((const CaseDev<float>*)h->cases_dev, h->ncases, h->items_dev, n,
+                                   h->tile.bx, h->parity, h->part, d_out, h->stream);
+  else
+    e = lbmk::launch_volume<double>((const CaseDev<double>*)h->cases_dev, h->ncases, h->items_dev, n,
+                                    h->tile.bx, h->parity, h->part, d_out, h->stream);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("volume: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_volume(lbm_handle* h, double* h_out) {
+  if (!h || !h_out) return fail(LBM_ERR_ARG, "null argument");
+  int rc = lbm_volume_async(h, h->vol);
+  if (rc) return rc;
+  LBM_CUDA(cudaMemcpyAsync(h_out, h->vol, h->total_regions * sizeof(double), cudaMemcpyDeviceToHost,
+                           h->stream));
+  return read_flags(h);
+}
+
+int lbm_fields(lbm_handle* h, int32_t c, double* phi, double* ux, double* uy, double* p) {
+  int rc = check_case(h, c);
+  if (rc) return rc;
+  if (h->precision == LBM_F32) return do_fields<float>(h, c, phi, ux, uy, p);
+  return do_fields<double>(h, c, phi, ux, uy, p);
+}
+
+int lbm_get_state(lbm_handle* h, int32_t c, double* f, double* g, double* j, int64_t* t) {
+  int rc = check_case(h, c);
+  if (rc) return rc;
+  if (t) *t = h->t;
+  if (h->flow != LBM_FLOW_COUPLED) f = nullptr;
+  if (h->precision == LBM_F32) return do_get_state<float>(h, c, f, g, j);
+  return do_get_state<double>(h, c, f, g, j);
+}
+
+int lbm_set_state(lbm_handle* h, int32_t c, const double* f, const double* g, const double* j,
+                  int64_t t) {
+  int rc = check_case(h, c);
+  if (rc) return rc;
+  if (t < 0) return fail(LBM_ERR_ARG, "t < 0");
+  if (h->flow != LBM_FLOW_COUPLED) f = nullptr;
+  rc = (h->precision == LBM_F32) ? do_set_state<float>(h, c, f, g, j)
+                                 : do_set_state<double>(h, c, f, g, j);
+  if (rc) return rc;
+  h->t = t;
+  return set_clock(h);
+}
+
+int64_t lbm_time(const lbm_handle* h) { return h ? h->t : -1; }
+
+size_t lbm_checkpoint_bytes(const lbm_handle* h) {
+  if (!h) return 0;
+  size_t b = sizeof(CkptHeader);
+  for (int k = 0; k < h->ncases; ++k) b += state_bytes_case(h, k);
+  return b;
+}
+
+int lbm_save(lbm_handle* h, void* h_buf, size_t bytes) {
+  if (!h || !h_buf) return fail(LBM_ERR_ARG, "null argument");
+  if (bytes < lbm_checkpoint_bytes(h)) return fail(LBM_ERR_ARG, "buffer too small");
+  CkptHeader hd{};
+  memcpy(hd.magic, "LBMCKPT1", 8);
+  hd.abi = LBM_ABI_VERSION;
+  hd.precision = h->precision;
+  hd.flow = h->flow;
+  hd.ncases = h->ncases;
+  hd.t = h->t;
+  hd.payload = lbm_checkpoint_bytes(h) - sizeof(CkptHeader);
+  memcpy(h_buf, &hd, sizeof hd);
+  char* p = (char*)h_buf + sizeof hd;
+  const size_t es = elem_size(h->precision);
+  for (int k = 0; k < h->ncases; ++k) {
+    const int64_t n = (int64_t)h->params[k].nx * h->params[k].ny;
+    const size_t pb = (size_t)h->L.plane[k] * es;
+    const char* gb = h->ws + h->L.g[k] + h->parity * 9 * pb;
+    LBM_CUDA(cudaMemcpy2DAsync(p, n * es, gb, pb, n * es, 9, cudaMemcpyDeviceToHost, h->stream));
+    p += 9 * n * es;
+    if (h->flow == LBM_FLOW_COUPLED) {
+      const char* fb = h->ws + h->L.f[k] + h->parity * 9 * pb;
+      LBM_CUDA(cudaMemcpy2DAsync(p, n * es, fb, pb, n * es, 9, cudaMemcpyDeviceToHost, h->stream));
+      p += 9 * n * es;
+    }
+    LBM_CUDA(cudaMemcpy2DAsync(p, n * es, h->ws + h->L.J[k], pb, n * es, 2, cudaMemcpyDeviceToHost,
+                               h->stream));
+    p += 2 * n * es;
+  }
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_load(lbm_handle* h, const void* h_buf, size_t bytes) {
+  if (!h || !h_buf) return fail(LBM_ERR_ARG, "null argument");
+  if (bytes < lbm_checkpoint_bytes(h)) return fail(LBM_ERR_ARG, "buffer too small");
+  CkptHeader hd;
+  memcpy(&hd, h_buf, sizeof hd);
+  if (memcmp(hd.magic, "LBMCKPT1", 8) != 0 || hd.abi != LBM_ABI_VERSION ||
+      hd.precision != h->precision || hd.flow != h->flow || hd.ncases != h->ncases ||
+      hd.payload != lbm_checkpoint_bytes(h) - sizeof(CkptHeader))
+    return fail(LBM_ERR_ARG, "checkpoint does not match this handle");
+  const char* p = (const char*)h_buf + sizeof hd;
+  const size_t es = elem_size(h->precision);
+  for (int k = 0; k < h->ncases; ++k) {
+    const int64_t n = (int64_t)h->params[k].nx * h->params[k].ny;
+    const size_t pb = (size_t)h->L.plane[k] * es;
+    char* gb = h->ws + h->L.g[k] + h->parity * 9 * pb;
+    LBM_CUDA(cudaMemcpy2DAsync(gb, pb, p, n * es, n * es, 9, cudaMemcpyHostToDevice, h->stream));
+    p += 9 * n * es;
+    if (h->flow == LBM_FLOW_COUPLED) {
+      char* fb = h->ws + h->L.f[k] + h->parity * 9 * pb;
+      LBM_CUDA(cudaMemcpy2DAsync(fb, pb, p, n * es, n * es, 9, cudaMemcpyHostToDevice, h->stream));
+      p += 9 * n * es;
+    }
+    LBM_CUDA(cudaMemcpy2DAsync(h->ws + h->L.J[k], pb, p, n * es, n * es, 2, cudaMemcpyHostToDevice,
+                               h->stream));
+    p += 2 * n * es;
+  }
+  h->t = hd.t;
+  return set_clock(h);
+}
+
+int lbm_status(lbm_handle* h) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  int rc = read_flags(h);
+  LBM_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int32_t), h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, double* h_param_grads) {
+  (void)h;
+  (void)d_adj_in;
+  (void)d_adj_out;
+  (void)h_param_grads;
+  return fail(LBM_ERR_UNIMPLEMENTED, "lbm_adjoint_step is not built");
+}
+
+void lbm_destroy(lbm_handle* h) {
+  if (!h) return;
+  drop_graph(h);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,191 @@
+// Auxiliary kernels: initial state, state import/export, phase volumes,
+// step clock.  None of them is on the per-step path except the clock.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm_layout.h"
+
+namespace lbmk {
+
+__device__ __constant__ static const int kCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ __constant__ static const int kCY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// Position in a pull buffer that holds the value population i must deliver
+// to node (x, y): (x - c_ix, y - c_iy), periodic.
+__device__ __forceinline__ int64_t pull_src(int i, int x, int y, int nx, int ny) {
+  int xs = x - kCX[i], ys = y - kCY[i];
+  xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+  ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+  return (int64_t)ys * nx + xs;
+}
+
+// Initial state (Sec. 4 set-ups), computed in FP64 and rounded once:
+// hbar0 = 4 beta phi0 (phi0-1)(phi0-1/2) - kappa lap(phi0) (Eq. 2),
+// g = g_eq(phi0, hbar0, u0) (Eq. 31), f = f_eq(p=0, rho(phi0), u0) (Eq. 22),
+// phi*u at t-1 = phi0 u0.
+template <typename T>
+__global__ void init_kernel(CaseDev<T> cd, double beta4, double kappa,
+                            double lambda, double rho_g, double drho,
+                            const double* __restrict__ phi0,
+                            const double* __restrict__ u0, int vortex,
+                            double vU, int parity) {
+  const int nx = cd.nx, ny = cd.ny;
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const double p = phi0[k];
+    const double pE = phi0[(int64_t)y * nx + xp], pW = phi0[(int64_t)y * nx + xm];
+    const double pN = phi0[(int64_t)yp * nx + x], pS = phi0[(int64_t)ym * nx + x];
+    const double pNE = phi0[(int64_t)yp * nx + xp], pNW = phi0[(int64_t)yp * nx + xm];
+    const double pSE = phi0[(int64_t)ym * nx + xp], pSW = phi0[(int64_t)ym * nx + xm];
+    const double lap = (2.0 / 3.0) * (((pE + pW) + (pN + pS)) - 4.0 * p) +
+                       (1.0 / 6.0) * (((pNE + pNW) + (pSE + pSW)) - 4.0 * p);
+    const double mu = beta4 * p * (p - 1.0) * (p - 0.5) - kappa * lap;
+    double ux = 0.0, uy = 0.0;
+    if (vortex) {
+      double sx, cx, sy, cy;
+      sincospi((x + 0.5) / nx, &sx, &cx);
+      sincospi((y + 0.5) / ny, &sy, &cy);
+      ux = -vU * sx * sx * (2.0 * sy * cy);
+      uy = vU * sy * sy * (2.0 * sx * cx);
+    } else if (u0) {
+      ux = u0[k];
+      uy = u0[n + k];
+    }
+    const double lam = mu + lambda * p;
+    const double Jx = p * ux, Jy = p * uy;
+    const double rho = rho_g + p * drho;
+    const double u2 = ux * ux + uy * uy;
+    const int par = parity;
+    T* gb = cd.g[par];
+    T* fb = cd.f[par];
+    for (int i = 0; i < 9; ++i) {
+      const double w = (i == 0) ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+      const double cu = kCX[i] * ux + kCY[i] * uy;
+      const double cJ = kCX[i] * Jx + kCY[i] * Jy;
+      const double gi = (i == 0) ? p + (w - 1.0) * lam : w * lam + 3.0 * w * cJ;
+      const int64_t dst = (int64_t)i * cd.plane + pull_src(i, x, y, nx, ny);
+      gb[dst] = (T)gi;
+      if (fb) fb[dst] = (T)(rho * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2));
+    }
+    cd.J[k] = (T)Jx;
+    cd.J[cd.plane + k] = (T)Jy;
+  }
+}
+
+// Import one population plane (FP64 host layout, value at the node it
+// belongs to after streaming) into a pull buffer, or export it.
+template <typename T>
+__global__ void plane_import(T* __restrict__ dst_plane, const double* __restrict__ src,
+                             int i, int nx, int ny) {
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    dst_plane[pull_src(i, x, y, nx, ny)] = (T)src[k];
+  }
+}
+
+template <typename T>
+__global__ void plane_export(double* __restrict__ dst, const T* __restrict__ src_plane,
+                             int i, int nx, int ny) {
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    dst[k] = (double)src_plane[pull_src(i, x, y, nx, ny)];
+  }
+}
+
+// Plain (unshifted) plane copies with precision change, for phi*u.
+template <typename T>
+__global__ void copy_to_T(T* __restrict__ dst, const double* __restrict__ src, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = (T)src[k];
+}
+template <typename T>
+__global__ void copy_to_f64(double* __restrict__ dst, const T* __restrict__ src, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = (double)src[k];
+}
+
+// Phase volumes, pass 1: every CTA reduces phi = sum_i g_i (pulled, Eq. 35)
+// over its work item into per-region FP64 partials, in a fixed order.
+template <typename T, int BX>
+__global__ void __launch_bounds__(BX) volume_partial(const CaseDev<T>* __restrict__ cases,
+                                                     const Item* __restrict__ items,
+                                                     int parity, double* __restrict__ part) {
+  __shared__ double red[BX / 32][kMaxRegions];
+  const Item it = items[blockIdx.x];
+  const CaseDev<T>& cd = cases[it.c];
+  const int nx = cd.nx, ny = cd.ny, nr = cd.nregions;
+  const int64_t P = cd.plane;
+  const int x = it.x0 + threadIdx.x;
+  const bool act = x < nx;
+  const T* __restrict__ gs = cd.g[parity];
+  double acc[kMaxRegions];
+#pragma unroll
+  for (int r = 0; r < kMaxRegions; ++r) acc[r] = 0.0;
+  if (act) {
+    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
+    for (int k = 0; k < it.nrows; ++k) {
+      const int y = it.y0 + k;
+      const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+      const int64_t o0 = (int64_t)y * nx, om = (int64_t)ym * nx, op = (int64_t)yp * nx;
+      double phi = (double)gs[o0 + x];
+      phi += (double)gs[P + o0 + xm];
+      phi += (double)gs[2 * P + om + x];
+      phi += (double)gs[3 * P + o0 + xp];
+      phi += (double)gs[4 * P + op + x];
+      phi += (double)gs[5 * P + om + xm];
+      phi += (double)gs[6 * P + om + xp];
+      phi += (double)gs[7 * P + op + xp];
+      phi += (double)gs[8 * P + op + xm];
+      const int lab = cd.labels ? (int)cd.labels[o0 + x] : 0;
+#pragma unroll
+      for (int r = 0; r < kMaxRegions; ++r)
+        if (lab == r) acc[r] += phi;
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < kMaxRegions; ++r) {
+    double v = acc[r];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][r] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kMaxRegions) {
+    double v = 0.0;
+    for (int w = 0; w < BX / 32; ++w) v += red[w][threadIdx.x];
+    if (threadIdx.x < nr) part[(int64_t)blockIdx.x * kMaxRegions + threadIdx.x] = v;
+  }
+}
+
+// Phase volumes, pass 2: one warp per case sums its items' partials in
+// item order (deterministic), lane r holding region r.
+template <typename T>
+__global__ void volume_final(const CaseDev<T>* __restrict__ cases, int ncases,
+                             const double* __restrict__ part, double* __restrict__ out) {
+  const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= ncases) return;
+  const CaseDev<T>& cd = cases[c];
+  if (lane >= cd.nregions) return;
+  double v = 0.0;
+  for (int b = cd.item_begin; b < cd.item_end; ++b) v += part[(int64_t)b * kMaxRegions + lane];
+  out[cd.vol_base + lane] = v;
+}
+
+// Step clock: t += n after a group of steps (read by the vortex flow).
+static __global__ void clock_kernel(int64_t* t, int64_t n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *t += n;
+}
+
+}  // namespace lbmk

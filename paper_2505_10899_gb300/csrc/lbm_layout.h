@@ -1,0 +1,74 @@
+// Device-side data layout shared by the host runtime (lbm_api.cu) and the
+// kernels.  One "case" is one periodic nx x ny grid; a batch holds several.
+//
+// Populations are structure-of-arrays planes: plane i of a buffer holds the
+// post-collision value f*_i at every node, [y][x] with x fastest, so that the
+// pull step of Eqs. 20/30 reads f_i(x, t+1) = f*_i(x - c_i, t) from plane i.
+// Two buffers (parity 0/1) alternate between source and destination.
+#pragma once
+#include <cstdint>
+
+namespace lbmk {
+
+constexpr int kQ = 9;
+constexpr int kMaxRegions = 8;
+
+template <typename T>
+struct CaseDev {
+  T* f[2];               // hydrodynamic populations, 9 planes per buffer
+  T* g[2];               // phase-field populations, 9 planes per buffer
+  T* J;                  // phi*u of the previous step, 2 planes (in place)
+  const int8_t* labels;  // volume regions, [y][x]; nullptr = one region
+  int64_t plane;         // elements per plane (nx*ny rounded up)
+  int32_t nx, ny;
+  T rho_g, drho;         // rho(phi) = rho_g + phi*drho
+  T mu_g, dmu;           // mu(phi)  = mu_g + phi*dmu
+  T sD7, hD7;            // uniform tau_f: -s7/4 and (1 - s7/2)/4 (s8 = s7)
+  int32_t var_tau;       // 1: tau_f varies with phi (Eq. 27 per node)
+  int32_t nregions;      // volume regions of this case
+  int32_t vol_base;      // first output slot of this case's volumes
+  int32_t item_begin, item_end;  // work items of this case
+};
+
+// Launch-uniform physics, converted to the working precision T.
+// Moment-space rates are folded with the inverse row norms
+// D = diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) of Eq. 24:
+//   sD[k] = -s_k D_k,  hD[k] = (1 - s_k/2) D_k.
+template <typename T>
+struct Phys {
+  T beta4;   // 4 beta, beta = 12 sigma / W
+  T kappa;   // 3 sigma W / 2
+  T lambda;
+  T lamW;    // lambda / W
+  T xi;
+  T tfac;    // 4 / (1 + 2 xi)^2 : 1 - tanh^2(2 psi / W) = tfac * a * b
+  T fsD[kQ], fhD[kQ];
+  T gsD[kQ], ghD3[kQ];  // ghD3 = ghD / 3 (the source moments carry a 1/3)
+  double vU, vT;        // prescribed vortex amplitude and period
+};
+
+struct Item {
+  int32_t c, x0, y0, nrows;  // case, first column, first row, rows
+};
+
+enum { kModeStep = 0, kModeFields = 1 };
+enum { kFlagNonFinite = 1 };
+
+template <typename T>
+struct StepArgs {
+  Phys<T> ph;
+  const CaseDev<T>* cases;
+  const Item* items;
+  const int64_t* t_base;  // device step counter
+  int64_t t_off;          // this launch is step t_base + t_off
+  int32_t parity;         // source buffer index
+  int32_t pad_;
+  int32_t* flags;         // device error flags (kFlag*)
+  // kModeFields outputs (FP64, [y][x]) for the items of one case
+  double* out_phi;
+  double* out_ux;
+  double* out_uy;
+  double* out_p;
+};
+
+}  // namespace lbmk

@@ -1,0 +1,213 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU oracle
+on the same seeded inputs.
+
+Tolerances:
+  * FP64 path: max |GPU - oracle| <= 1e-12 on populations, phi*u and the
+    macroscopic fields after 100 steps (both sides differ only in rounding
+    order and FMA contraction);
+  * FP32 path: <= 1e-5 on phi after 100 steps; u and p (values ~1e-4..1e-2)
+    to 1e-6 absolute.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32_PHI = 1e-5
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2505_10899_gb300 import build
+    build.build()
+    from paper_2505_10899_gb300 import lbm
+    return lbm
+
+
+def maxdiff(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max())
+
+
+def run_pair(L, case, phi0, u0, nsteps, precision, state=None):
+    o = oracle.Oracle(case, phi0, u0) if state is None else oracle.Oracle(case, state=state)
+    s = L.Sim(case, phi0 if phi0 is not None else np.zeros((case["ny"], case["nx"])),
+              u0, precision=precision)
+    if state is not None:
+        f, g, j, t = state
+        s.set_state(0, f, g, j, t)
+    o.step(nsteps)
+    s.step(nsteps)
+    return o, s
+
+
+def compare_full(o, s, tol_pop, tol_phi, tol_u, tol_p):
+    f, g, j, t = s.get_state(0)
+    assert t == o.t
+    if o.coupled:
+        assert maxdiff(f, o.f) <= tol_pop
+    assert maxdiff(g, o.g) <= tol_pop
+    assert maxdiff(j, o.j) <= tol_pop
+    phi, ux, uy, p = s.fields(0)
+    ophi, oux, ouy, op = o.fields()
+    assert maxdiff(phi, ophi) <= tol_phi
+    assert maxdiff(ux, oux) <= tol_u and maxdiff(uy, ouy) <= tol_u
+    assert maxdiff(p, op) <= tol_p
+    assert s.status() == L_OK
+
+
+L_OK = 0
+
+
+@pytest.mark.parametrize("lam", [0.5, 0.0])
+def test_two_droplets_fp64(L, lam):
+    case, phi0, u0, lab, _ = W.two_droplets(noise=1e-3, lam=lam)
+    o, s = run_pair(L, case, phi0, u0, 100, "f64")
+    compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
+    s.set_regions(0, lab, 2)
+    v = s.volume()
+    assert np.abs(v / o.volume(lab, 2) - 1).max() < 1e-13
+
+
+def test_two_droplets_fp32(L):
+    case, phi0, u0, lab, _ = W.two_droplets(noise=1e-3)
+    o, s = run_pair(L, case, phi0, u0, 100, "f32")
+    phi, ux, uy, p = s.fields(0)
+    ophi, oux, ouy, op = o.fields()
+    assert maxdiff(phi, ophi) <= TOL32_PHI
+    assert maxdiff(ux, oux) <= 1e-6 and maxdiff(uy, ouy) <= 1e-6
+    assert maxdiff(p, op) <= 1e-6
+    s.set_regions(0, lab, 2)
+    assert np.abs(s.volume() / o.volume(lab, 2) - 1).max() < 1e-6
+
+
+def test_variable_density_random_state_fp64(L):
+    # ragged grid (several strips and a partial one), density ratio 10,
+    # unequal viscosities, non-default free rates, random non-equilibrium state
+    case = W.base_case(300, 70, sigma=5e-3, rho_l=10.0, rho_g=1.0, tau_f_l=0.7,
+                       tau_f_g=1.2, s_f=[1.1, 1.3, 0.9, 1.0, 1.2, 1.0, 1.4, 1.0, 1.0],
+                       s_g=[1.0, 1.2, 1.3, 1.0, 0.8, 1.0, 0.9, 1.1, 1.5])
+    f, g, j = W.random_state(300, 70, seed=77)
+    o, s = run_pair(L, case, None, None, 30, "f64", state=(f, g, j, 5))
+    compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
+
+
+def test_translating_droplet_fp64(L):
+    case = W.base_case(96, 80, rho_l=3.0, tau_f_l=0.9, tau_f_g=0.9)
+    phi0 = W.tanh_disc(96, 80, 40.0, 37.0, 15.0, 4.0, periodic=True)
+    phi0 += W.uniform(5, phi0.shape, -1e-3, 1e-3)
+    u0 = np.zeros((2, 80, 96))
+    u0[0], u0[1] = 0.013, -0.008
+    o, s = run_pair(L, case, phi0, u0, 100, "f64")
+    compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (3, 3), (1, 5), (4, 1), (2, 7), (33, 5), (129, 3)])
+def test_degenerate_grids_fp64(L, shape):
+    ny, nx = shape
+    case = W.base_case(nx, ny, sigma=1e-2)
+    f, g, j = W.random_state(nx, ny, seed=nx * 100 + ny)
+    o, s = run_pair(L, case, None, None, 7, "f64", state=(f, g, j, 0))
+    compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
+
+
+def test_vortex_fp64(L):
+    case, phi0, _ = W.single_vortex(n=64, W=3.0, U=0.02, T=256)
+    phi0 = phi0 + W.uniform(9, phi0.shape, -1e-3, 1e-3)
+    o, s = run_pair(L, case, phi0, None, 100, "f64")
+    compare_full(o, s, TOL64, TOL64, TOL64, 0.0)
+
+
+def test_vortex_fp32(L):
+    case, phi0, _ = W.single_vortex(n=64, W=3.0, U=0.02, T=256)
+    o, s = run_pair(L, case, phi0, None, 100, "f32")
+    phi = s.fields(0)[0]
+    assert maxdiff(phi, o.fields()[0]) <= TOL32_PHI
+
+
+def test_graph_replay_and_parity_realignment_fp64(L):
+    # 1 + 64 + 65 + 20 steps: a direct step, a graph replay, a realigning step
+    # plus a replay, and a remainder; must equal 150 oracle steps.
+    case, phi0, u0, _, _ = W.two_droplets(noise=1e-3)
+    o = oracle.Oracle(case, phi0, u0).step(150)
+    s = L.Sim(case, phi0, u0, precision="f64")
+    for n in (1, 64, 65, 20):
+        s.step(n)
+    assert s.t == 150
+    f, g, j, t = s.get_state(0)
+    assert maxdiff(f, o.f) <= TOL64 and maxdiff(g, o.g) <= TOL64
+
+
+def test_batch_of_uneven_cases_fp64(L):
+    specs = [(64, 64, 1.0), (96, 40, 4.0), (37, 51, 10.0)]
+    cases, phis, us, oracles = [], [], [], []
+    for k, (nx, ny, ratio) in enumerate(specs):
+        c = W.base_case(nx, ny, rho_l=ratio, tau_f_l=0.8, tau_f_g=0.8)
+        phi = W.tanh_disc(nx, ny, nx / 2, ny / 2, min(nx, ny) / 4, 4.0, periodic=True)
+        phi += W.uniform(k, phi.shape, -1e-3, 1e-3)
+        u = np.zeros((2, ny, nx))
+        u[0] = 0.01 * (k + 1)
+        cases.append(c), phis.append(phi), us.append(u)
+        oracles.append(oracle.Oracle(c, phi, u).step(40))
+    s = L.Sim(cases, phis, us, precision="f64")
+    s.step(40)
+    for k, o in enumerate(oracles):
+        f, g, j, t = s.get_state(k)
+        assert maxdiff(f, o.f) <= TOL64 and maxdiff(g, o.g) <= TOL64
+        assert maxdiff(j, o.j) <= TOL64
+    v = s.volume()
+    for k, o in enumerate(oracles):
+        assert abs(v[k] / o.volume()[0] - 1) < 1e-13
+
+
+def test_checkpoint_roundtrip_bitwise(L):
+    case, phi0, u0, _, _ = W.two_droplets(noise=1e-3)
+    for prec in ("f32", "f64"):
+        s = L.Sim(case, phi0, u0, precision=prec)
+        s.step(37)
+        blob = s.save()
+        s.step(70)
+        a = s.get_state(0)
+        s.load(blob)
+        assert s.t == 37
+        s.step(70)
+        b = s.get_state(0)
+        for x, y in zip(a[:3], b[:3]):
+            assert np.array_equal(x, y)
+
+
+def test_nonfinite_is_reported(L):
+    case = W.base_case(40, 20)
+    f, g, j = W.random_state(40, 20, seed=3)
+    g[0, 5, 7] = np.nan
+    s = L.Sim(case, np.zeros((20, 40)), None, precision="f32")
+    s.set_state(0, f, g, j, 0)
+    s.step(2)
+    assert s.status() == L.LBM_ERR_NONFINITE
+    assert s.status() == L.LBM_OK  # flags were cleared
+
+
+def test_adjoint_entry_point_is_declared_unimplemented(L):
+    case, phi0, u0, _, _ = W.two_droplets()
+    s = L.Sim(case, phi0, u0, precision="f32")
+    assert L.lbm_adjoint_step(s.h) == L.LBM_ERR_UNIMPLEMENTED
+
+
+def test_zero_steps_and_bad_calls(L):
+    case, phi0, u0, _, _ = W.two_droplets()
+    s = L.Sim(case, phi0, u0, precision="f32")
+    f0 = s.get_state(0)
+    s.step(0)
+    assert all(np.array_equal(a, b) for a, b in zip(f0[:3], s.get_state(0)[:3]))
+    with pytest.raises(L.LbmError):
+        s.step(-1)
+    with pytest.raises(L.LbmError):
+        L.lbm_fields(s.h, 1, (64, 128))   # no case 1: rejected by the ABI
+    with pytest.raises(L.LbmError):
+        s.set_regions(0, None, 9)
