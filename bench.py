@@ -1,0 +1,446 @@
+#!/usr/bin/env python3
+"""Benchmark of the coupled volume-conserving LB step on GB300.
+
+Default workload: 512 independent 2-D droplet cases advanced together, one
+kernel launch per time step over all of them (static and translating droplets,
+square edges drawn from {64, ..., 512}, density ratio 1:1 to 1:10, W = 4,
+FP32 populations, FP64 phase-volume sums fused into the step).  A bench "step"
+is one coupled LB time step of every case: pull-stream, phi/psi, isotropic
+stencils, chemical potential and surface force, hydrodynamic and phase-field
+MRT collisions, phi*u update and the per-case FP64 volume reduction.
+
+metric: MLUPS (million lattice-node updates per second, whole job).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun) every rank advances its own independent batch (weak
+scaling); the only communication is the barrier and the max-time reduction.
+`--impl reference` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+BYTES_PER_NODE = {"f32": 160, "f64": 320}  # f, g read+write, phi*u read+write
+WORKLOAD_NAME = ("batched droplets: 512 independent 2-D cases, square edges from "
+                 "{64,96,128,192,256,384,512}, R in [0.05,0.3]*edge, translation "
+                 "speed in [0,0.02] lu/step, density ratio 1:1..1:10, W=4, "
+                 "coupled D2Q9 MRT phase-field + hydrodynamic LB")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--ncases", type=int, default=512)
+    ap.add_argument("--seed", type=int, default=2026)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def rank_cases(args, rank):
+    """Each rank owns an independent batch (seeded by rank)."""
+    return W.batched_droplets(args.ncases, seed=args.seed + 7919 * rank)
+
+
+def host_inputs(cases):
+    phis, us = [], []
+    for c in cases:
+        phi, u = W.case_fields(c)
+        phis.append(phi)
+        us.append(u)
+    return phis, us
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = tempfile.mktemp(prefix="clocks_", suffix=".csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "power_w_max": float(max(power)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2505_10899_gb300", "csrc")
+    for name in ("lbm_kernels.cuh", "lbm_layout.h", "kern_impl.cuh"):
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_tag, nodes):
+    """DRAM bytes per launch scaled from the committed ncu summary, or None if
+    the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel_tag}.md")
+    if not os.path.exists(path):
+        return None, None
+    txt = open(path).read()
+    m_h = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    m_b = re.search(r"dram_bytes_per_node:\s*([0-9.]+)", txt)
+    if not m_h or not m_b:
+        return None, None
+    if m_h.group(1) != kernel_source_hash():
+        return None, "stale"
+    return float(m_b.group(1)) * nodes, "scaled"
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_2505_10899_gb300 import lbm
+
+    ws, rank, local, pg = dist_setup(args)
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    cases = rank_cases(args, rank)
+    nodes = sum(c["nx"] * c["ny"] for c in cases)
+    phis, us = host_inputs(cases)
+
+    with torch.cuda.stream(stream):
+        sim = lbm.Sim(cases, phis, us, precision=args.precision, stream=stream)
+        vol = sim.track_volume(True)
+        v0 = None
+        sim.step(max(args.warmup, 3))
+        stream.synchronize()
+        v0 = vol.clone()
+
+        # ---------------- timed region ----------------
+        K = args.steps
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        sampler = ClockSampler(local) if rank == 0 else None
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+            time.sleep(0.4)
+        ev[0].record(stream)
+        for k in range(K):
+            sim.step(1)
+            ev[k + 1].record(stream)
+        stream.synchronize()
+        torch.cuda.synchronize(dev)
+        if pg:
+            pg.barrier()
+        clocks = sampler.stop() if sampler else None
+        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
+        total_ms = ev[0].elapsed_time(ev[K])
+        status = sim.status()
+        vend = vol.clone().cpu().numpy()
+        drift = float(np.max(np.abs(vend / v0.cpu().numpy() - 1.0)))
+
+    t_max = total_ms
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = ws * nodes * K / (t_max * 1e-3) / 1e6
+
+    # kernel duration: each per-step event pair brackets the step kernel plus
+    # the volume finalisation and clock kernels (a few microseconds)
+    kms = float(np.mean(step_ms))
+    bpn = BYTES_PER_NODE[args.precision]
+    achieved = bpn * nodes / (kms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    tag = f"coupled_step_{args.precision}_batched512"
+    traffic, traffic_kind = profiled_traffic(tag, nodes)
+
+    result = {
+        "metric": "coupled-step MLUPS",
+        "value": round(value, 1),
+        "unit": "MLUPS",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_max / K, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == "f32" else "f64",
+        "data": "synthetic (seeded tanh droplets; no dataset in the paper)",
+        "config": {"workload": WORKLOAD_NAME, "ncases": len(cases), "nodes_per_gpu": nodes,
+                   "precision": args.precision, "volume_sums": "f64, fused, every step",
+                   "l2": "inputs larger than L2 (%.1f GB of state)" % (
+                       sim.ws_bytes / 1e9),
+                   "parallelism": f"independent batches, {ws} rank(s)",
+                   "tiling": "strip/run work items, one launch per step for all cases"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "traffic_source": traffic_kind,
+                     "kernel": f"step_kernel<{'float' if args.precision == 'f32' else 'double'},"
+                               f"{sim_bx(sim)},coupled>",
+                     "algorithmic_bytes_per_node": bpn, "peak_kind": peak_kind,
+                     "kernel_ms": round(kms, 4)},
+        "clocks": clocks,
+        "gpu_launches": 3 * K,
+        "status": status,
+        "volume_drift_rel": drift,
+    }
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    if rank == 0 and not args.no_e2e:
+        result["e2e"] = run_e2e(args, cases, phis, us, dev, K)
+    if rank == 0 and not args.no_extras:
+        result["extras"] = run_extras(args, cases, dev)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(cases, args.cpu_seconds)
+    if pg:
+        pg.barrier()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def sim_bx(sim):
+    return sim.tiling()[0]
+
+
+def run_e2e(args, cases, phis, us, dev, K):
+    """End to end through the public API: H2D of the initial fields from
+    pinned host memory (lbm_init), K steps, and every step a D2H read of the
+    per-case volumes (the step's result)."""
+    import torch
+    from paper_2505_10899_gb300 import lbm
+
+    stream = torch.cuda.Stream(device=dev)
+    pin_phi = [torch.from_numpy(p).pin_memory() for p in phis]
+    pin_u = [torch.from_numpy(u).pin_memory() for u in us]
+    params = [lbm.make_params(c, args.precision) for c in cases]
+    nbytes = lbm.lbm_workspace_bytes(params)
+    wsbuf = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    ptr = (wsbuf.data_ptr() + 255) // 256 * 256
+    vol_d = torch.zeros(len(cases), dtype=torch.float64, device=dev)
+    vol_h = torch.zeros(len(cases), dtype=torch.float64).pin_memory()
+    h2d = sum(p.numel() * 8 for p in pin_phi) + sum(u.numel() * 8 for u in pin_u)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    h = lbm.lbm_init(params, ptr, nbytes, [p.numpy() for p in pin_phi],
+                     [u.numpy() for u in pin_u], stream.cuda_stream)
+    lbm.lbm_track_volume(h, vol_d.data_ptr())
+    for _ in range(K):
+        lbm.lbm_step(h, 1)
+        with torch.cuda.stream(stream):
+            vol_h.copy_(vol_d, non_blocking=True)
+        stream.synchronize()
+    t1 = time.perf_counter()
+    lbm.lbm_destroy(h)
+    nodes = sum(c["nx"] * c["ny"] for c in cases)
+    return {"value": round(nodes * K / (t1 - t0) / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": int(h2d / K), "d2h_bytes_per_step": len(cases) * 8,
+            "includes": "lbm_init (H2D of phi0, u0 from pinned memory + init kernel), "
+                        "K x (lbm_step + D2H of per-case volumes + sync)"}
+
+
+def run_extras(args, cases, dev):
+    """Secondary numbers: FP64 on a slice of the batch; FP32 vs FP64 phi error."""
+    import torch
+    from paper_2505_10899_gb300 import lbm
+
+    out = {}
+    sub = cases[:64]
+    nodes = sum(c["nx"] * c["ny"] for c in sub)
+    phis, us = host_inputs(sub)
+    for prec in ("f64", "f32"):
+        s = lbm.Sim(sub, phis, us, precision=prec)
+        s.step(3)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n = 20
+        a.record(s.stream)
+        s.step(n)
+        b.record(s.stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        out[f"{prec}_mlups_first64cases"] = round(nodes * n / (ms * 1e-3) / 1e6, 1)
+        s.close()
+    # accuracy: FP32 vs FP64 after 200 steps on case 0
+    c0 = [cases[0]]
+    p0, u0 = host_inputs(c0)
+    res = {}
+    for prec in ("f32", "f64"):
+        s = lbm.Sim(c0, p0, u0, precision=prec)
+        s.step(200)
+        res[prec] = s.fields(0)[0]
+        s.close()
+    out["phi_maxdiff_f32_vs_f64_case0_200steps"] = float(np.abs(res["f32"] - res["f64"]).max())
+    return out
+
+
+def cpu_baseline(cases, seconds):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the same workload: the first cases of the batch, 2 steps each."""
+    import oracle
+
+    oracle.build()
+    steps = 2
+    done_nodes, t_used, used = 0, 0.0, 0
+    for c in cases:
+        phi, u = W.case_fields(c)
+        o = oracle.Oracle(c, phi, u)
+        t0 = time.perf_counter()
+        o.step(steps)
+        t_used += time.perf_counter() - t0
+        done_nodes += c["nx"] * c["ny"]
+        used += 1
+        if t_used > seconds:
+            break
+    return {"value": round(done_nodes * steps / t_used / 1e6, 3), "unit": "MLUPS",
+            "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"first {used} of {len(cases)} cases x {steps} steps "
+                      f"({done_nodes} nodes, {t_used:.1f} s of oracle time)"}
+
+
+def run_reference(args):
+    ws, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        if pg:
+            pg.destroy_process_group()
+        return
+    cases = rank_cases(args, 0)
+    import oracle
+    oracle.build()
+    # each "step" is a bounded sample: the oracle advances a fixed subset of
+    # the batch by one time step
+    budget_nodes = 300_000
+    sub, n = [], 0
+    for c in cases:
+        if n + c["nx"] * c["ny"] > budget_nodes and sub:
+            break
+        sub.append(c)
+        n += c["nx"] * c["ny"]
+    ors = []
+    for c in sub:
+        phi, u = W.case_fields(c)
+        ors.append(oracle.Oracle(c, phi, u))
+    for _ in range(args.warmup):
+        for o in ors:
+            o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for o in ors:
+            o.step(1)
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt / 1e6
+    res = {"impl": "reference", "metric": "coupled-step MLUPS", "value": round(value, 3),
+           "unit": "MLUPS", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded tanh droplets)",
+           "config": {"workload": WORKLOAD_NAME, "ncases": len(cases)},
+           "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS",
+                            "cores": oracle.num_threads(), "kind": "oracle",
+                            "sample": f"first {len(sub)} cases ({n} nodes) per step"},
+           "e2e": {"value": round(value, 3), "unit": "MLUPS",
+                   "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -138,6 +138,24 @@ int lbm_volume(lbm_handle* h, double* h_out);
  * without synchronising. */
 int lbm_volume_async(lbm_handle* h, double* d_out);
 
+/* Fused volume tracking.  With d_out non-NULL, every following step also
+ * reduces phi (Eq. 35, the state entering the step) over each case in FP64
+ * inside the step kernel and writes the per-case totals to d_out[ncases]
+ * (device memory, overwritten every step, so after lbm_step(n) it holds the
+ * volumes at time t+n-1).  Only for batches whose cases all have one region
+ * (no labels): LBM_ERR_ARG otherwise.  d_out = NULL switches tracking off. */
+int lbm_track_volume(lbm_handle* h, double* d_out);
+
+/* Work tiling of the step kernel: each CTA owns a strip of bx columns
+ * (bx in {32, 64, 128}) and marches down runs of `rows` rows (2..1024).
+ * lbm_init picks a default from the batch size; lbm_set_tiling replaces it
+ * (results are identical for every tiling, only speed changes; the step
+ * order of floating-point operations per node does not depend on it).
+ * lbm_get_tiling also reports the number of CTAs (work items) per step. */
+int lbm_get_tiling(const lbm_handle* h, int32_t* bx, int32_t* rows,
+                   int32_t* n_items);
+int lbm_set_tiling(lbm_handle* h, int32_t bx, int32_t rows);
+
 /* Total number of volume regions over all cases. */
 int32_t lbm_num_regions(const lbm_handle* h);
 

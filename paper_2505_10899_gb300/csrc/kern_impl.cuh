@@ -97,4 +97,12 @@ cudaError_t launch_volume<LBM_T>(const CaseDev<LBM_T>* cases, int ncases,
   return cudaGetLastError();
 }
 
+template <>
+cudaError_t launch_volume_final<LBM_T>(const CaseDev<LBM_T>* cases, int ncases,
+                                       const double* part, double* out, cudaStream_t s) {
+  const int warps = 4;
+  volume_final<LBM_T><<<(ncases + warps - 1) / warps, 32 * warps, 0, s>>>(cases, ncases, part, out);
+  return cudaGetLastError();
+}
+
 }  // namespace lbmk

@@ -37,6 +37,11 @@ cudaError_t launch_volume(const CaseDev<T>* cases, int ncases,
                           const Item* items, int n_items, int bx, int parity,
                           double* part, double* out, cudaStream_t s);
 
+// Per-case sums of the partials written by the step kernel (vol_part).
+template <typename T>
+cudaError_t launch_volume_final(const CaseDev<T>* cases, int ncases, const double* part,
+                                double* out, cudaStream_t s);
+
 cudaError_t launch_clock(int64_t* t, int64_t n, cudaStream_t s);
 
 }  // namespace lbmk

@@ -2,6 +2,7 @@
 // workspace carving, work-item tiling, CUDA-graph replay of the step loop,
 // state import/export, checkpointing and error reporting.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,6 +81,7 @@ struct lbm_handle {
   std::vector<CaseDev<double>> cd;
   cudaGraphExec_t gexec = nullptr;
   int graph_parity = -1;
+  double* track = nullptr;  // fused volume output (device), or null
   // device pointers
   int32_t* flags = nullptr;
   int64_t* t_dev = nullptr;
@@ -181,6 +183,14 @@ Tiling choose_tiling(const lbm_params* c, int n) {
     t.bx /= 2;
   }
   return t;
+}
+
+// Work items of the finest tiling (bx = 32, rows = 2): the workspace holds
+// item and partial-sum tables of this size so that any tiling fits.
+int max_items(const lbm_params* c, int n) {
+  int64_t m = 0;
+  for (int k = 0; k < n; ++k) m += (int64_t)((c[k].nx + 31) / 32) * ((c[k].ny + 1) / 2);
+  return (int)std::min<int64_t>(m, INT32_MAX);
 }
 
 Layout make_layout(const lbm_params* c, int n, int n_items, int total_regions) {
@@ -340,12 +350,21 @@ int enqueue_steps(lbm_handle* h, cudaStream_t s, int parity, int count) {
   for (int j = 0; j < count; ++j) {
     const int par = (parity + j) & 1;
     cudaError_t e;
-    if (h->precision == LBM_F32)
-      e = lbmk::launch_step<float>(step_args<float>(h, par, j), h->tile.bx, coupled,
-                                   lbmk::kModeStep, n, s);
-    else
-      e = lbmk::launch_step<double>(step_args<double>(h, par, j), h->tile.bx, coupled,
-                                    lbmk::kModeStep, n, s);
+    if (h->precision == LBM_F32) {
+      StepArgs<float> a = step_args<float>(h, par, j);
+      a.vol_part = h->track ? h->part : nullptr;
+      e = lbmk::launch_step<float>(a, h->tile.bx, coupled, lbmk::kModeStep, n, s);
+      if (e == cudaSuccess && h->track)
+        e = lbmk::launch_volume_final<float>((const CaseDev<float>*)h->cases_dev, h->ncases,
+                                             h->part, h->track, s);
+    } else {
+      StepArgs<double> a = step_args<double>(h, par, j);
+      a.vol_part = h->track ? h->part : nullptr;
+      e = lbmk::launch_step<double>(a, h->tile.bx, coupled, lbmk::kModeStep, n, s);
+      if (e == cudaSuccess && h->track)
+        e = lbmk::launch_volume_final<double>((const CaseDev<double>*)h->cases_dev, h->ncases,
+                                              h->part, h->track, s);
+    }
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
   }
   LBM_CUDA(lbmk::launch_clock(h->t_dev, count, s));
@@ -519,10 +538,7 @@ const char* lbm_status_string(int s) {
 
 size_t lbm_workspace_bytes(const lbm_params* cases, int32_t ncases) {
   if (check_params(cases, ncases) != LBM_OK) return 0;
-  Tiling t = choose_tiling(cases, ncases);
-  std::vector<int> b, e;
-  std::vector<Item> it = make_items(cases, ncases, t, &b, &e);
-  return make_layout(cases, ncases, (int)it.size(), ncases * lbmk::kMaxRegions).total;
+  return make_layout(cases, ncases, max_items(cases, ncases), ncases * lbmk::kMaxRegions).total;
 }
 
 int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t ws_bytes,
@@ -550,7 +566,7 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   h->vol_base.resize(ncases);
   for (int k = 0; k < ncases; ++k) h->vol_base[k] = k;
   h->total_regions = ncases;
-  h->L = make_layout(cases, ncases, (int)h->items.size(), ncases * lbmk::kMaxRegions);
+  h->L = make_layout(cases, ncases, max_items(cases, ncases), ncases * lbmk::kMaxRegions);
   if (ws_bytes < h->L.total) {
     delete h;
     return fail(LBM_ERR_WORKSPACE, "workspace too small: need " + std::to_string(h->L.total));
@@ -649,6 +665,8 @@ int lbm_set_regions(lbm_handle* h, int32_t c, const int8_t* h_labels, int32_t nr
   if (rc) return rc;
   if (nregions < 1 || nregions > lbmk::kMaxRegions)
     return fail(LBM_ERR_ARG, "nregions must lie in [1, 8]");
+  if (h->track && (h_labels || nregions != 1))
+    return fail(LBM_ERR_ARG, "switch volume tracking off before declaring labelled regions");
   const int64_t n = (int64_t)h->params[c].nx * h->params[c].ny;
   const int8_t* dlab = nullptr;
   if (h_labels) {
@@ -671,6 +689,49 @@ int lbm_set_regions(lbm_handle* h, int32_t c, const int8_t* h_labels, int32_t nr
 }
 
 int32_t lbm_num_regions(const lbm_handle* h) { return h ? h->total_regions : 0; }
+
+int lbm_get_tiling(const lbm_handle* h, int32_t* bx, int32_t* rows, int32_t* n_items) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (bx) *bx = h->tile.bx;
+  if (rows) *rows = h->tile.rows;
+  if (n_items) *n_items = (int32_t)h->items.size();
+  return LBM_OK;
+}
+
+int lbm_set_tiling(lbm_handle* h, int32_t bx, int32_t rows) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (!lbmk::valid_bx(bx) || rows < 2 || rows > 1024)
+    return fail(LBM_ERR_ARG, "bx must be 32, 64 or 128 and rows in [2, 1024]");
+  Tiling t;
+  t.bx = bx;
+  t.rows = rows;
+  std::vector<int> b, e;
+  std::vector<Item> it = make_items(h->params.data(), h->ncases, t, &b, &e);
+  if ((int64_t)it.size() > max_items(h->params.data(), h->ncases))
+    return fail(LBM_ERR_ARG, "tiling needs more work items than the workspace holds");
+  // the previous step's kernels may still read the item table
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  h->tile = t;
+  h->items.swap(it);
+  h->item_begin.swap(b);
+  h->item_end.swap(e);
+  LBM_CUDA(cudaMemcpyAsync(h->items_dev, h->items.data(), h->items.size() * sizeof(Item),
+                           cudaMemcpyHostToDevice, h->stream));
+  drop_graph(h);
+  return upload_cases(h);
+}
+
+int lbm_track_volume(lbm_handle* h, double* d_out) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (d_out)
+    for (int k = 0; k < h->ncases; ++k)
+      if (h->nregions[k] != 1 ||
+          (h->precision == LBM_F32 ? h->cf[k].labels != nullptr : h->cd[k].labels != nullptr))
+        return fail(LBM_ERR_ARG, "volume tracking needs one unlabelled region per case");
+  if (d_out != h->track) drop_graph(h);
+  h->track = d_out;
+  return LBM_OK;
+}
 
 int lbm_volume_async(lbm_handle* h, double* d_out) {
   if (!h || !d_out) return fail(LBM_ERR_ARG, "null argument");

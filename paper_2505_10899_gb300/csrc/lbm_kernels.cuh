@@ -155,6 +155,7 @@ struct VortexCol {
 template <typename T, int BX, bool COUPLED, int MODE>
 __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
   __shared__ Ring<T, BX> ring;
+  __shared__ double vred[BX / 32];
 
   const Item it = a.items[blockIdx.x];
   const CaseDev<T>* __restrict__ cdp = a.cases + it.c;
@@ -191,6 +192,9 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
 
   const Phys<T>& ph = a.ph;
   const T xi = ph.xi;
+  // fused phase volume of the case (one region: the whole grid)
+  const bool do_vol = (MODE == kModeStep) && (a.vol_part != nullptr);
+  double vacc = 0.0;
 
   // case constants
   const T rho_g = cdp->rho_g, drho = cdp->drho;
@@ -294,6 +298,7 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
       const int lc = tid + 1;
       const int sm = (k + 3) & 3, s0 = k & 3, sp = (k + 1) & 3;
       const T phi = ring.phi[s0][lc];  // = sum of Gc (Eq. 35)
+      if (do_vol) vacc += (double)phi;
       const T pE = ring.phi[s0][lc + 1], pW = ring.phi[s0][lc - 1];
       const T pN = ring.phi[sp][lc], pS = ring.phi[sm][lc];
       const T pNE = ring.phi[sp][lc + 1], pNW = ring.phi[sp][lc - 1];
@@ -423,6 +428,17 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
     stage(k, Fc, Gc, Fq, Gq);
     if (k + 1 < nrows) stage(k + 1, Fn, Gn, Fc, Gc);
     if (k + 2 < nrows) stage(k + 2, Fq, Gq, Fn, Gn);
+  }
+
+  if (do_vol) {  // deterministic CTA reduction: warp shuffles, then warps in order
+    for (int o = 16; o > 0; o >>= 1) vacc += __shfl_down_sync(0xffffffffu, vacc, o);
+    if ((tid & 31) == 0) vred[tid >> 5] = vacc;
+    __syncthreads();
+    if (tid == 0) {
+      double v = 0.0;
+      for (int w = 0; w < BX / 32; ++w) v += vred[w];
+      a.vol_part[(int64_t)blockIdx.x * kMaxRegions] = v;
+    }
   }
 }
 

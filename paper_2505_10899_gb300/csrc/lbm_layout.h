@@ -64,6 +64,9 @@ struct StepArgs {
   int32_t parity;         // source buffer index
   int32_t pad_;
   int32_t* flags;         // device error flags (kFlag*)
+  // kModeStep: if non-null, each CTA writes the FP64 sum of the phi it
+  // collided (the pre-collision phi of Eq. 35) to vol_part[blockIdx.x * 8]
+  double* vol_part;
   // kModeFields outputs (FP64, [y][x]) for the items of one case
   double* out_phi;
   double* out_ux;

@@ -67,6 +67,10 @@ def _load():
         "lbm_volume": ([_H, _D], ctypes.c_int),
         "lbm_volume_async": ([_H, _VP], ctypes.c_int),
         "lbm_num_regions": ([_H], ctypes.c_int32),
+        "lbm_track_volume": ([_H, _VP], ctypes.c_int),
+        "lbm_get_tiling": ([_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "lbm_set_tiling": ([_H, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "lbm_fields": ([_H, ctypes.c_int32, _D, _D, _D, _D], ctypes.c_int),
         "lbm_get_state": ([_H, ctypes.c_int32, _D, _D, _D, ctypes.POINTER(ctypes.c_int64)],
                           ctypes.c_int),
@@ -165,6 +169,22 @@ def lbm_set_regions(h, c: int, labels, nregions: int):
         labels = np.ascontiguousarray(labels, dtype=np.int8)
         lp = labels.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
     return _check(_lib.lbm_set_regions(h, int(c), lp, int(nregions)), "lbm_set_regions")
+
+
+def lbm_track_volume(h, d_out: int):
+    return _check(_lib.lbm_track_volume(h, ctypes.c_void_p(d_out) if d_out else None),
+                  "lbm_track_volume")
+
+
+def lbm_get_tiling(h):
+    bx, rows, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.lbm_get_tiling(h, ctypes.byref(bx), ctypes.byref(rows), ctypes.byref(n)),
+           "lbm_get_tiling")
+    return int(bx.value), int(rows.value), int(n.value)
+
+
+def lbm_set_tiling(h, bx: int, rows: int):
+    return _check(_lib.lbm_set_tiling(h, int(bx), int(rows)), "lbm_set_tiling")
 
 
 def lbm_num_regions(h) -> int:
@@ -282,6 +302,23 @@ class Sim:
 
     def volume(self):
         return lbm_volume(self.h)
+
+    def tiling(self):
+        return lbm_get_tiling(self.h)
+
+    def set_tiling(self, bx, rows):
+        lbm_set_tiling(self.h, bx, rows)
+
+    def track_volume(self, enable=True):
+        """Fused per-step volumes into a device tensor (one FP64 per case)."""
+        import torch
+        if enable:
+            self.vol_track = torch.zeros(len(self.cases), dtype=torch.float64, device=self.device)
+            lbm_track_volume(self.h, self.vol_track.data_ptr())
+            return self.vol_track
+        lbm_track_volume(self.h, 0)
+        self.vol_track = None
+        return None
 
     def fields(self, c=0):
         return lbm_fields(self.h, c, self.shape(c))

@@ -211,3 +211,47 @@ def test_zero_steps_and_bad_calls(L):
         L.lbm_fields(s.h, 1, (64, 128))   # no case 1: rejected by the ABI
     with pytest.raises(L.LbmError):
         s.set_regions(0, None, 9)
+
+
+def test_tiling_does_not_change_results(L):
+    # per-node arithmetic is independent of the work tiling: bitwise equal
+    case = W.base_case(200, 90, rho_l=5.0, tau_f_l=0.7, tau_f_g=1.1)
+    phi0 = W.tanh_disc(200, 90, 90.0, 40.0, 25.0, 4.0, periodic=True)
+    u0 = np.zeros((2, 90, 200))
+    u0[0] = 0.01
+    ref = None
+    for bx, rows in [(32, 2), (64, 17), (128, 64), (128, 3)]:
+        for prec in ("f32",):
+            s = L.Sim(case, phi0, u0, precision=prec)
+            s.set_tiling(bx, rows)
+            assert s.tiling()[:2] == (bx, rows)
+            s.step(33)
+            st = s.get_state(0)
+            if ref is None:
+                ref = st
+            else:
+                for x, y in zip(ref[:3], st[:3]):
+                    assert np.array_equal(x, y)
+    with pytest.raises(L.LbmError):
+        s.set_tiling(48, 8)
+
+
+def test_fused_volume_tracking(L):
+    import torch
+    cases = [W.base_case(64, 48), W.base_case(100, 30, rho_l=3.0)]
+    phis = [W.tanh_disc(64, 48, 30, 20, 10, 4.0, True), W.tanh_disc(100, 30, 50, 15, 8, 4.0, True)]
+    s = L.Sim(cases, phis, None, precision="f64")
+    vol = s.track_volume(True)
+    s.step(10)
+    torch.cuda.synchronize()
+    # tracked value = volume of the state entering the last step (t = 9)
+    s2 = L.Sim(cases, phis, None, precision="f64")
+    s2.step(9)
+    ref = s2.volume()
+    assert np.array_equal(vol.cpu().numpy(), ref) or np.abs(vol.cpu().numpy() / ref - 1).max() < 1e-14
+    with pytest.raises(L.LbmError):
+        s.set_regions(0, np.zeros((48, 64), np.int8), 2)
+    s.track_volume(False)
+    s.set_regions(0, np.zeros((48, 64), np.int8), 2)
+    with pytest.raises(L.LbmError):
+        s.track_volume(True)
