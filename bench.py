@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register, 2 bulk-copy")
+    ap.add_argument("--tiling", type=str, default=None, help="BX,ROWS (default: library choice)")
     return ap.parse_args()
 
 
@@ -192,6 +194,10 @@ def run_ours(args):
 
     with torch.cuda.stream(stream):
         sim = lbm.Sim(cases, phis, us, precision=args.precision, stream=stream)
+        sim.set_kernel(args.kernel)
+        if args.tiling:
+            bx, rows = (int(v) for v in args.tiling.split(","))
+            sim.set_tiling(bx, rows)
         vol = sim.track_volume(True)
         v0 = None
         sim.step(max(args.warmup, 3))
@@ -261,8 +267,11 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "traffic_source": traffic_kind,
-                     "kernel": f"step_kernel<{'float' if args.precision == 'f32' else 'double'},"
+                     "kernel": ("step_kernel_tma" if sim.kernel() == 2 else "step_kernel")
+                               + f"<{'float' if args.precision == 'f32' else 'double'},"
                                f"{sim_bx(sim)},coupled>",
+                     "tiling": {"bx": sim.tiling()[0], "rows": sim.tiling()[1],
+                                "ctas": sim.tiling()[2]},
                      "algorithmic_bytes_per_node": bpn, "peak_kind": peak_kind,
                      "kernel_ms": round(kms, 4)},
         "clocks": clocks,

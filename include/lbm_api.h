@@ -156,6 +156,13 @@ int lbm_get_tiling(const lbm_handle* h, int32_t* bx, int32_t* rows,
                    int32_t* n_items);
 int lbm_set_tiling(lbm_handle* h, int32_t bx, int32_t rows);
 
+/* Step-kernel variant: 0 = automatic, 1 = register-pipelined loads (any
+ * grid), 2 = bulk-copy (TMA) staged loads through shared memory (needs every
+ * case to have nx >= 4 and nx a multiple of 4 in FP32, of 2 in FP64).  Both
+ * give identical results.  lbm_get_kernel returns the variant in use (1 or 2). */
+int lbm_set_kernel(lbm_handle* h, int32_t variant);
+int32_t lbm_get_kernel(const lbm_handle* h);
+
 /* Total number of volume regions over all cases. */
 int32_t lbm_num_regions(const lbm_handle* h);
 

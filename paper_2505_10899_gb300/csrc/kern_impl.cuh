@@ -1,8 +1,11 @@
 // Explicit instantiation of the launch wrappers for precision LBM_T.
 // Included by kern_f32.cu (LBM_T = float) and kern_f64.cu (LBM_T = double).
+#include <type_traits>
+
 #include "launch.h"
 #include "lbm_aux.cuh"
 #include "lbm_kernels.cuh"
+#include "lbm_kernels_tma.cuh"
 
 namespace lbmk {
 
@@ -13,8 +16,42 @@ inline int grid_for(int64_t n, int threads) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// pipeline depth of the TMA kernel: 4 stages in FP32, 3 in FP64 (smem)
+constexpr int kStages = sizeof(LBM_T) == 4 ? 4 : 3;
+
+template <int BX, bool COUPLED, int MODE>
+cudaError_t step_tma(const StepArgs<LBM_T>& a, int n, cudaStream_t s) {
+  using SH = TmaShape<LBM_T, BX, COUPLED, MODE, kStages>;
+  step_kernel_tma<LBM_T, BX, COUPLED, MODE, kStages><<<n, BX, SH::SMEM_BYTES, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <int BX, bool COUPLED, int MODE>
+cudaError_t prep_one() {
+  using SH = TmaShape<LBM_T, BX, COUPLED, MODE, kStages>;
+  return cudaFuncSetAttribute(step_kernel_tma<LBM_T, BX, COUPLED, MODE, kStages>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::SMEM_BYTES);
+}
+
 template <int BX>
-cudaError_t step_bx(const StepArgs<LBM_T>& a, bool coupled, int mode, int n, cudaStream_t s) {
+cudaError_t prep_bx() {
+  cudaError_t e;
+  if ((e = prep_one<BX, true, kModeStep>()) != cudaSuccess) return e;
+  if ((e = prep_one<BX, true, kModeFields>()) != cudaSuccess) return e;
+  if ((e = prep_one<BX, false, kModeStep>()) != cudaSuccess) return e;
+  return prep_one<BX, false, kModeFields>();
+}
+
+template <int BX>
+cudaError_t step_bx(const StepArgs<LBM_T>& a, bool coupled, int mode, bool tma, int n,
+                    cudaStream_t s) {
+  if (tma) {
+    if (coupled)
+      return mode == kModeStep ? step_tma<BX, true, kModeStep>(a, n, s)
+                               : step_tma<BX, true, kModeFields>(a, n, s);
+    return mode == kModeStep ? step_tma<BX, false, kModeStep>(a, n, s)
+                             : step_tma<BX, false, kModeFields>(a, n, s);
+  }
   if (coupled) {
     if (mode == kModeStep)
       step_kernel<LBM_T, BX, true, kModeStep><<<n, BX, 0, s>>>(a);
@@ -31,14 +68,40 @@ cudaError_t step_bx(const StepArgs<LBM_T>& a, bool coupled, int mode, int n, cud
 }  // namespace
 
 template <>
-cudaError_t launch_step<LBM_T>(const StepArgs<LBM_T>& a, int bx, bool coupled,
-                               int mode, int n_items, cudaStream_t s) {
+cudaError_t launch_step<LBM_T>(const StepArgs<LBM_T>& a, int bx, bool coupled, int mode,
+                               bool tma, int n_items, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   switch (bx) {
-    case 32: return step_bx<32>(a, coupled, mode, n_items, s);
-    case 64: return step_bx<64>(a, coupled, mode, n_items, s);
-    case 128: return step_bx<128>(a, coupled, mode, n_items, s);
+    case 32: return step_bx<32>(a, coupled, mode, tma, n_items, s);
+    case 64: return step_bx<64>(a, coupled, mode, tma, n_items, s);
+    case 128: return step_bx<128>(a, coupled, mode, tma, n_items, s);
     default: return cudaErrorInvalidValue;
+  }
+}
+
+template <>
+cudaError_t prepare_tma<LBM_T>() {
+  cudaError_t e;
+  if ((e = prep_bx<32>()) != cudaSuccess) return e;
+  if ((e = prep_bx<64>()) != cudaSuccess) return e;
+  return prep_bx<128>();
+}
+
+template <>
+size_t tma_smem_bytes<LBM_T>(int bx, bool coupled, int mode) {
+  auto pick = [&](auto bxc) -> size_t {
+    constexpr int B = decltype(bxc)::value;
+    if (coupled)
+      return mode == kModeStep ? TmaShape<LBM_T, B, true, kModeStep, kStages>::SMEM_BYTES
+                               : TmaShape<LBM_T, B, true, kModeFields, kStages>::SMEM_BYTES;
+    return mode == kModeStep ? TmaShape<LBM_T, B, false, kModeStep, kStages>::SMEM_BYTES
+                             : TmaShape<LBM_T, B, false, kModeFields, kStages>::SMEM_BYTES;
+  };
+  switch (bx) {
+    case 32: return pick(std::integral_constant<int, 32>{});
+    case 64: return pick(std::integral_constant<int, 64>{});
+    case 128: return pick(std::integral_constant<int, 128>{});
+    default: return 0;
   }
 }
 

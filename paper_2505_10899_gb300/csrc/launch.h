@@ -11,9 +11,20 @@ namespace lbmk {
 // Supported strip widths (threads per CTA of the step kernel).
 inline bool valid_bx(int bx) { return bx == 32 || bx == 64 || bx == 128; }
 
+// tma: use the bulk-copy staged kernel (every case must have nx a multiple
+// of 16 bytes of T and nx >= 4), else the register-pipelined kernel.
 template <typename T>
-cudaError_t launch_step(const StepArgs<T>& a, int bx, bool coupled, int mode,
+cudaError_t launch_step(const StepArgs<T>& a, int bx, bool coupled, int mode, bool tma,
                         int n_items, cudaStream_t s);
+
+// Allow the dynamic shared memory of every TMA kernel variant on the current
+// device (call once per device before the first launch or graph capture).
+template <typename T>
+cudaError_t prepare_tma();
+
+// Dynamic shared memory of the TMA kernel variant (0 if not available).
+template <typename T>
+size_t tma_smem_bytes(int bx, bool coupled, int mode);
 
 template <typename T>
 cudaError_t launch_init(const CaseDev<T>& cd, double beta4, double kappa,

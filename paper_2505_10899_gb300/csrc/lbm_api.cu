@@ -82,6 +82,8 @@ struct lbm_handle {
   cudaGraphExec_t gexec = nullptr;
   int graph_parity = -1;
   double* track = nullptr;  // fused volume output (device), or null
+  bool tma_ok = false;      // every case allows the bulk-copy kernel
+  int kernel = 0;           // 0 auto, 1 register-pipelined, 2 bulk-copy staged
   // device pointers
   int32_t* flags = nullptr;
   int64_t* t_dev = nullptr;
@@ -109,7 +111,8 @@ int check_params(const lbm_params* c, int n) {
     if (p.abi_version != LBM_ABI_VERSION) return bad("abi_version mismatch");
     if (p.nx < 1 || p.ny < 1 || p.nx > (1 << 20) || p.ny > (1 << 20))
       return bad("nx, ny must lie in [1, 2^20]");
-    if ((int64_t)p.nx * p.ny > (int64_t(1) << 34)) return bad("grid too large");
+    // kernels address a 9-plane buffer with 32-bit element offsets
+    if ((int64_t)p.nx * p.ny > 230000000) return bad("grid too large (at most 2.3e8 nodes)");
     if (p.precision != LBM_F64 && p.precision != LBM_F32) return bad("precision");
     if (p.flow != LBM_FLOW_COUPLED && p.flow != LBM_FLOW_VORTEX) return bad("flow");
     if (!(p.W > 0) || !std::isfinite(p.W)) return bad("W must be > 0");
@@ -329,6 +332,10 @@ int upload_cases(lbm_handle* h) {
   return LBM_OK;
 }
 
+bool use_tma(const lbm_handle* h) {
+  return h->kernel == 2 || (h->kernel == 0 && h->tma_ok);
+}
+
 template <typename T>
 StepArgs<T> step_args(const lbm_handle* h, int parity, int64_t t_off) {
   StepArgs<T> a{};
@@ -353,14 +360,14 @@ int enqueue_steps(lbm_handle* h, cudaStream_t s, int parity, int count) {
     if (h->precision == LBM_F32) {
       StepArgs<float> a = step_args<float>(h, par, j);
       a.vol_part = h->track ? h->part : nullptr;
-      e = lbmk::launch_step<float>(a, h->tile.bx, coupled, lbmk::kModeStep, n, s);
+      e = lbmk::launch_step<float>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), n, s);
       if (e == cudaSuccess && h->track)
         e = lbmk::launch_volume_final<float>((const CaseDev<float>*)h->cases_dev, h->ncases,
                                              h->part, h->track, s);
     } else {
       StepArgs<double> a = step_args<double>(h, par, j);
       a.vol_part = h->track ? h->part : nullptr;
-      e = lbmk::launch_step<double>(a, h->tile.bx, coupled, lbmk::kModeStep, n, s);
+      e = lbmk::launch_step<double>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), n, s);
       if (e == cudaSuccess && h->track)
         e = lbmk::launch_volume_final<double>((const CaseDev<double>*)h->cases_dev, h->ncases,
                                               h->part, h->track, s);
@@ -408,6 +415,7 @@ int read_flags(lbm_handle* h) {
   int32_t fl = 0;
   LBM_CUDA(cudaMemcpyAsync(&fl, h->flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (fl & lbmk::kFlagTimeout) return fail(LBM_ERR_TIMEOUT, "a bounded device wait timed out");
   if (fl & lbmk::kFlagNonFinite) return fail(LBM_ERR_NONFINITE, "non-finite macroscopic field");
   return LBM_OK;
 }
@@ -423,8 +431,8 @@ int do_fields(lbm_handle* h, int c, double* phi, double* ux, double* uy, double*
   a.out_uy = st + 2 * n;
   a.out_p = st + 3 * n;
   cudaError_t e = lbmk::launch_step<T>(a, h->tile.bx, h->flow == LBM_FLOW_COUPLED,
-                                       lbmk::kModeFields, h->item_end[c] - h->item_begin[c],
-                                       h->stream);
+                                       lbmk::kModeFields, use_tma(h),
+                                       h->item_end[c] - h->item_begin[c], h->stream);
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("fields: ") + cudaGetErrorString(e));
   double* outs[4] = {phi, ux, uy, p};
   for (int q = 0; q < 4; ++q)
@@ -582,6 +590,12 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   h->staging = (double*)(h->ws + h->L.staging);
   h->pf = make_phys<float>(cases[0]);
   h->pd = make_phys<double>(cases[0]);
+  {
+    const int vec = h->precision == LBM_F32 ? 4 : 2;  // elements per 16 bytes
+    h->tma_ok = true;
+    for (int k = 0; k < ncases; ++k)
+      if (cases[k].nx % vec != 0 || cases[k].nx < 4) h->tma_ok = false;
+  }
 
   auto cleanup = [&](int code) {
     lbm_destroy(h);
@@ -589,6 +603,11 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   };
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(fail(LBM_ERR_CUDA, "cannot create capture stream"));
+  {
+    cudaError_t e = h->precision == LBM_F32 ? lbmk::prepare_tma<float>() : lbmk::prepare_tma<double>();
+    if (e != cudaSuccess)
+      return cleanup(fail(LBM_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e)));
+  }
   if (cudaMemsetAsync(h->ws + h->L.hdr, 0, 64, h->stream) != cudaSuccess ||
       cudaMemcpyAsync(h->items_dev, h->items.data(), h->items.size() * sizeof(Item),
                       cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
@@ -689,6 +708,21 @@ int lbm_set_regions(lbm_handle* h, int32_t c, const int8_t* h_labels, int32_t nr
 }
 
 int32_t lbm_num_regions(const lbm_handle* h) { return h ? h->total_regions : 0; }
+
+int lbm_set_kernel(lbm_handle* h, int32_t variant) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (variant < 0 || variant > 2) return fail(LBM_ERR_ARG, "kernel variant must be 0, 1 or 2");
+  if (variant == 2 && !h->tma_ok)
+    return fail(LBM_ERR_ARG, "bulk-copy kernel needs nx a multiple of 16 bytes and nx >= 4");
+  if (variant != h->kernel) drop_graph(h);
+  h->kernel = variant;
+  return LBM_OK;
+}
+
+int32_t lbm_get_kernel(const lbm_handle* h) {
+  if (!h) return -1;
+  return use_tma(h) ? 2 : 1;
+}
 
 int lbm_get_tiling(const lbm_handle* h, int32_t* bx, int32_t* rows, int32_t* n_items) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");

@@ -1,0 +1,241 @@
+// TMA-staged step kernel (grids whose width nx is a multiple of 16 bytes of
+// the working type and at least 4).
+//
+// Work decomposition is that of step_kernel (a CTA owns a strip of BX
+// columns and marches down `nrows` rows), but the populations reach shared
+// memory through the bulk-copy engine instead of registers: for every row
+// the CTA needs, lanes of warp 0 issue one cp.async.bulk per population plane
+// for the pulled source row (r - c_iy) over columns [x0-4, x0+wact+4) (the
+// periodic wrap in x splits a segment into at most three 16-byte aligned
+// pieces) and two for phi*u of the previous step.  Completion is tracked by
+// one mbarrier per stage with its transaction byte count.  S stages form a
+// ring; rows are fetched S-1 ahead of the collision, so the consumer threads
+// never wait on DRAM latency.  The halo columns of the phi/psi ring come from
+// the same staged segments, without extra global loads.
+//
+// Every mbarrier wait is bounded (kWaitCycles); on expiry the CTA raises
+// kFlagTimeout, waits (bounded) for its own copies in flight and returns.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "lbm_layout.h"
+#include "lbm_node.cuh"
+#include "lbm_tma.cuh"
+
+namespace lbmk {
+
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// D2Q9 velocity components (Eq. 19) as compile-time functions of i.
+__host__ __device__ constexpr int cx_of(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy_of(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+
+template <typename T, int BX, bool COUPLED, int MODE, int S>
+struct TmaShape {
+  static constexpr int SEG = BX + 8;                 // staged columns per plane
+  static constexpr int NPL = COUPLED ? 18 : 9;        // population planes
+  static constexpr int NJ = (MODE == kModeStep) ? 2 : 0;  // phi*u planes
+  static constexpr int STAGE = NPL * SEG + NJ * BX;   // elements per stage
+  static constexpr size_t STAGE_BYTES = (size_t)STAGE * sizeof(T);
+  static constexpr size_t BAR_OFF = S * STAGE_BYTES;
+  static constexpr size_t RING_OFF = (BAR_OFF + S * 8 + 127) / 128 * 128;
+  static constexpr size_t VRED_OFF = RING_OFF + sizeof(Ring<T, BX>);
+  static constexpr size_t SMEM_BYTES = VRED_OFF + (BX / 32) * sizeof(double);
+  static_assert(STAGE_BYTES % 16 == 0, "stage must keep 16-byte alignment");
+  static_assert((SEG * sizeof(T)) % 16 == 0, "plane segment must keep 16-byte alignment");
+};
+
+template <typename T, int BX, bool COUPLED, int MODE, int S>
+__global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
+  using SH = TmaShape<T, BX, COUPLED, MODE, S>;
+  constexpr int SEG = SH::SEG, NPL = SH::NPL, NJ = SH::NJ, STAGE = SH::STAGE;
+  extern __shared__ __align__(128) unsigned char smem[];
+  T* const stages = reinterpret_cast<T*>(smem);
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(smem + SH::BAR_OFF);
+  Ring<T, BX>& ring = *reinterpret_cast<Ring<T, BX>*>(smem + SH::RING_OFF);
+  double* const vred = reinterpret_cast<double*>(smem + SH::VRED_OFF);
+
+  const Item it = a.items[blockIdx.x];
+  const CaseDev<T>* __restrict__ cdp = a.cases + it.c;
+  const int nx = cdp->nx, ny = cdp->ny;
+  const uint32_t P = (uint32_t)cdp->plane;
+  const int x0 = it.x0, y0 = it.y0, nrows = it.nrows;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wact = min(BX, nx - x0);
+  const bool act = tid < wact;
+  const int xc = act ? x0 + tid : x0;
+
+  const T* __restrict__ gs = cdp->g[a.parity];
+  T* __restrict__ gd = cdp->g[a.parity ^ 1];
+  const T* __restrict__ fs = COUPLED ? cdp->f[a.parity] : nullptr;
+  T* __restrict__ fd = COUPLED ? cdp->f[a.parity ^ 1] : nullptr;
+  T* __restrict__ Jb = cdp->J;
+
+  // halo columns of the phi/psi ring: local column -1 (thread 0) and wact
+  // (thread BX-1), both inside the staged segments
+  const bool hthr = (tid == 0) || (tid == BX - 1);
+  const int hcol = (tid == 0) ? -1 : wact;
+  const int hslot = (tid == 0) ? 0 : wact + 1;
+
+  const T xi = a.ph.xi;
+  const bool do_vol = (MODE == kModeStep) && (a.vol_part != nullptr);
+  double vacc = 0.0;
+  const CaseK<T> K = case_consts<T, COUPLED>(a, cdp, xc);
+
+  auto wrap = [&](int r) -> int { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
+  auto slot_of = [](int k) -> int { return (k + 1) % S; };
+  auto parity_of = [](int k) -> uint32_t { return (uint32_t)(((k + 1) / S) & 1); };
+  auto stage_of = [&](int k) -> T* { return stages + slot_of(k) * STAGE; };
+
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  // Issue the bulk copies of local row k (k in [-1, nrows]); warp 0 only.
+  // Rows -1 and nrows (the halo rows of the item) need the g planes only.
+  auto issue = [&](int k) {
+    const bool full = (k >= 0 && k < nrows);
+    const int np = full ? NPL : 9;
+    const int nj = full ? NJ : 0;
+    T* st = stage_of(k);
+    uint64_t* bar = &bars[slot_of(k)];
+    const uint32_t seg_bytes = (uint32_t)(wact + 8) * sizeof(T);
+    if (lane == 0)
+      mbar_arrive_expect_tx(bar, np * seg_bytes + nj * (uint32_t)wact * sizeof(T));
+    __syncwarp();
+    const int r = wrap(y0 + k);
+    if (lane < np) {
+      const int i = lane < 9 ? lane : lane - 9;
+      const T* plane = (lane < 9 ? gs : fs) + (size_t)i * P;
+      const T* row = plane + (size_t)wrap(r - cy_of(i)) * nx;  // pull: source row r - c_iy
+      T* dst = st + lane * SEG;
+      // staged column j holds global column (x0 - 4 + j) mod nx, j < wact + 8
+      int j = 0, g0, len;
+      if (x0 == 0) {
+        bulk_g2s(dst, row + (nx - 4), 4 * sizeof(T), bar);
+        j = 4;
+        g0 = 0;
+        len = wact;
+      } else {
+        g0 = x0 - 4;
+        len = wact + 4;
+      }
+      if (x0 + wact < nx) {
+        bulk_g2s(dst + j, row + g0, (uint32_t)(len + 4) * sizeof(T), bar);
+      } else {
+        bulk_g2s(dst + j, row + g0, (uint32_t)len * sizeof(T), bar);
+        bulk_g2s(dst + j + len, row, 4 * sizeof(T), bar);
+      }
+    } else if (lane >= 18 && lane < 18 + nj) {
+      const int q = lane - 18;
+      bulk_g2s(st + NPL * SEG + q * BX, Jb + (size_t)q * P + (size_t)r * nx + x0,
+               (uint32_t)wact * sizeof(T), bar);
+    }
+  };
+
+  // g of local column c (may be -1 or wact) from a staged row
+  auto staged_g = [&](const T* st, int c, T G[9]) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) G[i] = st[i * SEG + c + 4 - cx_of(i)];
+  };
+
+  // phi and psi of local row k into the ring (row k must have landed)
+  auto put_row = [&](int k) {
+    const T* st = stage_of(k);
+    const int s = (k + 4) & 3;
+    T G[9];
+    if (act) {
+      staged_g(st, tid, G);
+      const T phi = sum9(G);
+      ring.phi[s][tid + 1] = phi;
+      ring.psi[s][tid + 1] = psi_of(phi, xi);
+    }
+    if (hthr) {
+      staged_g(st, hcol, G);
+      const T phi = sum9(G);
+      ring.phi[s][hslot] = phi;
+      ring.psi[s][hslot] = psi_of(phi, xi);
+    }
+  };
+
+  // ---- prologue: rows -1 .. S-2 in flight; phi of rows -1 and 0 ----------
+  if (warp == 0) {
+    const int last = min(S - 2, nrows);
+    for (int k = -1; k <= last; ++k) issue(k);
+  }
+  bool bad = !mbar_wait_bounded(&bars[slot_of(-1)], parity_of(-1), kWaitCycles);
+  if (!bad) put_row(-1);
+  bad = bad || !mbar_wait_bounded(&bars[slot_of(0)], parity_of(0), kWaitCycles);
+  if (!bad) put_row(0);
+
+  int issued_last = min(S - 2, nrows);  // highest row issued so far
+  for (int k = 0; k < nrows; ++k) {
+    // row k+1 (own row or the halo row below the item) into the ring
+    bad = bad || !mbar_wait_bounded(&bars[slot_of(k + 1)], parity_of(k + 1), kWaitCycles);
+    if (!bad) put_row(k + 1);
+    if (__syncthreads_or(bad)) {
+      // a bulk copy never completed: report, drain what is in flight, leave
+      if (tid == 0) atomicOr(a.flags, kFlagTimeout);
+      for (int m = k + 1; m <= issued_last; ++m)
+        mbar_wait_bounded(&bars[slot_of(m)], parity_of(m), kWaitCycles / 8);
+      return;
+    }
+    // the stage of row k-1 is free: refill it with row k-1+S
+    const int nxt = k - 1 + S;
+    if (nxt <= nrows) {
+      if (warp == 0) {
+        fence_proxy_async_smem();
+        issue(nxt);
+      }
+      issued_last = nxt;
+    }
+    if (act) {
+      const T* st = stage_of(k);
+      T F[9], G[9];
+      staged_g(st, tid, G);
+      if (COUPLED) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) F[i] = st[(9 + i) * SEG + tid + 4 - cx_of(i)];
+      }
+      T jpx = T(0), jpy = T(0);
+      if (MODE == kModeStep) {
+        jpx = st[NPL * SEG + tid];
+        jpy = st[NPL * SEG + BX + tid];
+      }
+      const int y = wrap(y0 + k);
+      const Stencil<T> Sn = read_stencil(ring, k, tid + 1);
+      if (do_vol) vacc += (double)Sn.p;
+      const NodeOut<T> o = node_update<T, COUPLED, MODE>(a.ph, K, F, G, jpx, jpy, Sn, y);
+      const uint32_t node = (uint32_t)y * (uint32_t)nx + (uint32_t)xc;
+      if (MODE == kModeStep) {
+        store_node<T, COUPLED>(fd, gd, Jb, P, node, F, G, o);
+        if (!isfinite(Sn.p + o.ux + o.uy + o.p)) atomicOr(a.flags, kFlagNonFinite);
+      } else {
+        a.out_phi[node] = (double)Sn.p;
+        a.out_ux[node] = (double)o.ux;
+        a.out_uy[node] = (double)o.uy;
+        a.out_p[node] = (double)o.p;
+      }
+    }
+  }
+
+  if (do_vol) {
+    for (int o = 16; o > 0; o >>= 1) vacc += __shfl_down_sync(0xffffffffu, vacc, o);
+    if (lane == 0) vred[warp] = vacc;
+    __syncthreads();
+    if (tid == 0) {
+      double v = 0.0;
+      for (int w = 0; w < BX / 32; ++w) v += vred[w];
+      a.vol_part[(int64_t)blockIdx.x * kMaxRegions] = v;
+    }
+  }
+}
+
+}  // namespace lbmk

@@ -52,7 +52,7 @@ struct Item {
 };
 
 enum { kModeStep = 0, kModeFields = 1 };
-enum { kFlagNonFinite = 1 };
+enum { kFlagNonFinite = 1, kFlagTimeout = 2 };
 
 template <typename T>
 struct StepArgs {

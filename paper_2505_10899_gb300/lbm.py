@@ -71,6 +71,8 @@ def _load():
         "lbm_get_tiling": ([_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                             ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "lbm_set_tiling": ([_H, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+        "lbm_set_kernel": ([_H, ctypes.c_int32], ctypes.c_int),
+        "lbm_get_kernel": ([_H], ctypes.c_int32),
         "lbm_fields": ([_H, ctypes.c_int32, _D, _D, _D, _D], ctypes.c_int),
         "lbm_get_state": ([_H, ctypes.c_int32, _D, _D, _D, ctypes.POINTER(ctypes.c_int64)],
                           ctypes.c_int),
@@ -185,6 +187,14 @@ def lbm_get_tiling(h):
 
 def lbm_set_tiling(h, bx: int, rows: int):
     return _check(_lib.lbm_set_tiling(h, int(bx), int(rows)), "lbm_set_tiling")
+
+
+def lbm_set_kernel(h, variant: int):
+    return _check(_lib.lbm_set_kernel(h, int(variant)), "lbm_set_kernel")
+
+
+def lbm_get_kernel(h) -> int:
+    return int(_lib.lbm_get_kernel(h))
 
 
 def lbm_num_regions(h) -> int:
@@ -308,6 +318,12 @@ class Sim:
 
     def set_tiling(self, bx, rows):
         lbm_set_tiling(self.h, bx, rows)
+
+    def set_kernel(self, variant):
+        lbm_set_kernel(self.h, variant)
+
+    def kernel(self):
+        return lbm_get_kernel(self.h)
 
     def track_volume(self, enable=True):
         """Fused per-step volumes into a device tensor (one FP64 per case)."""

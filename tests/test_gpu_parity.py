@@ -35,10 +35,11 @@ def maxdiff(a, b):
     return float(np.abs(np.asarray(a) - np.asarray(b)).max())
 
 
-def run_pair(L, case, phi0, u0, nsteps, precision, state=None):
+def run_pair(L, case, phi0, u0, nsteps, precision, state=None, variant=0):
     o = oracle.Oracle(case, phi0, u0) if state is None else oracle.Oracle(case, state=state)
     s = L.Sim(case, phi0 if phi0 is not None else np.zeros((case["ny"], case["nx"])),
               u0, precision=precision)
+    s.set_kernel(variant)
     if state is not None:
         f, g, j, t = state
         s.set_state(0, f, g, j, t)
@@ -65,19 +66,24 @@ def compare_full(o, s, tol_pop, tol_phi, tol_u, tol_p):
 L_OK = 0
 
 
+VARIANTS = pytest.mark.parametrize("variant", [1, 2], ids=["regs", "tma"])
+
+
+@VARIANTS
 @pytest.mark.parametrize("lam", [0.5, 0.0])
-def test_two_droplets_fp64(L, lam):
+def test_two_droplets_fp64(L, lam, variant):
     case, phi0, u0, lab, _ = W.two_droplets(noise=1e-3, lam=lam)
-    o, s = run_pair(L, case, phi0, u0, 100, "f64")
+    o, s = run_pair(L, case, phi0, u0, 100, "f64", variant=variant)
     compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
     s.set_regions(0, lab, 2)
     v = s.volume()
     assert np.abs(v / o.volume(lab, 2) - 1).max() < 1e-13
 
 
-def test_two_droplets_fp32(L):
+@VARIANTS
+def test_two_droplets_fp32(L, variant):
     case, phi0, u0, lab, _ = W.two_droplets(noise=1e-3)
-    o, s = run_pair(L, case, phi0, u0, 100, "f32")
+    o, s = run_pair(L, case, phi0, u0, 100, "f32", variant=variant)
     phi, ux, uy, p = s.fields(0)
     ophi, oux, ouy, op = o.fields()
     assert maxdiff(phi, ophi) <= TOL32_PHI
@@ -87,46 +93,56 @@ def test_two_droplets_fp32(L):
     assert np.abs(s.volume() / o.volume(lab, 2) - 1).max() < 1e-6
 
 
-def test_variable_density_random_state_fp64(L):
+@VARIANTS
+def test_variable_density_random_state_fp64(L, variant):
     # ragged grid (several strips and a partial one), density ratio 10,
     # unequal viscosities, non-default free rates, random non-equilibrium state
     case = W.base_case(300, 70, sigma=5e-3, rho_l=10.0, rho_g=1.0, tau_f_l=0.7,
                        tau_f_g=1.2, s_f=[1.1, 1.3, 0.9, 1.0, 1.2, 1.0, 1.4, 1.0, 1.0],
                        s_g=[1.0, 1.2, 1.3, 1.0, 0.8, 1.0, 0.9, 1.1, 1.5])
     f, g, j = W.random_state(300, 70, seed=77)
-    o, s = run_pair(L, case, None, None, 30, "f64", state=(f, g, j, 5))
+    o, s = run_pair(L, case, None, None, 30, "f64", state=(f, g, j, 5), variant=variant)
     compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
 
 
-def test_translating_droplet_fp64(L):
+@VARIANTS
+def test_translating_droplet_fp64(L, variant):
     case = W.base_case(96, 80, rho_l=3.0, tau_f_l=0.9, tau_f_g=0.9)
     phi0 = W.tanh_disc(96, 80, 40.0, 37.0, 15.0, 4.0, periodic=True)
     phi0 += W.uniform(5, phi0.shape, -1e-3, 1e-3)
     u0 = np.zeros((2, 80, 96))
     u0[0], u0[1] = 0.013, -0.008
-    o, s = run_pair(L, case, phi0, u0, 100, "f64")
+    o, s = run_pair(L, case, phi0, u0, 100, "f64", variant=variant)
     compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
 
 
-@pytest.mark.parametrize("shape", [(1, 1), (3, 3), (1, 5), (4, 1), (2, 7), (33, 5), (129, 3)])
+@pytest.mark.parametrize("shape", [(1, 1), (3, 3), (1, 5), (4, 1), (2, 7), (33, 5), (129, 3),
+                                   (5, 4), (3, 8), (7, 36), (2, 132)])
 def test_degenerate_grids_fp64(L, shape):
     ny, nx = shape
     case = W.base_case(nx, ny, sigma=1e-2)
     f, g, j = W.random_state(nx, ny, seed=nx * 100 + ny)
     o, s = run_pair(L, case, None, None, 7, "f64", state=(f, g, j, 0))
     compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
+    if nx % 4 == 0:   # also through the bulk-copy kernel (periodic-wrap pieces)
+        o, s = run_pair(L, case, None, None, 7, "f64", state=(f, g, j, 0), variant=2)
+        compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
+        o, s = run_pair(L, case, None, None, 7, "f32", state=(f, g, j, 0), variant=2)
+        assert maxdiff(s.fields(0)[0], o.fields()[0]) <= TOL32_PHI
 
 
-def test_vortex_fp64(L):
+@VARIANTS
+def test_vortex_fp64(L, variant):
     case, phi0, _ = W.single_vortex(n=64, W=3.0, U=0.02, T=256)
     phi0 = phi0 + W.uniform(9, phi0.shape, -1e-3, 1e-3)
-    o, s = run_pair(L, case, phi0, None, 100, "f64")
+    o, s = run_pair(L, case, phi0, None, 100, "f64", variant=variant)
     compare_full(o, s, TOL64, TOL64, TOL64, 0.0)
 
 
-def test_vortex_fp32(L):
+@VARIANTS
+def test_vortex_fp32(L, variant):
     case, phi0, _ = W.single_vortex(n=64, W=3.0, U=0.02, T=256)
-    o, s = run_pair(L, case, phi0, None, 100, "f32")
+    o, s = run_pair(L, case, phi0, None, 100, "f32", variant=variant)
     phi = s.fields(0)[0]
     assert maxdiff(phi, o.fields()[0]) <= TOL32_PHI
 
@@ -144,8 +160,10 @@ def test_graph_replay_and_parity_realignment_fp64(L):
     assert maxdiff(f, o.f) <= TOL64 and maxdiff(g, o.g) <= TOL64
 
 
-def test_batch_of_uneven_cases_fp64(L):
-    specs = [(64, 64, 1.0), (96, 40, 4.0), (37, 51, 10.0)]
+@pytest.mark.parametrize("specs", [[(64, 64, 1.0), (96, 40, 4.0), (37, 51, 10.0)],
+                                   [(64, 64, 1.0), (192, 40, 4.0), (36, 52, 10.0)]],
+                         ids=["regs-only", "tma-eligible"])
+def test_batch_of_uneven_cases_fp64(L, specs):
     cases, phis, us, oracles = [], [], [], []
     for k, (nx, ny, ratio) in enumerate(specs):
         c = W.base_case(nx, ny, rho_l=ratio, tau_f_l=0.8, tau_f_g=0.8)
@@ -213,7 +231,8 @@ def test_zero_steps_and_bad_calls(L):
         s.set_regions(0, None, 9)
 
 
-def test_tiling_does_not_change_results(L):
+@VARIANTS
+def test_tiling_does_not_change_results(L, variant):
     # per-node arithmetic is independent of the work tiling: bitwise equal
     case = W.base_case(200, 90, rho_l=5.0, tau_f_l=0.7, tau_f_g=1.1)
     phi0 = W.tanh_disc(200, 90, 90.0, 40.0, 25.0, 4.0, periodic=True)
@@ -223,6 +242,7 @@ def test_tiling_does_not_change_results(L):
     for bx, rows in [(32, 2), (64, 17), (128, 64), (128, 3)]:
         for prec in ("f32",):
             s = L.Sim(case, phi0, u0, precision=prec)
+            s.set_kernel(variant)
             s.set_tiling(bx, rows)
             assert s.tiling()[:2] == (bx, rows)
             s.step(33)
@@ -255,3 +275,23 @@ def test_fused_volume_tracking(L):
     s.set_regions(0, np.zeros((48, 64), np.int8), 2)
     with pytest.raises(L.LbmError):
         s.track_volume(True)
+
+
+def test_kernel_variants_agree_bitwise_fp32(L):
+    # both load paths feed the same per-node arithmetic: identical results
+    case = W.base_case(160, 72, rho_l=4.0, tau_f_l=0.8, tau_f_g=1.2)
+    phi0 = W.tanh_disc(160, 72, 70.0, 30.0, 20.0, 4.0, periodic=True)
+    u0 = np.zeros((2, 72, 160))
+    u0[1] = -0.012
+    out = []
+    for variant in (1, 2):
+        s = L.Sim(case, phi0, u0, precision="f32")
+        s.set_kernel(variant)
+        assert s.kernel() == variant
+        s.step(50)
+        out.append(s.get_state(0))
+    for x, y in zip(out[0][:3], out[1][:3]):
+        assert np.array_equal(x, y)
+    s = L.Sim(W.base_case(30, 8), np.zeros((8, 30)), None, precision="f32")
+    with pytest.raises(L.LbmError):
+        s.set_kernel(2)          # 30 is not a multiple of 4
