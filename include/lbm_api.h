@@ -149,8 +149,10 @@ int lbm_track_volume(lbm_handle* h, double* d_out);
 /* Work tiling of the step kernel: each CTA owns a strip of bx columns
  * (bx in {32, 64, 128}) and marches down runs of `rows` rows (2..1024).
  * lbm_init picks a default from the batch size; lbm_set_tiling replaces it
- * (results are identical for every tiling, only speed changes; the step
- * order of floating-point operations per node does not depend on it).
+ * (results agree for every tiling up to floating-point rounding: the
+ * per-node operations are the same, but different kernel instantiations
+ * may fuse multiply-adds differently; for a given tiling runs are
+ * bitwise reproducible).
  * lbm_get_tiling also reports the number of CTAs (work items) per step. */
 int lbm_get_tiling(const lbm_handle* h, int32_t* bx, int32_t* rows,
                    int32_t* n_items);
@@ -159,7 +161,8 @@ int lbm_set_tiling(lbm_handle* h, int32_t bx, int32_t rows);
 /* Step-kernel variant: 0 = automatic, 1 = register-pipelined loads (any
  * grid), 2 = bulk-copy (TMA) staged loads through shared memory (needs every
  * case to have nx >= 4 and nx a multiple of 4 in FP32, of 2 in FP64).  Both
- * give identical results.  lbm_get_kernel returns the variant in use (1 or 2). */
+ * run the same per-node arithmetic (equal up to rounding, see
+ * lbm_set_tiling).  lbm_get_kernel returns the variant in use (1 or 2). */
 int lbm_set_kernel(lbm_handle* h, int32_t variant);
 int32_t lbm_get_kernel(const lbm_handle* h);
 
