@@ -204,6 +204,35 @@ int lbm_status(lbm_handle* h);
 int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out,
                      double* h_param_grads);
 
+/* Allocation-free phase volumes, for callers that cannot allocate device
+ * memory (for example code that runs while a memory pool forbids new
+ * allocations, or a host framework that only lends out buffers it owns).
+ * The paper has no counterpart: this is a variant of the labelled volume
+ * reduction behind lbm_volume that needs no workspace.
+ *   d_g: device pointer to the nine phase-field populations after streaming,
+ *        g_i(x,t), plane i at d_g + i*plane_stride elements, each plane
+ *        [y][x] with x fastest; element type FP64 or FP32 (precision).
+ *   d_labels: device int8 [ny][nx], region of each node in [0, nregions) or
+ *        -1 (none); NULL = one region, the whole grid.
+ *   d_out: device FP64 [nregions], V_r = sum over region r of
+ *        phi = sum_i g_i (Eq. 35), reduced in a fixed order.
+ *   stream: cudaStream_t (NULL = legacy default stream); the call enqueues
+ *        two kernels and does not synchronise.
+ * Limits: 1 <= nregions <= 8, plane_stride >= nx*ny, nx <= 524288 columns
+ * (4096 CTAs of 128 columns); larger sizes return LBM_ERR_ARG with a message
+ * in lbm_last_error().  Allocates nothing: the per-CTA partial sums live in a
+ * fixed static device array of 256 KiB that every GPU which loads the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's address on the current device, so make the first call before any
+ * stream capture.  All calls share the array and each overwrites what it
+ * uses; calls whose kernels overlap on the GPU (different streams, or
+ * concurrent host threads) race on it and must be serialised by the caller.
+ * Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_phase_volume_noalloc(const void* d_g, int32_t precision, int32_t nx,
+                             int32_t ny, int64_t plane_stride,
+                             const int8_t* d_labels, int32_t nregions,
+                             double* d_out, void* stream);
+
 void lbm_destroy(lbm_handle* h);
 const char* lbm_status_string(int status);
 const char* lbm_last_error(void);

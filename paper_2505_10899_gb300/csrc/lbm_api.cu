@@ -522,6 +522,10 @@ size_t state_bytes_case(const lbm_handle* h, int k) {
 
 }  // namespace
 
+namespace lbmk {
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace lbmk
+
 // ============================================================================
 // C ABI
 // ============================================================================

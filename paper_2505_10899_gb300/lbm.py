@@ -84,6 +84,9 @@ def _load():
         "lbm_status": ([_H], ctypes.c_int),
         "lbm_adjoint_step": ([_H, _VP, _VP, _D], ctypes.c_int),
         "lbm_destroy": ([_H], None),
+        "lbm_phase_volume_noalloc": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int64, _VP, ctypes.c_int32, _VP, _VP],
+                                     ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -264,6 +267,16 @@ def lbm_status(h) -> int:
 def lbm_adjoint_step(h, d_in=0, d_out=0):
     grads = np.zeros(8)
     return int(_lib.lbm_adjoint_step(h, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), _dp(grads)))
+
+
+def lbm_phase_volume_noalloc(d_g: int, precision: str, nx: int, ny: int, plane_stride: int,
+                             d_labels: int, nregions: int, d_out: int, stream: int = 0):
+    """Phase volumes of device populations without any device allocation."""
+    prec = {"f64": LBM_F64, "f32": LBM_F32}[precision]
+    return _check(_lib.lbm_phase_volume_noalloc(
+        ctypes.c_void_p(d_g), prec, int(nx), int(ny), int(plane_stride),
+        ctypes.c_void_p(d_labels) if d_labels else None, int(nregions),
+        ctypes.c_void_p(d_out), ctypes.c_void_p(stream)), "lbm_phase_volume_noalloc")
 
 
 def lbm_destroy(h):
