@@ -16,20 +16,24 @@ inline int grid_for(int64_t n, int threads) {
   return (int)(b < 1 ? 1 : b);
 }
 
-// pipeline depth of the TMA kernel: 4 stages in FP32, 3 in FP64 (smem)
-constexpr int kStages = sizeof(LBM_T) == 4 ? 4 : 3;
+// pipeline depth of the TMA kernel: 4 stages for narrow strips in FP32,
+// 3 otherwise (keeps shared memory per CTA low enough for 5-6 CTAs per SM)
+template <int BX>
+constexpr int stages_for() {
+  return (sizeof(LBM_T) == 4 && BX <= 64) ? 4 : 3;
+}
 
 template <int BX, bool COUPLED, int MODE>
 cudaError_t step_tma(const StepArgs<LBM_T>& a, int n, cudaStream_t s) {
-  using SH = TmaShape<LBM_T, BX, COUPLED, MODE, kStages>;
-  step_kernel_tma<LBM_T, BX, COUPLED, MODE, kStages><<<n, BX, SH::SMEM_BYTES, s>>>(a);
+  using SH = TmaShape<LBM_T, BX, COUPLED, MODE, stages_for<BX>()>;
+  step_kernel_tma<LBM_T, BX, COUPLED, MODE, stages_for<BX>()><<<n, BX, SH::SMEM_BYTES, s>>>(a);
   return cudaGetLastError();
 }
 
 template <int BX, bool COUPLED, int MODE>
 cudaError_t prep_one() {
-  using SH = TmaShape<LBM_T, BX, COUPLED, MODE, kStages>;
-  return cudaFuncSetAttribute(step_kernel_tma<LBM_T, BX, COUPLED, MODE, kStages>,
+  using SH = TmaShape<LBM_T, BX, COUPLED, MODE, stages_for<BX>()>;
+  return cudaFuncSetAttribute(step_kernel_tma<LBM_T, BX, COUPLED, MODE, stages_for<BX>()>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::SMEM_BYTES);
 }
 
@@ -91,11 +95,12 @@ template <>
 size_t tma_smem_bytes<LBM_T>(int bx, bool coupled, int mode) {
   auto pick = [&](auto bxc) -> size_t {
     constexpr int B = decltype(bxc)::value;
+    constexpr int S = stages_for<B>();
     if (coupled)
-      return mode == kModeStep ? TmaShape<LBM_T, B, true, kModeStep, kStages>::SMEM_BYTES
-                               : TmaShape<LBM_T, B, true, kModeFields, kStages>::SMEM_BYTES;
-    return mode == kModeStep ? TmaShape<LBM_T, B, false, kModeStep, kStages>::SMEM_BYTES
-                             : TmaShape<LBM_T, B, false, kModeFields, kStages>::SMEM_BYTES;
+      return mode == kModeStep ? TmaShape<LBM_T, B, true, kModeStep, S>::SMEM_BYTES
+                               : TmaShape<LBM_T, B, true, kModeFields, S>::SMEM_BYTES;
+    return mode == kModeStep ? TmaShape<LBM_T, B, false, kModeStep, S>::SMEM_BYTES
+                             : TmaShape<LBM_T, B, false, kModeFields, S>::SMEM_BYTES;
   };
   switch (bx) {
     case 32: return pick(std::integral_constant<int, 32>{});

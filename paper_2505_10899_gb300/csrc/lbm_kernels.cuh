@@ -138,13 +138,11 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
     const int s = (k + 4) & 3;
     if (act) {
       const T phi = sum9(G);
-      ring.phi[s][tid + 1] = phi;
-      ring.psi[s][tid + 1] = psi_of(phi, xi);
+      ring.put(s, tid + 1, phi, psi_of(phi, xi));
     }
     if (hthr) {
       const T phi = sum9(H);
-      ring.phi[s][hslot] = phi;
-      ring.psi[s][hslot] = psi_of(phi, xi);
+      ring.put(s, hslot, phi, psi_of(phi, xi));
     }
   };
 

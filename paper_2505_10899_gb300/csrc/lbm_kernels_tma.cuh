@@ -154,14 +154,12 @@ __global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
     if (act) {
       staged_g(st, tid, G);
       const T phi = sum9(G);
-      ring.phi[s][tid + 1] = phi;
-      ring.psi[s][tid + 1] = psi_of(phi, xi);
+      ring.put(s, tid + 1, phi, psi_of(phi, xi));
     }
     if (hthr) {
       staged_g(st, hcol, G);
       const T phi = sum9(G);
-      ring.phi[s][hslot] = phi;
-      ring.psi[s][hslot] = psi_of(phi, xi);
+      ring.put(s, hslot, phi, psi_of(phi, xi));
     }
   };
 

@@ -107,12 +107,29 @@ __device__ __forceinline__ void add_back(T v[9], T d0, T d1, T d2, T d3, T d4,
   v[8] += (B + Xd) - (Yd + d8);
 }
 
-// Shared-memory ring of phi and psi: 4 rows x (BX + 2) columns; column 0 and
+// (phi, psi) pair of one node, read with one vector load.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+  using type = float2;
+};
+template <>
+struct Pair<double> {
+  using type = double2;
+};
+
+// Shared-memory ring of (phi, psi): 4 rows x (BX + 2) columns; column 0 and
 // BX+1 (or wact+1) hold the halo columns left and right of the strip.
 template <typename T, int BX>
 struct Ring {
-  T phi[4][BX + 2];
-  T psi[4][BX + 2];
+  typename Pair<T>::type pq[4][BX + 2];
+  __device__ __forceinline__ void put(int s, int c, T phi, T psi) {
+    typename Pair<T>::type v;
+    v.x = phi;
+    v.y = psi;
+    pq[s][c] = v;
+  }
 };
 
 // phi at the node and its 8 neighbours, psi at the 8 neighbours.
@@ -127,23 +144,26 @@ template <typename T, int BX>
 __device__ __forceinline__ Stencil<T> read_stencil(const Ring<T, BX>& ring, int k, int lc) {
   const int sm = (k + 3) & 3, s0 = k & 3, sp = (k + 1) & 3;
   Stencil<T> S;
-  S.p = ring.phi[s0][lc];
-  S.pE = ring.phi[s0][lc + 1];
-  S.pW = ring.phi[s0][lc - 1];
-  S.pN = ring.phi[sp][lc];
-  S.pS = ring.phi[sm][lc];
-  S.pNE = ring.phi[sp][lc + 1];
-  S.pNW = ring.phi[sp][lc - 1];
-  S.pSE = ring.phi[sm][lc + 1];
-  S.pSW = ring.phi[sm][lc - 1];
-  S.qE = ring.psi[s0][lc + 1];
-  S.qW = ring.psi[s0][lc - 1];
-  S.qN = ring.psi[sp][lc];
-  S.qS = ring.psi[sm][lc];
-  S.qNE = ring.psi[sp][lc + 1];
-  S.qNW = ring.psi[sp][lc - 1];
-  S.qSE = ring.psi[sm][lc + 1];
-  S.qSW = ring.psi[sm][lc - 1];
+  const auto c = ring.pq[s0][lc], e = ring.pq[s0][lc + 1], w = ring.pq[s0][lc - 1];
+  const auto n = ring.pq[sp][lc], ne = ring.pq[sp][lc + 1], nw = ring.pq[sp][lc - 1];
+  const auto so = ring.pq[sm][lc], se = ring.pq[sm][lc + 1], sw = ring.pq[sm][lc - 1];
+  S.p = c.x;
+  S.pE = e.x;
+  S.pW = w.x;
+  S.pN = n.x;
+  S.pS = so.x;
+  S.pNE = ne.x;
+  S.pNW = nw.x;
+  S.pSE = se.x;
+  S.pSW = sw.x;
+  S.qE = e.y;
+  S.qW = w.y;
+  S.qN = n.y;
+  S.qS = so.y;
+  S.qNE = ne.y;
+  S.qNW = nw.y;
+  S.qSE = se.y;
+  S.qSW = sw.y;
   return S;
 }
 
