@@ -57,7 +57,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register, 2 bulk-copy")
-    ap.add_argument("--tiling", type=str, default=None, help="BX,ROWS (default: library choice)")
+    ap.add_argument("--tiling", type=str, default=None, help="BX,ROWS (default: autotuned)")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -195,9 +196,12 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         sim = lbm.Sim(cases, phis, us, precision=args.precision, stream=stream)
         sim.set_kernel(args.kernel)
+        tuned = None
         if args.tiling:
             bx, rows = (int(v) for v in args.tiling.split(","))
             sim.set_tiling(bx, rows)
+        elif not args.no_autotune and args.kernel == 0:
+            tuned = sim.autotune(2)   # part of the warm-up; the state is unchanged
         vol = sim.track_volume(True)
         v0 = None
         sim.step(max(args.warmup, 3))
@@ -271,7 +275,8 @@ def run_ours(args):
                                + f"<{'float' if args.precision == 'f32' else 'double'},"
                                f"{sim_bx(sim)},coupled>",
                      "tiling": {"bx": sim.tiling()[0], "rows": sim.tiling()[1],
-                                "ctas": sim.tiling()[2]},
+                                "ctas": sim.tiling()[2],
+                                "chosen_by": "autotune" if tuned else "fixed"},
                      "algorithmic_bytes_per_node": bpn, "peak_kind": peak_kind,
                      "kernel_ms": round(kms, 4)},
         "clocks": clocks,

@@ -158,6 +158,14 @@ int lbm_get_tiling(const lbm_handle* h, int32_t* bx, int32_t* rows,
                    int32_t* n_items);
 int lbm_set_tiling(lbm_handle* h, int32_t bx, int32_t rows);
 
+/* Self-tuning: time every (kernel variant, bx, rows) candidate on this
+ * batch with `trials` trial launches each (CUDA events on the handle's
+ * stream) and keep the fastest.  Trial launches read the current state and
+ * write only the buffers the next step overwrites, so the state and the step
+ * index do not change.  Outputs may be NULL.  Synchronises. */
+int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel,
+                 int32_t* best_bx, int32_t* best_rows, double* best_ms);
+
 /* Step-kernel variant: 0 = automatic, 1 = register-pipelined loads (any
  * grid), 2 = bulk-copy (TMA) staged loads through shared memory (needs every
  * case to have nx >= 4 and nx a multiple of 4 in FP32, of 2 in FP64).  Both

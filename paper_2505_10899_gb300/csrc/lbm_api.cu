@@ -165,26 +165,30 @@ std::vector<Item> make_items(const lbm_params* c, int n, const Tiling& t,
   return it;
 }
 
-// Default tiling: wide strips and long runs (few halo re-reads) unless the
-// batch is too small to give every SM several CTAs.
+// Default tiling: the widest strip that leaves at most 15% of the threads idle
+// on ragged strips, and runs of 16 rows (short runs balance the load across
+// SMs; the halo rows they re-read come from L2) unless the batch is too small
+// to give every SM several CTAs.
 Tiling choose_tiling(const lbm_params* c, int n) {
-  int min_nx = c[0].nx;
   int64_t nodes = 0;
-  for (int k = 0; k < n; ++k) {
-    min_nx = std::min(min_nx, c[k].nx);
-    nodes += (int64_t)c[k].nx * c[k].ny;
-  }
-  const int64_t want = 152 * 8;  // CTAs for a full machine
+  for (int k = 0; k < n; ++k) nodes += (int64_t)c[k].nx * c[k].ny;
   Tiling t;
-  t.bx = min_nx >= 128 ? 128 : (min_nx >= 64 ? 64 : 32);
-  for (;;) {
-    int64_t rows = nodes / (t.bx * want);
-    if (rows >= 16 || t.bx == 32) {
-      t.rows = (int)std::max<int64_t>(2, std::min<int64_t>(64, rows));
+  t.bx = 32;
+  for (int bx : {128, 64}) {
+    int64_t padded = 0;
+    for (int k = 0; k < n; ++k) padded += (int64_t)((c[k].nx + bx - 1) / bx) * bx * c[k].ny;
+    if (padded * 100 <= nodes * 115) {
+      t.bx = bx;
       break;
     }
-    t.bx /= 2;
   }
+  const int64_t want = 152 * 12;  // CTAs for a full machine
+  int64_t rows = nodes / (t.bx * want);
+  while (rows < 4 && t.bx > 32) {
+    t.bx /= 2;
+    rows = nodes / (t.bx * want);
+  }
+  t.rows = (int)std::max<int64_t>(2, std::min<int64_t>(16, rows));
   return t;
 }
 
@@ -233,8 +237,8 @@ Layout make_layout(const lbm_params* c, int n, int n_items, int total_regions) {
     } else {
       L.f[k] = 0;
     }
-    L.J[k] = off;
-    off = align_up(off + 2 * pb);
+    L.J[k] = off;  // two buffers of 2 planes
+    off = align_up(off + 4 * pb);
     L.lab[k] = off;
     off = align_up(off + (size_t)plane);
   }
@@ -278,7 +282,8 @@ CaseDev<T> make_case(const lbm_handle* h, int k) {
     c.f[0] = (T*)(h->ws + L.f[k]);
     c.f[1] = (T*)(h->ws + L.f[k] + 9 * pb);
   }
-  c.J = (T*)(h->ws + L.J[k]);
+  c.J[0] = (T*)(h->ws + L.J[k]);
+  c.J[1] = (T*)(h->ws + L.J[k] + 2 * pb);
   c.labels = nullptr;
   c.plane = L.plane[k];
   c.nx = p.nx;
@@ -462,7 +467,7 @@ int do_get_state(lbm_handle* h, int c, double* f, double* g, double* j) {
   }
   if (j) {
     for (int q = 0; q < 2; ++q) {
-      cudaError_t e = lbmk::launch_copy_to_f64<T>(st, cd.J + q * cd.plane, n, h->stream);
+      cudaError_t e = lbmk::launch_copy_to_f64<T>(st, cd.J[h->parity] + q * cd.plane, n, h->stream);
       if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
       LBM_CUDA(cudaMemcpyAsync(j + q * n, st, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
       LBM_CUDA(cudaStreamSynchronize(h->stream));
@@ -491,7 +496,7 @@ int do_set_state(lbm_handle* h, int c, const double* f, const double* g, const d
   if (j) {
     for (int q = 0; q < 2; ++q) {
       LBM_CUDA(cudaMemcpyAsync(st, j + q * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-      cudaError_t e = lbmk::launch_copy_to_T<T>(cd.J + q * cd.plane, st, n, h->stream);
+      cudaError_t e = lbmk::launch_copy_to_T<T>(cd.J[h->parity] + q * cd.plane, st, n, h->stream);
       if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
       LBM_CUDA(cudaStreamSynchronize(h->stream));
     }
@@ -728,6 +733,85 @@ int32_t lbm_get_kernel(const lbm_handle* h) {
   return use_tma(h) ? 2 : 1;
 }
 
+int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel, int32_t* best_bx,
+                 int32_t* best_rows, double* best_ms) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (trials < 1 || trials > 100) return fail(LBM_ERR_ARG, "trials must lie in [1, 100]");
+  const bool coupled = h->flow == LBM_FLOW_COUPLED;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LBM_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(LBM_ERR_CUDA, "event create failed");
+  }
+  // Trial launches read the current source buffers and write the other
+  // buffer set (populations and phi*u), which the next real step overwrites
+  // completely: the state is not changed and the clock does not advance.
+  auto trial = [&](int n) -> cudaError_t {
+    for (int j = 0; j < n; ++j) {
+      cudaError_t e;
+      if (h->precision == LBM_F32)
+        e = lbmk::launch_step<float>(step_args<float>(h, h->parity, 0), h->tile.bx, coupled,
+                                     lbmk::kModeStep, use_tma(h), (int)h->items.size(), h->stream);
+      else
+        e = lbmk::launch_step<double>(step_args<double>(h, h->parity, 0), h->tile.bx, coupled,
+                                      lbmk::kModeStep, use_tma(h), (int)h->items.size(), h->stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
+  const Tiling keep_tile = h->tile;
+  const int keep_kernel = h->kernel;
+  double best = 1e300;
+  Tiling best_t = keep_tile;
+  int best_k = use_tma(h) ? 2 : 1;
+  int rc = LBM_OK;
+  for (int kv : {2, 1}) {
+    if (kv == 2 && !h->tma_ok) continue;
+    for (int bx : {128, 64, 32}) {
+      for (int rows : {4, 8, 16, 32, 64}) {
+        h->kernel = kv;
+        rc = lbm_set_tiling(h, bx, rows);
+        if (rc != LBM_OK) break;
+        cudaError_t e = trial(1);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        if (e == cudaSuccess) e = trial(trials);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          rc = fail(LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+          break;
+        }
+        if (ms / trials < best) {
+          best = ms / trials;
+          best_t.bx = bx;
+          best_t.rows = rows;
+          best_k = kv;
+        }
+      }
+      if (rc != LBM_OK) break;
+    }
+    if (rc != LBM_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != LBM_OK) {
+    h->kernel = keep_kernel;
+    lbm_set_tiling(h, keep_tile.bx, keep_tile.rows);
+    return rc;
+  }
+  h->kernel = best_k;
+  rc = lbm_set_tiling(h, best_t.bx, best_t.rows);
+  if (rc != LBM_OK) return rc;
+  if (best_kernel) *best_kernel = best_k;
+  if (best_bx) *best_bx = best_t.bx;
+  if (best_rows) *best_rows = best_t.rows;
+  if (best_ms) *best_ms = best;
+  return read_flags(h);
+}
+
 int lbm_get_tiling(const lbm_handle* h, int32_t* bx, int32_t* rows, int32_t* n_items) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (bx) *bx = h->tile.bx;
@@ -857,7 +941,8 @@ int lbm_save(lbm_handle* h, void* h_buf, size_t bytes) {
       LBM_CUDA(cudaMemcpy2DAsync(p, n * es, fb, pb, n * es, 9, cudaMemcpyDeviceToHost, h->stream));
       p += 9 * n * es;
     }
-    LBM_CUDA(cudaMemcpy2DAsync(p, n * es, h->ws + h->L.J[k], pb, n * es, 2, cudaMemcpyDeviceToHost,
+    LBM_CUDA(cudaMemcpy2DAsync(p, n * es, h->ws + h->L.J[k] + h->parity * 2 * pb, pb, n * es, 2,
+                               cudaMemcpyDeviceToHost,
                                h->stream));
     p += 2 * n * es;
   }
@@ -887,7 +972,8 @@ int lbm_load(lbm_handle* h, const void* h_buf, size_t bytes) {
       LBM_CUDA(cudaMemcpy2DAsync(fb, pb, p, n * es, n * es, 9, cudaMemcpyHostToDevice, h->stream));
       p += 9 * n * es;
     }
-    LBM_CUDA(cudaMemcpy2DAsync(h->ws + h->L.J[k], pb, p, n * es, n * es, 2, cudaMemcpyHostToDevice,
+    LBM_CUDA(cudaMemcpy2DAsync(h->ws + h->L.J[k] + h->parity * 2 * pb, pb, p, n * es, n * es, 2,
+                               cudaMemcpyHostToDevice,
                                h->stream));
     p += 2 * n * es;
   }

@@ -72,8 +72,8 @@ __global__ void init_kernel(CaseDev<T> cd, double beta4, double kappa,
       gb[dst] = (T)gi;
       if (fb) fb[dst] = (T)(rho * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2));
     }
-    cd.J[k] = (T)Jx;
-    cd.J[cd.plane + k] = (T)Jy;
+    cd.J[par][k] = (T)Jx;
+    cd.J[par][cd.plane + k] = (T)Jy;
   }
 }
 

@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
   T* __restrict__ gd = cdp->g[a.parity ^ 1];
   const T* __restrict__ fs = COUPLED ? cdp->f[a.parity] : nullptr;
   T* __restrict__ fd = COUPLED ? cdp->f[a.parity ^ 1] : nullptr;
-  T* __restrict__ Jb = cdp->J;
+  const T* __restrict__ Js = cdp->J[a.parity];
+  T* __restrict__ Jd = cdp->J[a.parity ^ 1];
 
   // Halo columns: thread 0 serves the column left of the strip, thread BX-1
   // the column right of the last active one.
@@ -117,8 +118,8 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
     pull9(gs, P, o0, om, op, xc, xm, xp, R.G);
     if (COUPLED) pull9(fs, P, o0, om, op, xc, xm, xp, R.F);
     if (MODE == kModeStep) {  // phi*u of the previous step at the own node
-      R.J[0] = Jb[o0 + xc];
-      R.J[1] = Jb[P + o0 + xc];
+      R.J[0] = Js[o0 + xc];
+      R.J[1] = Js[P + o0 + xc];
     }
   };
   auto fetch_g = [&](int r, Regs& R) {
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
       const NodeOut<T> o = node_update<T, COUPLED, MODE>(a.ph, K, C.F, C.G, C.J[0], C.J[1], S, y);
       const uint32_t node = rowoff(y) + (uint32_t)xc;
       if (MODE == kModeStep) {
-        store_node<T, COUPLED>(fd, gd, Jb, P, node, C.F, C.G, o);
+        store_node<T, COUPLED>(fd, gd, Jd, P, node, C.F, C.G, o);
         if (!isfinite(S.p + o.ux + o.uy + o.p)) atomicOr(a.flags, kFlagNonFinite);
       } else {
         a.out_phi[node] = (double)S.p;

@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
   T* __restrict__ gd = cdp->g[a.parity ^ 1];
   const T* __restrict__ fs = COUPLED ? cdp->f[a.parity] : nullptr;
   T* __restrict__ fd = COUPLED ? cdp->f[a.parity ^ 1] : nullptr;
-  T* __restrict__ Jb = cdp->J;
+  const T* __restrict__ Js = cdp->J[a.parity];
+  T* __restrict__ Jd = cdp->J[a.parity ^ 1];
 
   // halo columns of the phi/psi ring: local column -1 (thread 0) and wact
   // (thread BX-1), both inside the staged segments
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
       }
     } else if (lane >= 18 && lane < 18 + nj) {
       const int q = lane - 18;
-      bulk_g2s(st + NPL * SEG + q * BX, Jb + (size_t)q * P + (size_t)r * nx + x0,
+      bulk_g2s(st + NPL * SEG + q * BX, Js + (size_t)q * P + (size_t)r * nx + x0,
                (uint32_t)wact * sizeof(T), bar);
     }
   };
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
       const NodeOut<T> o = node_update<T, COUPLED, MODE>(a.ph, K, F, G, jpx, jpy, Sn, y);
       const uint32_t node = (uint32_t)y * (uint32_t)nx + (uint32_t)xc;
       if (MODE == kModeStep) {
-        store_node<T, COUPLED>(fd, gd, Jb, P, node, F, G, o);
+        store_node<T, COUPLED>(fd, gd, Jd, P, node, F, G, o);
         if (!isfinite(Sn.p + o.ux + o.uy + o.p)) atomicOr(a.flags, kFlagNonFinite);
       } else {
         a.out_phi[node] = (double)Sn.p;

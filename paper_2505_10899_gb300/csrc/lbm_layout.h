@@ -17,7 +17,7 @@ template <typename T>
 struct CaseDev {
   T* f[2];               // hydrodynamic populations, 9 planes per buffer
   T* g[2];               // phase-field populations, 9 planes per buffer
-  T* J;                  // phi*u of the previous step, 2 planes (in place)
+  T* J[2];               // phi*u of the previous step, 2 planes per buffer
   const int8_t* labels;  // volume regions, [y][x]; nullptr = one region
   int64_t plane;         // elements per plane (nx*ny rounded up)
   int32_t nx, ny;

@@ -318,11 +318,11 @@ __device__ __forceinline__ NodeOut<T> node_update(const Phys<T>& ph, const CaseK
 // Store the post-collision state of one node (pull layout: own position).
 template <typename T, bool COUPLED>
 __device__ __forceinline__ void store_node(T* __restrict__ fd, T* __restrict__ gd,
-                                           T* __restrict__ Jb, uint32_t P, uint32_t node,
+                                           T* __restrict__ Jd, uint32_t P, uint32_t node,
                                            const T (&Fc)[9], const T (&Gc)[9],
                                            const NodeOut<T>& o) {
-  Jb[node] = o.Jx;
-  Jb[P + node] = o.Jy;
+  Jd[node] = o.Jx;
+  Jd[P + node] = o.Jy;
 #pragma unroll
   for (int i = 0; i < 9; ++i) gd[i * P + node] = Gc[i];
   if (COUPLED) {

@@ -72,6 +72,9 @@ def _load():
                             ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "lbm_set_tiling": ([_H, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
         "lbm_set_kernel": ([_H, ctypes.c_int32], ctypes.c_int),
+        "lbm_autotune": ([_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _D],
+                         ctypes.c_int),
         "lbm_get_kernel": ([_H], ctypes.c_int32),
         "lbm_fields": ([_H, ctypes.c_int32, _D, _D, _D, _D], ctypes.c_int),
         "lbm_get_state": ([_H, ctypes.c_int32, _D, _D, _D, ctypes.POINTER(ctypes.c_int64)],
@@ -190,6 +193,15 @@ def lbm_get_tiling(h):
 
 def lbm_set_tiling(h, bx: int, rows: int):
     return _check(_lib.lbm_set_tiling(h, int(bx), int(rows)), "lbm_set_tiling")
+
+
+def lbm_autotune(h, trials: int = 3):
+    k, bx, rows = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    ms = ctypes.c_double()
+    _check(_lib.lbm_autotune(h, int(trials), ctypes.byref(k), ctypes.byref(bx),
+                             ctypes.byref(rows), ctypes.byref(ms)), "lbm_autotune")
+    return {"kernel": int(k.value), "bx": int(bx.value), "rows": int(rows.value),
+            "ms": float(ms.value)}
 
 
 def lbm_set_kernel(h, variant: int):
@@ -331,6 +343,9 @@ class Sim:
 
     def set_tiling(self, bx, rows):
         lbm_set_tiling(self.h, bx, rows)
+
+    def autotune(self, trials=3):
+        return lbm_autotune(self.h, trials)
 
     def set_kernel(self, variant):
         lbm_set_kernel(self.h, variant)

@@ -297,3 +297,21 @@ def test_kernel_variants_agree_fp32(L):
     s = L.Sim(W.base_case(30, 8), np.zeros((8, 30)), None, precision="f32")
     with pytest.raises(L.LbmError):
         s.set_kernel(2)          # 30 is not a multiple of 4
+
+
+def test_autotune_keeps_state_and_parity(L):
+    case, phi0, u0, _, _ = W.two_droplets(noise=1e-3)
+    o = oracle.Oracle(case, phi0, u0).step(30)
+    s = L.Sim(case, phi0, u0, precision="f64")
+    s.step(10)
+    before = s.get_state(0)
+    best = s.autotune(1)
+    assert best["kernel"] in (1, 2) and best["bx"] in (32, 64, 128) and best["ms"] > 0
+    assert s.tiling()[:2] == (best["bx"], best["rows"]) and s.kernel() == best["kernel"]
+    after = s.get_state(0)
+    assert after[3] == before[3] == 10
+    for x, y in zip(before[:3], after[:3]):
+        assert np.array_equal(x, y)
+    s.step(20)
+    f, g, j, t = s.get_state(0)
+    assert maxdiff(f, o.f) <= TOL64 and maxdiff(g, o.g) <= TOL64 and maxdiff(j, o.j) <= TOL64
