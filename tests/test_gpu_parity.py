@@ -315,3 +315,17 @@ def test_autotune_keeps_state_and_parity(L):
     s.step(20)
     f, g, j, t = s.get_state(0)
     assert maxdiff(f, o.f) <= TOL64 and maxdiff(g, o.g) <= TOL64 and maxdiff(j, o.j) <= TOL64
+
+
+@pytest.mark.parametrize("ratio", [1.0, 3.0, 10.0])
+def test_translating_droplet_fp32(L, ratio):
+    # FP32 storage and arithmetic against the FP64 oracle: phi to 1e-5 after
+    # 100 steps for a droplet moving at 0.02 lu/step, density ratio 1..10
+    case = W.base_case(96, 80, rho_l=ratio, tau_f_l=1.0, tau_f_g=1.0)
+    phi0 = W.tanh_disc(96, 80, 40.0, 37.0, 15.0, 4.0, periodic=True)
+    u0 = np.zeros((2, 80, 96))
+    u0[0], u0[1] = 0.016, -0.012
+    o, s = run_pair(L, case, phi0, u0, 100, "f32")
+    err = maxdiff(s.fields(0)[0], o.fields()[0])
+    print(f"ratio {ratio}: max |phi_f32 - phi_oracle| = {err:.3e}")
+    assert err <= TOL32_PHI
