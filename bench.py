@@ -159,7 +159,7 @@ def measured_peaks():
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2505_10899_gb300", "csrc")
-    for name in ("lbm_kernels.cuh", "lbm_layout.h", "kern_impl.cuh"):
+    for name in ("lbm_kernels_tma.cuh", "lbm_node.cuh", "lbm_tma.cuh", "lbm_layout.h"):
         h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()[:16]
 

@@ -168,8 +168,9 @@ __global__ void __launch_bounds__(BX) volume_partial(const CaseDev<T>* __restric
   }
 }
 
-// Phase volumes, pass 2: one warp per case sums its items' partials in
-// item order (deterministic), lane r holding region r.
+// Phase volumes, pass 2: one warp per case.  For each region, lane l sums
+// the partials of items l, l+32, ... in order, then the lanes are combined
+// by a fixed shuffle tree: the result does not depend on timing.
 template <typename T>
 __global__ void volume_final(const CaseDev<T>* __restrict__ cases, int ncases,
                              const double* __restrict__ part, double* __restrict__ out) {
@@ -177,10 +178,13 @@ __global__ void volume_final(const CaseDev<T>* __restrict__ cases, int ncases,
   const int lane = threadIdx.x & 31;
   if (c >= ncases) return;
   const CaseDev<T>& cd = cases[c];
-  if (lane >= cd.nregions) return;
-  double v = 0.0;
-  for (int b = cd.item_begin; b < cd.item_end; ++b) v += part[(int64_t)b * kMaxRegions + lane];
-  out[cd.vol_base + lane] = v;
+  for (int r = 0; r < cd.nregions; ++r) {
+    double v = 0.0;
+    for (int b = cd.item_begin + lane; b < cd.item_end; b += 32)
+      v += part[(int64_t)b * kMaxRegions + r];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[cd.vol_base + r] = v;
+  }
 }
 
 // Step clock: t += n after a group of steps (read by the vortex flow).
