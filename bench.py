@@ -343,9 +343,19 @@ def run_e2e(args, cases, phis, us, dev, K):
 
 
 def run_extras(args, cases, dev):
-    """Secondary numbers: FP64 on a slice of the batch; FP32 vs FP64 phi error."""
+    """Secondary numbers: FP64 on a slice of the batch; FP32 vs FP64 on the
+    two-droplet case; the single-vortex period (256^2, T = 16384 steps) in
+    FP32 and FP64 with its shape error and volume drift."""
     import torch
     from paper_2505_10899_gb300 import lbm
+
+    def timed(sim, n):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(sim.stream)
+        sim.step(n)
+        b.record(sim.stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b)
 
     out = {}
     sub = cases[:64]
@@ -353,27 +363,39 @@ def run_extras(args, cases, dev):
     phis, us = host_inputs(sub)
     for prec in ("f64", "f32"):
         s = lbm.Sim(sub, phis, us, precision=prec)
+        s.autotune(1)
         s.step(3)
         torch.cuda.synchronize(dev)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        n = 20
-        a.record(s.stream)
-        s.step(n)
-        b.record(s.stream)
-        torch.cuda.synchronize(dev)
-        ms = a.elapsed_time(b)
-        out[f"{prec}_mlups_first64cases"] = round(nodes * n / (ms * 1e-3) / 1e6, 1)
+        ms = timed(s, 20)
+        out[f"{prec}_mlups_first64cases"] = round(nodes * 20 / (ms * 1e-3) / 1e6, 1)
         s.close()
-    # accuracy: FP32 vs FP64 after 200 steps on case 0
-    c0 = [cases[0]]
-    p0, u0 = host_inputs(c0)
+    # FP32 vs FP64 on the two-droplet case (128x64, 100 steps)
+    case, phi0, u0, _, _ = W.two_droplets(noise=1e-3)
     res = {}
     for prec in ("f32", "f64"):
-        s = lbm.Sim(c0, p0, u0, precision=prec)
-        s.step(200)
+        s = lbm.Sim(case, phi0, u0, precision=prec)
+        s.step(100)
         res[prec] = s.fields(0)[0]
         s.close()
-    out["phi_maxdiff_f32_vs_f64_case0_200steps"] = float(np.abs(res["f32"] - res["f64"]).max())
+    out["two_droplets_phi_maxdiff_f32_vs_f64_100steps"] = float(
+        np.abs(res["f32"] - res["f64"]).max())
+    # single vortex, one full period
+    vcase, vphi0, _ = W.single_vortex(n=256, W=3.0, U=0.02, T=16384)
+    vort = {"grid": "256x256", "period_steps": 16384}
+    fin = {}
+    for prec in ("f32", "f64"):
+        s = lbm.Sim(vcase, vphi0, None, precision=prec)
+        s.autotune(1)
+        v0 = s.volume()[0]
+        ms = timed(s, 16384)
+        phi = s.fields(0)[0]
+        fin[prec] = phi
+        vort[f"{prec}_mlups"] = round(256 * 256 * 16384 / (ms * 1e-3) / 1e6, 1)
+        vort[f"{prec}_shape_error"] = float(np.abs(phi - vphi0).sum() / vphi0.sum())
+        vort[f"{prec}_volume_drift"] = float(s.volume()[0] / v0 - 1.0)
+        s.close()
+    vort["phi_maxdiff_f32_vs_f64"] = float(np.abs(fin["f32"] - fin["f64"]).max())
+    out["single_vortex"] = vort
     return out
 
 
