@@ -79,6 +79,19 @@ def dist_setup(args):
     return ws, rank, local, pg
 
 
+def max_over_ranks(pg, value, device):
+    """Max of a per-rank scalar over all ranks (timing plumbing only)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world_size, nodes_per_rank, steps, t_max_ms):
+    """Weak scaling: every rank updates its own nodes each step."""
+    return world_size * nodes_per_rank * steps / (t_max_ms * 1e-3) / 1e6
+
+
 def rank_cases(args, rank):
     """Each rank owns an independent batch (seeded by rank)."""
     return W.batched_droplets(args.ncases, seed=args.seed + 7919 * rank)
@@ -233,12 +246,8 @@ def run_ours(args):
         vend = vol.clone().cpu().numpy()
         drift = float(np.max(np.abs(vend / v0.cpu().numpy() - 1.0)))
 
-    t_max = total_ms
-    if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ws * nodes * K / (t_max * 1e-3) / 1e6
+    t_max = max_over_ranks(pg, total_ms, dev) if pg else total_ms
+    value = whole_job_mlups(ws, nodes, K, t_max)
 
     # kernel duration: each per-step event pair brackets the step kernel plus
     # the volume finalisation and clock kernels (a few microseconds)
