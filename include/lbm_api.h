@@ -208,8 +208,47 @@ int lbm_load(lbm_handle* h, const void* h_buf, size_t bytes);
  * LBM_OK, LBM_ERR_NONFINITE or LBM_ERR_CUDA.  Clears the flags. */
 int lbm_status(lbm_handle* h);
 
-/* Adjoint of the coupled step (not built): returns LBM_ERR_UNIMPLEMENTED. */
+/* Device snapshots of the state of case c, for checkpointed recomputation:
+ * [f*: 9 planes][g*: 9 planes][phi*u: 2 planes], each nx*ny elements of the
+ * device precision, in the pull layout (plane i, position x holds the
+ * post-collision value that streams to x + c_i; f planes are zero in vortex
+ * mode).  lbm_restore writes such a buffer back as the current state; the
+ * step index is set separately with lbm_set_time.  Asynchronous. */
+size_t lbm_snapshot_bytes(const lbm_handle* h, int32_t c);
+int lbm_snapshot(lbm_handle* h, int32_t c, void* d_buf);
+int lbm_restore(lbm_handle* h, int32_t c, const void* d_buf);
+int lbm_set_time(lbm_handle* h, int64_t t);
+
+/* Reverse mode (discrete adjoint of the coupled step; FP64, single-case
+ * handles).  An adjoint state has the snapshot layout above in FP64
+ * (20 planes of nx*ny doubles): the derivative of a scalar objective with
+ * respect to each stored value.
+ *   lbm_adjoint_attach: device FP64 scratch of lbm_adjoint_workspace_bytes()
+ *     bytes (256-byte aligned, caller-owned, outlives the handle).
+ *   lbm_adjoint_seed_phi: adjoint state of an objective that depends on the
+ *     current phi only, from its field derivative d_dphi [ny][nx]
+ *     (phi = sum of the pulled g, Eq. 35).
+ *   lbm_adjoint_step: the handle must hold the state S_t at step index t;
+ *     given the adjoint of S_{t+1} (d_adj_in), writes the adjoint of S_t
+ *     (d_adj_out, a different buffer) through the transposed Jacobian of one
+ *     step (Eqs. 20-37 as computed by lbm_step), and adds to h_param_grads[4]
+ *     (may be NULL) the derivatives with respect to (sigma, tau_g, lambda,
+ *     tau_f); the tau_f entry is zero when tau_f varies with phi or in vortex
+ *     mode.  The state is not modified.  At the clip of Eq. 37 and where
+ *     |grad psi| = 0 the derivative of the branch taken is used.
+ *   lbm_adjoint_init: adjoint of the initial-state map of lbm_init: given the
+ *     adjoint of S_0, writes d_adj_phi0 [ny][nx] and adds the sigma and lambda
+ *     derivatives; d_phi0 [ny][nx] and d_u0 ([2][ny][nx] or NULL) are the
+ *     device copies of the initial fields.
+ * Synchronise when h_param_grads is non-NULL.  Errors: LBM_ERR_ARG (batch,
+ * FP32 handle, null buffers), LBM_ERR_WORKSPACE (no scratch), LBM_ERR_CUDA. */
+size_t lbm_adjoint_workspace_bytes(const lbm_handle* h);
+int lbm_adjoint_attach(lbm_handle* h, void* d_scratch, size_t bytes);
+int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, double* d_adj_state);
 int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out,
+                     double* h_param_grads);
+int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
+                     const void* d_adj_state, double* d_adj_phi0,
                      double* h_param_grads);
 
 /* Allocation-free phase volumes, for callers that cannot allocate device

@@ -1,0 +1,132 @@
+"""Reverse mode of the coupled step for PyTorch: checkpointed recomputation
+around the library's discrete adjoint (lbm_adjoint_step / lbm_adjoint_init).
+
+``coupled_run(phi0, theta, case, nsteps, ckpt_every)`` advances one FP64 case
+and returns phi at the final step as a CUDA tensor; it is differentiable with
+respect to the initial field phi0 and theta = (sigma, tau_g, lambda, tau_f).
+The backward pass restores a snapshot every ``ckpt_every`` steps, recomputes
+the states of that segment on the GPU, and runs the adjoint steps backwards.
+All arithmetic runs in the CUDA library; torch holds the device buffers.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import lbm
+
+
+class AdjointSim:
+    """One FP64 case with device snapshots and reverse-mode scratch."""
+
+    def __init__(self, case, phi0, u0=None):
+        self.case = dict(case)
+        self.sim = lbm.Sim(case, phi0, u0, precision="f64")
+        self.h = self.sim.h
+        self.dev = self.sim.device
+        ny, nx = case["ny"], case["nx"]
+        self.shape = (ny, nx)
+        nb = lbm.lbm_adjoint_workspace_bytes(self.h)
+        self._scratch = torch.empty(nb + 256, dtype=torch.uint8, device=self.dev)
+        ptr = (self._scratch.data_ptr() + 255) // 256 * 256
+        lbm.lbm_adjoint_attach(self.h, ptr, nb)
+        self.phi0 = torch.as_tensor(np.ascontiguousarray(phi0), dtype=torch.float64,
+                                    device=self.dev)
+        self.u0 = None if u0 is None else torch.as_tensor(np.ascontiguousarray(u0),
+                                                          dtype=torch.float64, device=self.dev)
+
+    def new_state(self):
+        return torch.zeros((20,) + self.shape, dtype=torch.float64, device=self.dev)
+
+    def snapshot(self):
+        buf = self.new_state()
+        lbm.lbm_snapshot(self.h, 0, buf.data_ptr())
+        return buf
+
+    def restore(self, buf, t):
+        lbm.lbm_restore(self.h, 0, buf.data_ptr())
+        lbm.lbm_set_time(self.h, int(t))
+
+    def step(self, n=1):
+        lbm.lbm_step(self.h, n)
+
+    @property
+    def t(self):
+        return lbm.lbm_time(self.h)
+
+    def phi(self):
+        return torch.as_tensor(self.sim.fields(0)[0], device=self.dev)
+
+    def seed_phi(self, dphi):
+        adj = self.new_state()
+        dphi = dphi.to(device=self.dev, dtype=torch.float64).contiguous()
+        lbm.lbm_adjoint_seed_phi(self.h, dphi.data_ptr(), adj.data_ptr())
+        return adj
+
+    def vjp_step(self, adj_in, grads):
+        adj_out = self.new_state()
+        rc = lbm.lbm_adjoint_step(self.h, adj_in.data_ptr(), adj_out.data_ptr(), grads)
+        if rc != lbm.LBM_OK:
+            raise lbm.LbmError(rc, "lbm_adjoint_step", lbm.lib().lbm_last_error().decode())
+        return adj_out
+
+    def vjp_init(self, adj_state, grads):
+        out = torch.zeros(self.shape, dtype=torch.float64, device=self.dev)
+        lbm.lbm_adjoint_init(self.h, self.phi0.data_ptr(),
+                             0 if self.u0 is None else self.u0.data_ptr(),
+                             adj_state.data_ptr(), out.data_ptr(), grads)
+        return out
+
+    def close(self):
+        self.sim.close()
+
+
+def case_with(case, theta):
+    c = dict(case)
+    c["sigma"], c["tau_g"], c["lambda"] = float(theta[0]), float(theta[1]), float(theta[2])
+    c["tau_f_l"] = c["tau_f_g"] = float(theta[3])
+    return c
+
+
+class CoupledRun(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, phi0, theta, case, nsteps, ckpt_every, u0):
+        th = theta.detach().cpu().numpy().astype(np.float64)
+        asim = AdjointSim(case_with(case, th), phi0.detach().cpu().numpy(), u0)
+        ckpts = {0: asim.snapshot()}
+        for t in range(1, nsteps + 1):
+            asim.step(1)
+            if t % ckpt_every == 0 and t < nsteps:
+                ckpts[t] = asim.snapshot()
+        phiT = asim.phi()
+        ctx.asim, ctx.ckpts, ctx.nsteps, ctx.k = asim, ckpts, nsteps, ckpt_every
+        ctx.theta_dtype, ctx.theta_device = theta.dtype, theta.device
+        return phiT
+
+    @staticmethod
+    def backward(ctx, grad_phiT):
+        asim, nsteps, k = ctx.asim, ctx.nsteps, ctx.k
+        grads = np.zeros(4)
+        adj = asim.seed_phi(grad_phiT)
+        seg_starts = sorted(ctx.ckpts)
+        for t0 in reversed(seg_starts):
+            t1 = min(t0 + k, nsteps)
+            # recompute the states of the segment [t0, t1)
+            asim.restore(ctx.ckpts[t0], t0)
+            states = {t0: ctx.ckpts[t0]}
+            for t in range(t0 + 1, t1):
+                asim.step(1)
+                states[t] = asim.snapshot()
+            for t in reversed(range(t0, t1)):
+                asim.restore(states[t], t)
+                adj = asim.vjp_step(adj, grads)
+        asim.restore(ctx.ckpts[0], 0)
+        dphi0 = asim.vjp_init(adj, grads)
+        asim.close()
+        gtheta = torch.as_tensor(grads, dtype=ctx.theta_dtype, device=ctx.theta_device)
+        return dphi0, gtheta, None, None, None, None
+
+
+def coupled_run(phi0, theta, case, nsteps, ckpt_every=16, u0=None):
+    """phi after nsteps coupled steps, differentiable in phi0 and theta."""
+    return CoupledRun.apply(phi0, theta, case, int(nsteps), int(ckpt_every), u0)

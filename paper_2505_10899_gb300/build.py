@@ -19,7 +19,7 @@ LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 SO_NAME = "liblbm_gb300.so"
 SO_PATH = os.path.join(LIBDIR, SO_NAME)
-SOURCES = ["kern_f32.cu", "kern_f64.cu", "lbm_api.cu", "lbm_noalloc.cu"]
+SOURCES = ["kern_f32.cu", "kern_f64.cu", "lbm_api.cu", "lbm_adjoint.cu", "lbm_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,705 @@
+// Reverse mode of the coupled step: vector-Jacobian products of one time step
+// and of the initial-state map, hand-written for the per-node arithmetic of
+// lbm_node.cuh (FP64, single-case handles).
+//
+// State S_t = the three source buffers of the pull layout: post-collision
+// populations f*, g* (9 planes each, value i of node x at position x) and
+// phi*u (2 planes).  One step maps S_t to S_{t+1}; lbm_adjoint_step maps an
+// adjoint lambda_{t+1} (same layout, FP64, 20 planes of nx*ny) to lambda_t and
+// accumulates the parameter gradients.  The sweep runs in three kernels:
+//   ad_phase:  phi = sum of pulled g (Eq. 35) and psi (Eq. 37) of S_t;
+//   ad_node:   at every node, recompute the collision, then apply its
+//              transposed Jacobian to the output adjoints: the adjoints of the
+//              node's pulled inputs go to their source positions (the
+//              transpose of the pull), the adjoints of the 9 phi and 8 psi
+//              stencil values go to scratch;
+//   ad_gather: every node sums the stencil adjoints that refer to its phi and
+//              psi, and adds the total to the adjoints of its 9 pulled g.
+// The clip of Eq. 37 and the normalisation of grad(psi) use the derivative
+// of the branch taken (0 outside (0,1) and where |grad psi| = 0).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "lbm_handle.h"
+#include "lbm_node.cuh"
+
+namespace lbmk {
+int set_last_error(int code, const char* msg);
+}  // namespace lbmk
+
+using lbmk::CaseDev;
+using lbmk::Mom;
+using lbmk::Phys;
+
+namespace {
+
+constexpr int kAdThreads = 256;
+constexpr int kAdBlocks = 152 * 8;
+constexpr int kNParam = 5;  // beta4, kappa, lambda, tau_g (via s3,s5), tau_f (via s7,s8)
+
+__device__ __constant__ int kAX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__device__ __constant__ int kAY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__device__ __constant__ double kAW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                                         1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+int fail(int code, const std::string& m) { return lbmk::set_last_error(code, m.c_str()); }
+
+__device__ __forceinline__ int64_t shift(int x, int y, int dx, int dy, int nx, int ny) {
+  x += dx;
+  y += dy;
+  x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+  y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+  return (int64_t)y * nx + x;
+}
+
+struct AdArgs {
+  const double* fA;  // f* source buffer (9 planes, stride P), null in vortex mode
+  const double* gA;  // g* source buffer
+  const double* JA;  // phi*u source buffer (2 planes)
+  int64_t P;         // plane stride of the state buffers
+  int nx, ny;
+  const double* phi;  // [n] scratch
+  const double* psi;  // [n] scratch
+  const double* ain;  // [20][n] adjoint of S_{t+1}
+  double* aout;       // [20][n] adjoint of S_t
+  double* lP;         // [9][n] scratch: adjoint of phi(x + c_j) used at node x
+  double* lQ;         // [8][n] scratch: adjoint of psi(x + c_j), j = 1..8
+  double* part;       // [gridDim][kNParam]
+  Phys<double> ph;
+  double rho_g, drho, mu_g, dmu, sD7, hD7, s7;
+  int var_tau, coupled;
+  double ct;    // vortex: U cos(pi t / T)
+  double invW;  // 1/W: d(lambda/W)/d(lambda)
+};
+
+// phi (Eq. 35, pulled sum in the forward order) and psi = ln(a/b) (Eq. 37).
+__global__ void ad_phase(const double* __restrict__ gA, int64_t P, int nx, int ny, double xi,
+                         double* __restrict__ phi, double* __restrict__ psi) {
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    double G[9];
+    for (int i = 0; i < 9; ++i) G[i] = gA[i * P + shift(x, y, -kAX[i], -kAY[i], nx, ny)];
+    const double p = lbmk::sum9(G);
+    phi[k] = p;
+    psi[k] = lbmk::psi_of(p, xi);
+  }
+}
+
+__global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
+  __shared__ double red[kAdThreads / 32][kNParam];
+  const int nx = a.nx, ny = a.ny;
+  const int64_t n = (int64_t)nx * ny, P = a.P;
+  const Phys<double>& ph = a.ph;
+  double gacc[kNParam] = {0, 0, 0, 0, 0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    int64_t src[9];
+    double F[9], G[9];
+    for (int i = 0; i < 9; ++i) {
+      src[i] = shift(x, y, -kAX[i], -kAY[i], nx, ny);
+      G[i] = a.gA[i * P + src[i]];
+      F[i] = a.coupled ? a.fA[i * P + src[i]] : 0.0;
+    }
+    const double jpx = a.JA[k], jpy = a.JA[P + k];
+    double Pv[9], Qv[9];
+    for (int j = 0; j < 9; ++j) {
+      const int64_t s = shift(x, y, kAX[j], kAY[j], nx, ny);
+      Pv[j] = a.phi[s];
+      Qv[j] = a.psi[s];
+    }
+    // ---------------- forward recompute (as node_update) ----------------
+    const double phi = Pv[0];
+    const double gpx = (1.0 / 3.0) * (Pv[1] - Pv[3]) + (1.0 / 12.0) * ((Pv[5] - Pv[6]) + (Pv[8] - Pv[7]));
+    const double gpy = (1.0 / 3.0) * (Pv[2] - Pv[4]) + (1.0 / 12.0) * ((Pv[5] - Pv[8]) + (Pv[6] - Pv[7]));
+    const double lap = (2.0 / 3.0) * (((Pv[1] + Pv[3]) + (Pv[2] + Pv[4])) - 4.0 * phi) +
+                       (1.0 / 6.0) * (((Pv[5] + Pv[6]) + (Pv[8] + Pv[7])) - 4.0 * phi);
+    const double qx = 4.0 * (Qv[1] - Qv[3]) + ((Qv[5] - Qv[6]) + (Qv[8] - Qv[7]));
+    const double qy = 4.0 * (Qv[2] - Qv[4]) + ((Qv[5] - Qv[8]) + (Qv[6] - Qv[7]));
+    const double poly = phi * (phi - 1.0) * (phi - 0.5);
+    const double mu = ph.beta4 * poly - ph.kappa * lap;
+    const double Fx = mu * gpx, Fy = mu * gpy;
+    double ux, uy;
+    double rho = 1.0, irho = 1.0, Rx = 0.0, Ry = 0.0, u2 = 0.0, mu_v = 0.0, s7 = a.s7;
+    double sD7 = a.sD7, hD7 = a.hD7;
+    Mom<double> mf{};
+    if (a.coupled) {
+      rho = a.rho_g + phi * a.drho;
+      irho = 1.0 / rho;
+      mf = lbmk::moments(F);
+      ux = (mf.m3 + 0.5 * Fx) * irho;
+      uy = (mf.m5 + 0.5 * Fy) * irho;
+      Rx = a.drho * gpx;
+      Ry = a.drho * gpy;
+      u2 = ux * ux + uy * uy;
+      if (a.var_tau) {
+        mu_v = a.mu_g + phi * a.dmu;
+        const double tau = 3.0 * mu_v * irho + 0.5;
+        s7 = 1.0 / tau;
+        sD7 = -0.25 * s7;
+        hD7 = 0.25 - 0.125 * s7;
+      }
+    } else {
+      double sx, cx, sy, cy;
+      sincospi((x + 0.5) / nx, &sx, &cx);
+      sincospi((y + 0.5) / ny, &sy, &cy);
+      ux = -a.ct * (sx * sx) * (2.0 * sy * cy);
+      uy = a.ct * (sy * sy) * (2.0 * sx * cx);
+    }
+    const double Jx = phi * ux, Jy = phi * uy;
+    const double dJx = Jx - jpx, dJy = Jy - jpy;
+    const double pc = fmin(fmax(phi, 0.0), 1.0);
+    const double ta = pc + ph.xi, tb = (1.0 - pc) + ph.xi;
+    const double q2 = qx * qx + qy * qy;
+    const double iq = (q2 > 0.0) ? 1.0 / sqrt(q2) : 0.0;
+    const double sh = ph.lamW * ph.tfac * ta * tb * iq;
+    const double Vx = 3.0 * dJx + sh * qx, Vy = 3.0 * dJy + sh * qy;
+    const Mom<double> mg = lbmk::moments(G);
+
+    // ---------------- reverse ----------------
+    double aF[9], aG[9];
+    for (int i = 0; i < 9; ++i) {
+      aF[i] = a.ain[i * n + k];
+      aG[i] = a.ain[(9 + i) * n + k];
+    }
+    const double aJx = a.ain[18 * n + k], aJy = a.ain[19 * n + k];
+
+    double lphi = 0.0, lmu = 0.0, lgpx = 0.0, lgpy = 0.0, llap = 0.0, lqx = 0.0, lqy = 0.0;
+    double lux = 0.0, luy = 0.0;
+    // g*_0 = phi - sum_{i>=1} g*'_i; g*' = G + M^T e (e0 = 0)
+    lphi += aG[0];
+    double aGp[9];
+    aGp[0] = 0.0;
+    for (int i = 1; i < 9; ++i) aGp[i] = aG[i] - aG[0];
+    double lG[9];
+    for (int i = 0; i < 9; ++i) lG[i] = aGp[i];
+    const Mom<double> le = lbmk::moments(aGp);  // lambda_e = M lambda_g*'
+    double lmg[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double lLam = 0.0, lJx = 0.0, lJy = 0.0, lVx = 0.0, lVy = 0.0;
+    // e1, e2
+    lmg[1] += ph.gsD[1] * le.m1;
+    lLam += -2.0 * ph.gsD[1] * le.m1;
+    lphi += 4.0 * ph.gsD[1] * le.m1;
+    lmg[2] += ph.gsD[2] * le.m2;
+    lphi += -4.0 * ph.gsD[2] * le.m2;
+    lLam += 3.0 * ph.gsD[2] * le.m2;
+    // e3..e6
+    lmg[3] += ph.gsD[3] * le.m3;
+    lJx += -ph.gsD[3] * le.m3;
+    lVx += ph.ghD3[3] * le.m3;
+    lmg[4] += ph.gsD[4] * le.m4;
+    lJx += ph.gsD[4] * le.m4;
+    lVx += -ph.ghD3[4] * le.m4;
+    lmg[5] += ph.gsD[5] * le.m5;
+    lJy += -ph.gsD[5] * le.m5;
+    lVy += ph.ghD3[5] * le.m5;
+    lmg[6] += ph.gsD[6] * le.m6;
+    lJy += ph.gsD[6] * le.m6;
+    lVy += -ph.ghD3[6] * le.m6;
+    lmg[7] += ph.gsD[7] * le.m7;
+    lmg[8] += ph.gsD[8] * le.m8;
+    {  // tau_g: s3 = s5 = 1/tau_g; gsD = -s/6, ghD3 = (1 - s/2)/18
+      const double lgs = (mg.m3 - Jx) * le.m3 + (mg.m5 - Jy) * le.m5;
+      const double lgh = Vx * le.m3 + Vy * le.m5;
+      const double ls = -lgs / 6.0 - lgh / 36.0;
+      const double sg = -6.0 * ph.gsD[3];  // = 1/tau_g
+      gacc[3] += -sg * sg * ls;
+    }
+    // mg = M G
+    lbmk::add_back(lG, lmg[0], lmg[1], lmg[2], lmg[3], lmg[4], lmg[5], lmg[6], lmg[7], lmg[8]);
+    // Lam = mu + lambda phi
+    lmu += lLam;
+    lphi += ph.lambda * lLam;
+    gacc[2] += phi * lLam;
+    // V = 3 dJ + sh q
+    const double ldJx = 3.0 * lVx, ldJy = 3.0 * lVy;
+    const double lsh = qx * lVx + qy * lVy;
+    lqx += sh * lVx;
+    lqy += sh * lVy;
+    // sh = lamW tfac ta tb iq
+    const double c0 = ph.lamW * ph.tfac;
+    const double lta = c0 * tb * iq * lsh, ltb = c0 * ta * iq * lsh, liq = c0 * ta * tb * lsh;
+    gacc[2] += ph.tfac * ta * tb * iq * lsh * a.invW;  // lamW = lambda / W
+    if (q2 > 0.0) {
+      const double lq2 = -0.5 * iq * iq * iq * liq;
+      lqx += 2.0 * qx * lq2;
+      lqy += 2.0 * qy * lq2;
+    }
+    if (phi > 0.0 && phi < 1.0) lphi += lta - ltb;
+    // dJ = J - J_prev; J also stored
+    lJx += ldJx + aJx;
+    lJy += ldJy + aJy;
+    const double ljpx = -ldJx, ljpy = -ldJy;
+    // J = phi u
+    lphi += ux * lJx + uy * lJy;
+    lux += phi * lJx;
+    luy += phi * lJy;
+
+    double lF[9];
+    for (int i = 0; i < 9; ++i) lF[i] = 0.0;
+    if (a.coupled) {
+      for (int i = 0; i < 9; ++i) lF[i] = aF[i];
+      const Mom<double> ld = lbmk::moments(aF);  // lambda_d = M lambda_f*
+      double lm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+      double lp = 0.0, lru2 = 0.0, luR = 0.0, ljx = 0.0, ljy = 0.0, lFx = 0.0, lFy = 0.0;
+      double lrho = 0.0, lRx = 0.0, lRy = 0.0, lsD7 = 0.0, lhD7 = 0.0, lirho = 0.0, lu2 = 0.0;
+      const double p =
+          0.6 * ((mf.m0 - F[0]) + 0.5 * (ux * Rx + uy * Ry) - (2.0 / 3.0) * rho * u2);
+      const double jx = rho * ux;
+      // d0..d6
+      lm[0] += ph.fsD[0] * ld.m0;
+      luR += ph.fhD[0] * ld.m0;
+      lm[1] += ph.fsD[1] * ld.m1;
+      lp += -6.0 * ph.fsD[1] * ld.m1;
+      lru2 += -3.0 * ph.fsD[1] * ld.m1;
+      lm[2] += ph.fsD[2] * ld.m2;
+      lp += 9.0 * ph.fsD[2] * ld.m2;
+      lru2 += 3.0 * ph.fsD[2] * ld.m2;
+      luR += -ph.fhD[2] * ld.m2;
+      lm[3] += ph.fsD[3] * ld.m3;
+      ljx += -ph.fsD[3] * ld.m3;
+      lFx += ph.fhD[3] * ld.m3;
+      lm[4] += ph.fsD[4] * ld.m4;
+      ljx += ph.fsD[4] * ld.m4;
+      lFx += -ph.fhD[4] * ld.m4;
+      lm[5] += ph.fsD[5] * ld.m5;
+      ljy += -ph.fsD[5] * ld.m5;
+      lFy += ph.fhD[5] * ld.m5;
+      lm[6] += ph.fsD[6] * ld.m6;
+      ljy += ph.fsD[6] * ld.m6;
+      lFy += -ph.fhD[6] * ld.m6;
+      // d7 = sD7 (m7 - rho(ux^2 - uy^2)) + hD7 (2/3)(ux Rx - uy Ry)
+      lm[7] += sD7 * ld.m7;
+      lrho += -sD7 * (ux * ux - uy * uy) * ld.m7;
+      lux += -2.0 * sD7 * rho * ux * ld.m7 + hD7 * (2.0 / 3.0) * Rx * ld.m7;
+      luy += 2.0 * sD7 * rho * uy * ld.m7 - hD7 * (2.0 / 3.0) * Ry * ld.m7;
+      lRx += hD7 * (2.0 / 3.0) * ux * ld.m7;
+      lRy += -hD7 * (2.0 / 3.0) * uy * ld.m7;
+      lsD7 += (mf.m7 - rho * (ux * ux - uy * uy)) * ld.m7;
+      lhD7 += (2.0 / 3.0) * (ux * Rx - uy * Ry) * ld.m7;
+      // d8 = sD7 (m8 - jx uy) + hD7 (1/3)(ux Ry + uy Rx)
+      lm[8] += sD7 * ld.m8;
+      ljx += -sD7 * uy * ld.m8;
+      luy += -sD7 * jx * ld.m8 + hD7 * (1.0 / 3.0) * Rx * ld.m8;
+      lux += hD7 * (1.0 / 3.0) * Ry * ld.m8;
+      lRy += hD7 * (1.0 / 3.0) * ux * ld.m8;
+      lRx += hD7 * (1.0 / 3.0) * uy * ld.m8;
+      lsD7 += (mf.m8 - jx * uy) * ld.m8;
+      lhD7 += (1.0 / 3.0) * (ux * Ry + uy * Rx) * ld.m8;
+      // s7 (= s8): sD7 = -s7/4, hD7 = 1/4 - s7/8
+      const double ls7 = -0.25 * lsD7 - 0.125 * lhD7;
+      if (a.var_tau) {
+        const double ltau = -s7 * s7 * ls7;  // s7 = 1/tau
+        const double lmuv = 3.0 * irho * ltau;
+        lirho += 3.0 * mu_v * ltau;
+        lphi += a.dmu * lmuv;
+      } else {
+        gacc[4] += -s7 * s7 * ls7;  // s7 = 1/tau_f
+      }
+      // jx = rho ux, jy = rho uy
+      lrho += ux * ljx + uy * ljy;
+      lux += rho * ljx;
+      luy += rho * ljy;
+      // ru2 = rho u2
+      lrho += u2 * lru2;
+      lu2 += rho * lru2;
+      // p = 0.6((m0 - F0) + uR/2 - (2/3) rho u2)
+      lm[0] += 0.6 * lp;
+      lF[0] += -0.6 * lp;
+      luR += 0.3 * lp;
+      lrho += -0.4 * u2 * lp;
+      lu2 += -0.4 * rho * lp;
+      (void)p;
+      // u2, uR
+      lux += 2.0 * ux * lu2 + Rx * luR;
+      luy += 2.0 * uy * lu2 + Ry * luR;
+      lRx += ux * luR;
+      lRy += uy * luR;
+      // R = drho grad phi
+      lgpx += a.drho * lRx;
+      lgpy += a.drho * lRy;
+      // u = (m + F/2) irho
+      lm[3] += irho * lux;
+      lFx += 0.5 * irho * lux;
+      lirho += (mf.m3 + 0.5 * Fx) * lux;
+      lm[5] += irho * luy;
+      lFy += 0.5 * irho * luy;
+      lirho += (mf.m5 + 0.5 * Fy) * luy;
+      // m = M F
+      lbmk::add_back(lF, lm[0], lm[1], lm[2], lm[3], lm[4], lm[5], lm[6], lm[7], lm[8]);
+      // irho = 1/rho, rho = rho_g + phi drho
+      lrho += -irho * irho * lirho;
+      lphi += a.drho * lrho;
+      // F = mu grad phi
+      lmu += gpx * lFx + gpy * lFy;
+      lgpx += mu * lFx;
+      lgpy += mu * lFy;
+    }
+    // mu = beta4 poly - kappa lap
+    lphi += ph.beta4 * (3.0 * phi * phi - 3.0 * phi + 0.5) * lmu;
+    llap += -ph.kappa * lmu;
+    gacc[0] += poly * lmu;
+    gacc[1] += -lap * lmu;
+
+    // stencil adjoints (transpose of the difference forms above)
+    const double gx3 = lgpx / 3.0, gy3 = lgpy / 3.0, gx12 = lgpx / 12.0, gy12 = lgpy / 12.0;
+    const double la = (2.0 / 3.0) * llap, ld6 = llap / 6.0;
+    a.lP[0 * n + k] = -(10.0 / 3.0) * llap + lphi;
+    a.lP[1 * n + k] = gx3 + la;
+    a.lP[3 * n + k] = -gx3 + la;
+    a.lP[2 * n + k] = gy3 + la;
+    a.lP[4 * n + k] = -gy3 + la;
+    a.lP[5 * n + k] = gx12 + gy12 + ld6;
+    a.lP[6 * n + k] = -gx12 + gy12 + ld6;
+    a.lP[7 * n + k] = -gx12 - gy12 + ld6;
+    a.lP[8 * n + k] = gx12 - gy12 + ld6;
+    a.lQ[0 * n + k] = 4.0 * lqx;   // Q1
+    a.lQ[2 * n + k] = -4.0 * lqx;  // Q3
+    a.lQ[1 * n + k] = 4.0 * lqy;   // Q2
+    a.lQ[3 * n + k] = -4.0 * lqy;  // Q4
+    a.lQ[4 * n + k] = lqx + lqy;   // Q5
+    a.lQ[5 * n + k] = -lqx + lqy;  // Q6
+    a.lQ[6 * n + k] = -lqx - lqy;  // Q7
+    a.lQ[7 * n + k] = lqx - lqy;   // Q8
+
+    // transpose of the pull: adjoint of the source positions
+    for (int i = 0; i < 9; ++i) {
+      a.aout[i * n + src[i]] = lF[i];
+      a.aout[(9 + i) * n + src[i]] = lG[i];
+    }
+    a.aout[18 * n + k] = ljpx;
+    a.aout[19 * n + k] = ljpy;
+  }
+  // deterministic CTA reduction of the parameter partials
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < kNParam; ++q) {
+    double v = gacc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNParam) {
+    double v = 0.0;
+    for (int w = 0; w < kAdThreads / 32; ++w) v += red[w][threadIdx.x];
+    a.part[(int64_t)blockIdx.x * kNParam + threadIdx.x] = v;
+  }
+}
+
+// Sum the stencil adjoints referring to each node's phi and psi and add them
+// to the adjoints of the node's 9 pulled g (phi = sum g).
+__global__ void ad_gather(const double* __restrict__ phi, const double* __restrict__ lP,
+                          const double* __restrict__ lQ, int nx, int ny, double xi,
+                          double* __restrict__ aout) {
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    double sp = lP[k], sq = 0.0;
+    for (int j = 1; j < 9; ++j) {
+      const int64_t s = shift(x, y, -kAX[j], -kAY[j], nx, ny);  // node using phi(k) as P_j
+      sp += lP[j * n + s];
+      sq += lQ[(j - 1) * n + s];
+    }
+    const double p = phi[k];
+    double dpsi = 0.0;  // d ln(a/b) / d phi inside the clip
+    if (p > 0.0 && p < 1.0) dpsi = 1.0 / (p + xi) + 1.0 / ((1.0 - p) + xi);
+    const double tot = sp + dpsi * sq;
+    for (int i = 0; i < 9; ++i) aout[(9 + i) * n + shift(x, y, -kAX[i], -kAY[i], nx, ny)] += tot;
+  }
+}
+
+// Adjoint of the initial state map (local part): phi0 -> hbar0, g_eq, f_eq,
+// phi0 u0.  Writes the local phi0 adjoint and the adjoint of lap(phi0).
+struct AdInitArgs {
+  const double* phi0;
+  const double* u0;  // [2][n] or null
+  const double* ain;  // adjoint of S_0 [20][n]
+  double* lphi;       // [n]
+  double* llap;       // [n]
+  double* part;
+  int nx, ny;
+  Phys<double> ph;
+  double rho_g, drho;
+  int coupled, vortex;
+  double vU;
+};
+
+__global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs a) {
+  __shared__ double red[kAdThreads / 32][kNParam];
+  const int nx = a.nx, ny = a.ny;
+  const int64_t n = (int64_t)nx * ny;
+  const Phys<double>& ph = a.ph;
+  double gacc[kNParam] = {0, 0, 0, 0, 0};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    const double p = a.phi0[k];
+    double s_ax = 0.0, s_dg = 0.0;
+    for (int j = 1; j < 9; ++j) {
+      const double v = a.phi0[shift(x, y, kAX[j], kAY[j], nx, ny)];
+      if (j < 5) s_ax += v; else s_dg += v;
+    }
+    const double lap = (2.0 / 3.0) * (s_ax - 4.0 * p) + (1.0 / 6.0) * (s_dg - 4.0 * p);
+    const double poly = p * (p - 1.0) * (p - 0.5);
+    double ux = 0.0, uy = 0.0;
+    if (a.vortex) {
+      double sx, cx, sy, cy;
+      sincospi((x + 0.5) / nx, &sx, &cx);
+      sincospi((y + 0.5) / ny, &sy, &cy);
+      ux = -a.vU * sx * sx * (2.0 * sy * cy);
+      uy = a.vU * sy * sy * (2.0 * sx * cx);
+    } else if (a.u0) {
+      ux = a.u0[k];
+      uy = a.u0[n + k];
+    }
+    double lLam = 0.0, lphi = 0.0, lJx = a.ain[18 * n + k], lJy = a.ain[19 * n + k], lrho = 0.0;
+    const double u2 = ux * ux + uy * uy;
+    for (int i = 0; i < 9; ++i) {
+      const int64_t s = shift(x, y, -kAX[i], -kAY[i], nx, ny);
+      const double lg = a.ain[(9 + i) * n + s];
+      if (i == 0) {
+        lphi += lg;
+        lLam += (kAW[0] - 1.0) * lg;
+      } else {
+        lLam += kAW[i] * lg;
+        lJx += 3.0 * kAW[i] * kAX[i] * lg;
+        lJy += 3.0 * kAW[i] * kAY[i] * lg;
+      }
+      if (a.coupled) {
+        const double cu = kAX[i] * ux + kAY[i] * uy;
+        lrho += kAW[i] * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2) * a.ain[i * n + s];
+      }
+    }
+    lphi += ux * lJx + uy * lJy + a.drho * lrho;
+    const double lmu = lLam;
+    lphi += ph.lambda * lLam;
+    gacc[2] += p * lLam;
+    lphi += ph.beta4 * (3.0 * p * p - 3.0 * p + 0.5) * lmu;
+    gacc[0] += poly * lmu;
+    gacc[1] += -lap * lmu;
+    a.lphi[k] = lphi;
+    a.llap[k] = -ph.kappa * lmu;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < kNParam; ++q) {
+    double v = gacc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNParam) {
+    double v = 0.0;
+    for (int w = 0; w < kAdThreads / 32; ++w) v += red[w][threadIdx.x];
+    a.part[(int64_t)blockIdx.x * kNParam + threadIdx.x] = v;
+  }
+}
+
+// lambda_phi0(y) = local + sum_j w_lap_j * llap(y - c_j) - (10/3) llap(y)
+__global__ void ad_init_gather(const double* __restrict__ lphi, const double* __restrict__ llap,
+                               int nx, int ny, double* __restrict__ out) {
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    double v = lphi[k] - (10.0 / 3.0) * llap[k];
+    for (int j = 1; j < 9; ++j)
+      v += (j < 5 ? 2.0 / 3.0 : 1.0 / 6.0) * llap[shift(x, y, -kAX[j], -kAY[j], nx, ny)];
+    out[k] = v;
+  }
+}
+
+// The adjoint of phi = sum of pulled g, seeded from a field adjoint.
+__global__ void ad_seed_phi(const double* __restrict__ dphi, int nx, int ny,
+                            double* __restrict__ aout) {
+  const int64_t n = (int64_t)nx * ny;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 20 * n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t plane = k / n, node = k % n;
+    double v = 0.0;
+    if (plane >= 9 && plane < 18) {
+      // position node of plane i holds the value delivered to node + c_i
+      const int i = (int)plane - 9;
+      const int x = (int)(node % nx), y = (int)(node / nx);
+      v = dphi[shift(x, y, kAX[i], kAY[i], nx, ny)];
+    }
+    aout[k] = v;
+  }
+}
+
+__global__ void ad_sum_partials(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  const int q = threadIdx.x;
+  if (q >= kNParam) return;
+  double v = 0.0;
+  for (int b = 0; b < nb; ++b) v += part[(int64_t)b * kNParam + q];
+  out[q] = v;
+}
+
+// Scratch layout inside the caller's adjoint workspace (doubles).
+struct AdScratch {
+  double *phi, *psi, *lP, *lQ, *part, *sums;
+};
+
+AdScratch carve(lbm_handle* h) {
+  const int64_t n = (int64_t)h->params[0].nx * h->params[0].ny;
+  double* b = (double*)h->adj_ws;
+  AdScratch s;
+  s.phi = b;
+  s.psi = b + n;
+  s.lP = b + 2 * n;
+  s.lQ = b + 11 * n;
+  s.part = b + 19 * n;
+  s.sums = s.part + kAdBlocks * kNParam;
+  return s;
+}
+
+size_t scratch_bytes(int64_t n) { return (size_t)(19 * n + kAdBlocks * kNParam + 8) * sizeof(double); }
+
+int check_handle(lbm_handle* h, bool need_ws) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (h->ncases != 1) return fail(LBM_ERR_ARG, "reverse mode needs a single-case handle");
+  if (h->precision != LBM_F64) return fail(LBM_ERR_ARG, "reverse mode needs an FP64 handle");
+  if (need_ws && !h->adj_ws) return fail(LBM_ERR_WORKSPACE, "call lbm_adjoint_attach first");
+  return LBM_OK;
+}
+
+// Combine the raw partial sums into d/d(sigma, tau_g, lambda, tau_f).
+void to_param_grads(const lbm_params& p, const double raw[kNParam], double* out) {
+  out[0] += raw[0] * (48.0 / p.W) + raw[1] * (1.5 * p.W);  // beta4 = 48 sigma/W, kappa = 1.5 sigma W
+  out[1] += raw[3];
+  out[2] += raw[2];
+  out[3] += raw[4];
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_adjoint_workspace_bytes(const lbm_handle* h) {
+  if (!h || h->ncases != 1) return 0;
+  return scratch_bytes((int64_t)h->params[0].nx * h->params[0].ny);
+}
+
+int lbm_adjoint_attach(lbm_handle* h, void* d_scratch, size_t bytes) {
+  int rc = check_handle(h, false);
+  if (rc) return rc;
+  if (!d_scratch) return fail(LBM_ERR_WORKSPACE, "adjoint scratch is null");
+  if ((uintptr_t)d_scratch % 256) return fail(LBM_ERR_WORKSPACE, "adjoint scratch not 256-byte aligned");
+  if (bytes < lbm_adjoint_workspace_bytes(h)) return fail(LBM_ERR_WORKSPACE, "adjoint scratch too small");
+  h->adj_ws = (char*)d_scratch;
+  h->adj_ws_bytes = bytes;
+  return LBM_OK;
+}
+
+int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, double* d_adj_state) {
+  int rc = check_handle(h, false);
+  if (rc) return rc;
+  if (!d_dphi || !d_adj_state) return fail(LBM_ERR_ARG, "null pointer");
+  const lbm_params& p = h->params[0];
+  ad_seed_phi<<<kAdBlocks, kAdThreads, 0, h->stream>>>(d_dphi, p.nx, p.ny, d_adj_state);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, double* h_param_grads) {
+  int rc = check_handle(h, true);
+  if (rc) return rc;
+  if (!d_adj_in || !d_adj_out) return fail(LBM_ERR_ARG, "null adjoint buffer");
+  if (d_adj_in == d_adj_out) return fail(LBM_ERR_ARG, "d_adj_in and d_adj_out must differ");
+  const lbm_params& p = h->params[0];
+  const CaseDev<double>& cd = h->cd[0];
+  const bool coupled = h->flow == LBM_FLOW_COUPLED;
+  AdScratch s = carve(h);
+  ad_phase<<<kAdBlocks, kAdThreads, 0, h->stream>>>(cd.g[h->parity], cd.plane, p.nx, p.ny, p.xi,
+                                                    s.phi, s.psi);
+  AdArgs a{};
+  a.fA = coupled ? cd.f[h->parity] : nullptr;
+  a.gA = cd.g[h->parity];
+  a.JA = cd.J[h->parity];
+  a.P = cd.plane;
+  a.nx = p.nx;
+  a.ny = p.ny;
+  a.phi = s.phi;
+  a.psi = s.psi;
+  a.ain = (const double*)d_adj_in;
+  a.aout = (double*)d_adj_out;
+  a.lP = s.lP;
+  a.lQ = s.lQ;
+  a.part = s.part;
+  a.ph = h->pd;
+  a.rho_g = cd.rho_g;
+  a.drho = cd.drho;
+  a.mu_g = cd.mu_g;
+  a.dmu = cd.dmu;
+  a.sD7 = cd.sD7;
+  a.hD7 = cd.hD7;
+  a.s7 = 1.0 / p.tau_f_l;
+  a.var_tau = cd.var_tau;
+  a.coupled = coupled ? 1 : 0;
+  a.ct = coupled ? 0.0 : cospi((double)h->t / p.vortex_T) * p.vortex_U;
+  a.invW = 1.0 / p.W;
+  if (!coupled) {  // the f planes and the tau_f entry stay zero
+    cudaError_t e = cudaMemsetAsync(d_adj_out, 0, 9 * sizeof(double) * p.nx * (size_t)p.ny, h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  }
+  ad_node<<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
+  ad_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.lP, s.lQ, p.nx, p.ny, p.xi,
+                                                     (double*)d_adj_out);
+  ad_sum_partials<<<1, 32, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  if (h_param_grads) {
+    double raw[kNParam];
+    e = cudaMemcpyAsync(raw, s.sums, sizeof raw, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+    to_param_grads(p, raw, h_param_grads);
+  }
+  return LBM_OK;
+}
+
+int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
+                     const void* d_adj_state, double* d_adj_phi0, double* h_param_grads) {
+  int rc = check_handle(h, true);
+  if (rc) return rc;
+  if (!d_phi0 || !d_adj_state || !d_adj_phi0) return fail(LBM_ERR_ARG, "null pointer");
+  const lbm_params& p = h->params[0];
+  const CaseDev<double>& cd = h->cd[0];
+  AdScratch s = carve(h);
+  AdInitArgs a{};
+  a.phi0 = d_phi0;
+  a.u0 = d_u0;
+  a.ain = (const double*)d_adj_state;
+  a.lphi = s.phi;  // reuse scratch planes
+  a.llap = s.psi;
+  a.part = s.part;
+  a.nx = p.nx;
+  a.ny = p.ny;
+  a.ph = h->pd;
+  a.rho_g = cd.rho_g;
+  a.drho = cd.drho;
+  a.coupled = h->flow == LBM_FLOW_COUPLED;
+  a.vortex = h->flow == LBM_FLOW_VORTEX;
+  a.vU = p.vortex_U;
+  ad_init_local<<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
+  ad_init_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.psi, p.nx, p.ny, d_adj_phi0);
+  ad_sum_partials<<<1, 32, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  if (h_param_grads) {
+    double raw[kNParam];
+    e = cudaMemcpyAsync(raw, s.sums, sizeof raw, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+    to_param_grads(p, raw, h_param_grads);
+  }
+  return LBM_OK;
+}
+
+}  // extern "C"

@@ -13,12 +13,15 @@
 
 #include "../../include/lbm_api.h"
 #include "launch.h"
+#include "lbm_handle.h"
 #include "lbm_layout.h"
 
 using lbmk::CaseDev;
 using lbmk::Item;
+using lbmk::Layout;
 using lbmk::Phys;
 using lbmk::StepArgs;
+using lbmk::Tiling;
 
 namespace {
 
@@ -45,55 +48,9 @@ size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 const double kD[9] = {1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 6, 1.0 / 12,
                       1.0 / 6, 1.0 / 12, 1.0 / 4,  1.0 / 4};
 
-struct Layout {
-  size_t hdr = 0, cases = 0, items = 0, part = 0, vol = 0, staging = 0;
-  std::vector<size_t> f, g, J, lab;  // per-case offsets (f: 2 buffers back to back)
-  std::vector<int64_t> plane;
-  size_t total = 0;
-};
-
-struct Tiling {
-  int bx = 128;
-  int rows = 32;
-};
 
 }  // namespace
 
-struct lbm_handle {
-  int ncases = 0;
-  int precision = LBM_F32;
-  int flow = LBM_FLOW_COUPLED;
-  std::vector<lbm_params> params;
-  char* ws = nullptr;
-  size_t ws_bytes = 0;
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap = nullptr;  // private stream for graph capture
-  Layout L;
-  Tiling tile;
-  std::vector<Item> items;
-  std::vector<int> item_begin, item_end, vol_base, nregions;
-  int total_regions = 0;
-  int64_t t = 0;   // step index
-  int parity = 0;  // source buffer
-  Phys<float> pf{};
-  Phys<double> pd{};
-  std::vector<CaseDev<float>> cf;
-  std::vector<CaseDev<double>> cd;
-  cudaGraphExec_t gexec = nullptr;
-  int graph_parity = -1;
-  double* track = nullptr;  // fused volume output (device), or null
-  bool tma_ok = false;      // every case allows the bulk-copy kernel
-  int kernel = 0;           // 0 auto, 1 register-pipelined, 2 bulk-copy staged
-  // device pointers
-  int32_t* flags = nullptr;
-  int64_t* t_dev = nullptr;
-  Item* items_dev = nullptr;
-  void* cases_dev = nullptr;
-  double* part = nullptr;
-  double* vol = nullptr;
-  double* staging = nullptr;
-  int64_t max_plane = 0;
-};
 
 namespace {
 
@@ -981,6 +938,57 @@ int lbm_load(lbm_handle* h, const void* h_buf, size_t bytes) {
   return set_clock(h);
 }
 
+size_t lbm_snapshot_bytes(const lbm_handle* h, int32_t c) {
+  if (!h || c < 0 || c >= h->ncases) return 0;
+  return (size_t)20 * h->params[c].nx * h->params[c].ny * elem_size(h->precision);
+}
+
+// Device copy of the state of case c: [f*: 9][g*: 9][phi*u: 2] planes of
+// nx*ny elements each, pull layout (f planes zero in vortex mode).
+int lbm_snapshot(lbm_handle* h, int32_t c, void* d_buf) {
+  int rc = check_case(h, c);
+  if (rc) return rc;
+  if (!d_buf) return fail(LBM_ERR_ARG, "d_buf is null");
+  const int64_t n = (int64_t)h->params[c].nx * h->params[c].ny;
+  const size_t es = elem_size(h->precision), pb = (size_t)h->L.plane[c] * es, nb = n * es;
+  char* out = (char*)d_buf;
+  const bool coupled = h->flow == LBM_FLOW_COUPLED;
+  if (coupled)
+    LBM_CUDA(cudaMemcpy2DAsync(out, nb, h->ws + h->L.f[c] + h->parity * 9 * pb, pb, nb, 9,
+                               cudaMemcpyDeviceToDevice, h->stream));
+  else
+    LBM_CUDA(cudaMemsetAsync(out, 0, 9 * nb, h->stream));
+  LBM_CUDA(cudaMemcpy2DAsync(out + 9 * nb, nb, h->ws + h->L.g[c] + h->parity * 9 * pb, pb, nb, 9,
+                             cudaMemcpyDeviceToDevice, h->stream));
+  LBM_CUDA(cudaMemcpy2DAsync(out + 18 * nb, nb, h->ws + h->L.J[c] + h->parity * 2 * pb, pb, nb, 2,
+                             cudaMemcpyDeviceToDevice, h->stream));
+  return LBM_OK;
+}
+
+int lbm_restore(lbm_handle* h, int32_t c, const void* d_buf) {
+  int rc = check_case(h, c);
+  if (rc) return rc;
+  if (!d_buf) return fail(LBM_ERR_ARG, "d_buf is null");
+  const int64_t n = (int64_t)h->params[c].nx * h->params[c].ny;
+  const size_t es = elem_size(h->precision), pb = (size_t)h->L.plane[c] * es, nb = n * es;
+  const char* in = (const char*)d_buf;
+  if (h->flow == LBM_FLOW_COUPLED)
+    LBM_CUDA(cudaMemcpy2DAsync(h->ws + h->L.f[c] + h->parity * 9 * pb, pb, in, nb, nb, 9,
+                               cudaMemcpyDeviceToDevice, h->stream));
+  LBM_CUDA(cudaMemcpy2DAsync(h->ws + h->L.g[c] + h->parity * 9 * pb, pb, in + 9 * nb, nb, nb, 9,
+                             cudaMemcpyDeviceToDevice, h->stream));
+  LBM_CUDA(cudaMemcpy2DAsync(h->ws + h->L.J[c] + h->parity * 2 * pb, pb, in + 18 * nb, nb, nb, 2,
+                             cudaMemcpyDeviceToDevice, h->stream));
+  return LBM_OK;
+}
+
+int lbm_set_time(lbm_handle* h, int64_t t) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (t < 0) return fail(LBM_ERR_ARG, "t < 0");
+  h->t = t;
+  return set_clock(h);
+}
+
 int lbm_status(lbm_handle* h) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -991,13 +999,6 @@ int lbm_status(lbm_handle* h) {
   return rc;
 }
 
-int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, double* h_param_grads) {
-  (void)h;
-  (void)d_adj_in;
-  (void)d_adj_out;
-  (void)h_param_grads;
-  return fail(LBM_ERR_UNIMPLEMENTED, "lbm_adjoint_step is not built");
-}
 
 void lbm_destroy(lbm_handle* h) {
   if (!h) return;

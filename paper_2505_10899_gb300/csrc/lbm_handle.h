@@ -1,0 +1,67 @@
+// Internal definition of the opaque lbm_handle, shared by the host runtime
+// (lbm_api.cu) and the reverse-mode code (lbm_adjoint.cu).  Not part of the
+// public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbm_api.h"
+#include "lbm_layout.h"
+
+namespace lbmk {
+
+struct Layout {
+  size_t hdr = 0, cases = 0, items = 0, part = 0, vol = 0, staging = 0;
+  std::vector<size_t> f, g, J, lab;  // per-case offsets (f: 2 buffers back to back)
+  std::vector<int64_t> plane;
+  size_t total = 0;
+};
+
+struct Tiling {
+  int bx = 128;
+  int rows = 32;
+};
+
+}  // namespace lbmk
+
+struct lbm_handle {
+  int ncases = 0;
+  int precision = LBM_F32;
+  int flow = LBM_FLOW_COUPLED;
+  std::vector<lbm_params> params;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream for graph capture
+  lbmk::Layout L;
+  lbmk::Tiling tile;
+  std::vector<lbmk::Item> items;
+  std::vector<int> item_begin, item_end, vol_base, nregions;
+  int total_regions = 0;
+  int64_t t = 0;   // step index
+  int parity = 0;  // source buffer
+  lbmk::Phys<float> pf{};
+  lbmk::Phys<double> pd{};
+  std::vector<lbmk::CaseDev<float>> cf;
+  std::vector<lbmk::CaseDev<double>> cd;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_parity = -1;
+  double* track = nullptr;  // fused volume output (device), or null
+  bool tma_ok = false;      // every case allows the bulk-copy kernel
+  int kernel = 0;           // 0 auto, 1 register-pipelined, 2 bulk-copy staged
+  // device pointers
+  int32_t* flags = nullptr;
+  int64_t* t_dev = nullptr;
+  lbmk::Item* items_dev = nullptr;
+  void* cases_dev = nullptr;
+  double* part = nullptr;
+  double* vol = nullptr;
+  double* staging = nullptr;
+  int64_t max_plane = 0;
+  // reverse mode (lbm_adjoint_attach): caller-provided FP64 scratch
+  char* adj_ws = nullptr;
+  size_t adj_ws_bytes = 0;
+};

@@ -86,6 +86,14 @@ def _load():
         "lbm_load": ([_H, _VP, ctypes.c_size_t], ctypes.c_int),
         "lbm_status": ([_H], ctypes.c_int),
         "lbm_adjoint_step": ([_H, _VP, _VP, _D], ctypes.c_int),
+        "lbm_adjoint_workspace_bytes": ([_H], ctypes.c_size_t),
+        "lbm_adjoint_attach": ([_H, _VP, ctypes.c_size_t], ctypes.c_int),
+        "lbm_adjoint_seed_phi": ([_H, _VP, _VP], ctypes.c_int),
+        "lbm_adjoint_init": ([_H, _VP, _VP, _VP, _VP, _D], ctypes.c_int),
+        "lbm_snapshot_bytes": ([_H, ctypes.c_int32], ctypes.c_size_t),
+        "lbm_snapshot": ([_H, ctypes.c_int32, _VP], ctypes.c_int),
+        "lbm_restore": ([_H, ctypes.c_int32, _VP], ctypes.c_int),
+        "lbm_set_time": ([_H, ctypes.c_int64], ctypes.c_int),
         "lbm_destroy": ([_H], None),
         "lbm_phase_volume_noalloc": ([_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_int64, _VP, ctypes.c_int32, _VP, _VP],
@@ -276,9 +284,48 @@ def lbm_status(h) -> int:
     return int(_lib.lbm_status(h))
 
 
-def lbm_adjoint_step(h, d_in=0, d_out=0):
-    grads = np.zeros(8)
-    return int(_lib.lbm_adjoint_step(h, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), _dp(grads)))
+def lbm_snapshot_bytes(h, c: int = 0) -> int:
+    return int(_lib.lbm_snapshot_bytes(h, int(c)))
+
+
+def lbm_snapshot(h, c: int, d_buf: int):
+    return _check(_lib.lbm_snapshot(h, int(c), ctypes.c_void_p(d_buf)), "lbm_snapshot")
+
+
+def lbm_restore(h, c: int, d_buf: int):
+    return _check(_lib.lbm_restore(h, int(c), ctypes.c_void_p(d_buf)), "lbm_restore")
+
+
+def lbm_set_time(h, t: int):
+    return _check(_lib.lbm_set_time(h, int(t)), "lbm_set_time")
+
+
+def lbm_adjoint_workspace_bytes(h) -> int:
+    return int(_lib.lbm_adjoint_workspace_bytes(h))
+
+
+def lbm_adjoint_attach(h, d_scratch: int, nbytes: int):
+    return _check(_lib.lbm_adjoint_attach(h, ctypes.c_void_p(d_scratch), int(nbytes)),
+                  "lbm_adjoint_attach")
+
+
+def lbm_adjoint_seed_phi(h, d_dphi: int, d_adj: int):
+    return _check(_lib.lbm_adjoint_seed_phi(h, ctypes.c_void_p(d_dphi), ctypes.c_void_p(d_adj)),
+                  "lbm_adjoint_seed_phi")
+
+
+def lbm_adjoint_step(h, d_in: int, d_out: int, grads=None):
+    """Returns the status; adds d/d(sigma, tau_g, lambda, tau_f) into grads (numpy[4])."""
+    gp = _dp(grads) if grads is not None else None
+    return int(_lib.lbm_adjoint_step(h, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), gp))
+
+
+def lbm_adjoint_init(h, d_phi0: int, d_u0: int, d_adj: int, d_out: int, grads=None):
+    gp = _dp(grads) if grads is not None else None
+    return _check(_lib.lbm_adjoint_init(h, ctypes.c_void_p(d_phi0),
+                                        ctypes.c_void_p(d_u0) if d_u0 else None,
+                                        ctypes.c_void_p(d_adj), ctypes.c_void_p(d_out), gp),
+                  "lbm_adjoint_init")
 
 
 def lbm_phase_volume_noalloc(d_g: int, precision: str, nx: int, ny: int, plane_stride: int,

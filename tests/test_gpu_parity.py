@@ -211,12 +211,6 @@ def test_nonfinite_is_reported(L):
     assert s.status() == L.LBM_OK  # flags were cleared
 
 
-def test_adjoint_entry_point_is_declared_unimplemented(L):
-    case, phi0, u0, _, _ = W.two_droplets()
-    s = L.Sim(case, phi0, u0, precision="f32")
-    assert L.lbm_adjoint_step(s.h) == L.LBM_ERR_UNIMPLEMENTED
-
-
 def test_zero_steps_and_bad_calls(L):
     case, phi0, u0, _, _ = W.two_droplets()
     s = L.Sim(case, phi0, u0, precision="f32")
