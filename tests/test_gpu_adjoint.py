@@ -101,7 +101,7 @@ def test_multistep_gradient_vs_oracle_fd(L):
     case = W.base_case(nx, ny, sigma=4e-3, tau_g=0.8)
     # droplet small enough that phi stays inside (0, 1): no clip
     phi0 = W.tanh_disc(nx, ny, 20.0, 19.0, 5.0, 4.0, periodic=True)
-    phi0 = phi0 + 0.02 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, :] * phi0
+    phi0 = phi0 + 0.2 * np.sin(2 * np.pi * np.arange(nx) / nx)[None, :] * phi0 * (1 - phi0)
     assert phi0.max() < 0.999 and phi0.min() > 0
     w = W.uniform(3, (ny, nx), 0.0, 1.0)
     theta0 = np.array([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"]])
