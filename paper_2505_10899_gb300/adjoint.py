@@ -101,6 +101,7 @@ class CoupledRun(torch.autograd.Function):
         phiT = asim.phi()
         ctx.asim, ctx.ckpts, ctx.nsteps, ctx.k = asim, ckpts, nsteps, ckpt_every
         ctx.theta_dtype, ctx.theta_device = theta.dtype, theta.device
+        ctx.phi0_dtype, ctx.phi0_device = phi0.dtype, phi0.device
         return phiT
 
     @staticmethod
@@ -124,6 +125,7 @@ class CoupledRun(torch.autograd.Function):
         dphi0 = asim.vjp_init(adj, grads)
         asim.close()
         gtheta = torch.as_tensor(grads, dtype=ctx.theta_dtype, device=ctx.theta_device)
+        dphi0 = dphi0.to(device=ctx.phi0_device, dtype=ctx.phi0_dtype)
         return dphi0, gtheta, None, None, None, None
 
 
