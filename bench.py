@@ -405,7 +405,59 @@ def run_extras(args, cases, dev):
         s.close()
     vort["phi_maxdiff_f32_vs_f64"] = float(np.abs(fin["f32"] - fin["f64"]).max())
     out["single_vortex"] = vort
+    out["adjoint"] = adjoint_timing(dev)
     return out
+
+
+def adjoint_timing(dev, nx=512, ny=256, nsteps=32, ckpt=8):
+    """Reverse mode (FP64) against the FP64 forward step on a 512x256 droplet:
+    the bare vector-Jacobian step, and the full checkpointed backward of
+    torch.autograd (recompute + adjoint) per step."""
+    import torch
+    from paper_2505_10899_gb300 import adjoint as A
+
+    case = W.base_case(nx, ny)
+    phi0 = W.tanh_disc(nx, ny, nx / 2, ny / 2, 40.0, 4.0, periodic=True)
+    s = A.AdjointSim(case, phi0)
+    stream = s.sim.stream
+
+    def timed(fn, n):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / n
+
+    fwd_ms = timed(lambda: s.step(1), 50)
+    s.restore(s.snapshot(), s.t)
+    adj = torch.as_tensor(W.uniform(5, (20, ny, nx), -1, 1), device=s.dev)
+
+    def one_vjp():
+        s.vjp_step(adj, None)
+
+    vjp_ms = timed(one_vjp, 20)
+    s.close()
+    # full backward through torch.autograd with checkpoint every `ckpt` steps
+    phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
+    theta = torch.tensor([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"]],
+                         dtype=torch.float64, requires_grad=True)
+    phiT = A.coupled_run(phi0_t, theta, case, nsteps, ckpt)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    phiT.sum().backward()
+    torch.cuda.synchronize(dev)
+    bwd_ms = (time.perf_counter() - t0) * 1e3 / nsteps
+    return {"grid": f"{nx}x{ny}", "precision": "f64",
+            "forward_ms_per_step": round(fwd_ms, 4),
+            "vjp_ms_per_step": round(vjp_ms, 4),
+            "vjp_over_forward": round(vjp_ms / fwd_ms, 3),
+            "checkpointed_backward_ms_per_step": round(bwd_ms, 4),
+            "checkpointed_backward_over_forward": round(bwd_ms / fwd_ms, 3),
+            "checkpoint_every": ckpt}
 
 
 def cpu_baseline(cases, seconds):
