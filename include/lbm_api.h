@@ -213,7 +213,8 @@ int lbm_status(lbm_handle* h);
  * device precision, in the pull layout (plane i, position x holds the
  * post-collision value that streams to x + c_i; f planes are zero in vortex
  * mode).  lbm_restore writes such a buffer back as the current state; the
- * step index is set separately with lbm_set_time.  Asynchronous. */
+ * step index is set separately with lbm_set_time.  All three are
+ * asynchronous on the handle's stream. */
 size_t lbm_snapshot_bytes(const lbm_handle* h, int32_t c);
 int lbm_snapshot(lbm_handle* h, int32_t c, void* d_buf);
 int lbm_restore(lbm_handle* h, int32_t c, const void* d_buf);
@@ -231,15 +232,20 @@ int lbm_set_time(lbm_handle* h, int64_t t);
  *   lbm_adjoint_step: the handle must hold the state S_t at step index t;
  *     given the adjoint of S_{t+1} (d_adj_in), writes the adjoint of S_t
  *     (d_adj_out, a different buffer) through the transposed Jacobian of one
- *     step (Eqs. 20-37 as computed by lbm_step), and adds to h_param_grads[4]
- *     (may be NULL) the derivatives with respect to (sigma, tau_g, lambda,
- *     tau_f); the tau_f entry is zero when tau_f varies with phi or in vortex
- *     mode.  The state is not modified.  At the clip of Eq. 37 and where
+ *     step (Eqs. 20-37 as computed by lbm_step), and accumulates on the device
+ *     the derivatives with respect to (sigma, tau_g, lambda, tau_f); with
+ *     h_param_grads[4] non-NULL the accumulated values are added to it and the
+ *     accumulator is cleared (this synchronises), with NULL the call is
+ *     asynchronous.  The tau_f entry is zero when tau_f varies with phi or in
+ *     vortex mode.  The state is not modified.  At the clip of Eq. 37 and where
  *     |grad psi| = 0 the derivative of the branch taken is used.
  *   lbm_adjoint_init: adjoint of the initial-state map of lbm_init: given the
- *     adjoint of S_0, writes d_adj_phi0 [ny][nx] and adds the sigma and lambda
- *     derivatives; d_phi0 [ny][nx] and d_u0 ([2][ny][nx] or NULL) are the
- *     device copies of the initial fields.
+ *     adjoint of S_0, writes d_adj_phi0 [ny][nx] and accumulates the sigma and
+ *     lambda derivatives (h_param_grads as for lbm_adjoint_step); d_phi0
+ *     [ny][nx] and d_u0 ([2][ny][nx] or NULL) are the device copies of the
+ *     initial fields.
+ *   lbm_adjoint_take_param_grads: adds the accumulated parameter derivatives
+ *     to h_param_grads[4] and clears the accumulator (synchronises).
  * Synchronise when h_param_grads is non-NULL.  Errors: LBM_ERR_ARG (batch,
  * FP32 handle, null buffers), LBM_ERR_WORKSPACE (no scratch), LBM_ERR_CUDA. */
 size_t lbm_adjoint_workspace_bytes(const lbm_handle* h);
@@ -250,6 +256,7 @@ int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out,
 int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
                      const void* d_adj_state, double* d_adj_phi0,
                      double* h_param_grads);
+int lbm_adjoint_take_param_grads(lbm_handle* h, double* h_param_grads);
 
 /* Allocation-free phase volumes, for callers that cannot allocate device
  * memory (for example code that runs while a memory pool forbids new

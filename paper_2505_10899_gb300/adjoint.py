@@ -38,8 +38,9 @@ class AdjointSim:
     def new_state(self):
         return torch.zeros((20,) + self.shape, dtype=torch.float64, device=self.dev)
 
-    def snapshot(self):
-        buf = self.new_state()
+    def snapshot(self, buf=None):
+        if buf is None:
+            buf = torch.empty((20,) + self.shape, dtype=torch.float64, device=self.dev)
         lbm.lbm_snapshot(self.h, 0, buf.data_ptr())
         return buf
 
@@ -63,12 +64,18 @@ class AdjointSim:
         lbm.lbm_adjoint_seed_phi(self.h, dphi.data_ptr(), adj.data_ptr())
         return adj
 
-    def vjp_step(self, adj_in, grads):
-        adj_out = self.new_state()
+    def vjp_step(self, adj_in, grads=None, adj_out=None):
+        """Adjoint of S_t from the adjoint of S_{t+1}.  Parameter derivatives
+        accumulate on the device; with ``grads`` (numpy[4]) they are fetched."""
+        if adj_out is None:
+            adj_out = torch.empty((20,) + self.shape, dtype=torch.float64, device=self.dev)
         rc = lbm.lbm_adjoint_step(self.h, adj_in.data_ptr(), adj_out.data_ptr(), grads)
         if rc != lbm.LBM_OK:
             raise lbm.LbmError(rc, "lbm_adjoint_step", lbm.lib().lbm_last_error().decode())
         return adj_out
+
+    def take_grads(self, grads):
+        lbm.lbm_adjoint_take_param_grads(self.h, grads)
 
     def vjp_init(self, adj_state, grads):
         out = torch.zeros(self.shape, dtype=torch.float64, device=self.dev)
@@ -109,20 +116,22 @@ class CoupledRun(torch.autograd.Function):
         asim, nsteps, k = ctx.asim, ctx.nsteps, ctx.k
         grads = np.zeros(4)
         adj = asim.seed_phi(grad_phiT)
-        seg_starts = sorted(ctx.ckpts)
-        for t0 in reversed(seg_starts):
+        spare = torch.empty_like(adj)
+        seg = [torch.empty_like(adj) for _ in range(k - 1)]  # recomputed states
+        for t0 in reversed(sorted(ctx.ckpts)):
             t1 = min(t0 + k, nsteps)
-            # recompute the states of the segment [t0, t1)
+            # recompute the states of the segment [t0, t1) from its checkpoint
             asim.restore(ctx.ckpts[t0], t0)
             states = {t0: ctx.ckpts[t0]}
             for t in range(t0 + 1, t1):
                 asim.step(1)
-                states[t] = asim.snapshot()
+                states[t] = asim.snapshot(seg[t - t0 - 1])
             for t in reversed(range(t0, t1)):
                 asim.restore(states[t], t)
-                adj = asim.vjp_step(adj, grads)
+                adj, spare = asim.vjp_step(adj, None, spare), adj
         asim.restore(ctx.ckpts[0], 0)
-        dphi0 = asim.vjp_init(adj, grads)
+        dphi0 = asim.vjp_init(adj, None)
+        asim.take_grads(grads)
         asim.close()
         gtheta = torch.as_tensor(grads, dtype=ctx.theta_dtype, device=ctx.theta_device)
         dphi0 = dphi0.to(device=ctx.phi0_device, dtype=ctx.phi0_dtype)

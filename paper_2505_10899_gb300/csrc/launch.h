@@ -54,5 +54,6 @@ cudaError_t launch_volume_final(const CaseDev<T>* cases, int ncases, const doubl
                                 double* out, cudaStream_t s);
 
 cudaError_t launch_clock(int64_t* t, int64_t n, cudaStream_t s);
+cudaError_t launch_set_clock(int64_t* t, int64_t value, cudaStream_t s);
 
 }  // namespace lbmk

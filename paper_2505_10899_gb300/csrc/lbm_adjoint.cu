@@ -532,12 +532,14 @@ __global__ void ad_seed_phi(const double* __restrict__ dphi, int nx, int ny,
   }
 }
 
-__global__ void ad_sum_partials(const double* __restrict__ part, int nb, double* __restrict__ out) {
+// Adds this sweep's parameter partials (in block order) to the device
+// accumulator `acc`, which lbm_adjoint_take_param_grads reads and clears.
+__global__ void ad_sum_partials(const double* __restrict__ part, int nb, double* __restrict__ acc) {
   const int q = threadIdx.x;
   if (q >= kNParam) return;
   double v = 0.0;
   for (int b = 0; b < nb; ++b) v += part[(int64_t)b * kNParam + q];
-  out[q] = v;
+  acc[q] += v;
 }
 
 // Scratch layout inside the caller's adjoint workspace (doubles).
@@ -576,6 +578,19 @@ void to_param_grads(const lbm_params& p, const double raw[kNParam], double* out)
   out[3] += raw[4];
 }
 
+// Reads and clears the device accumulator, adding d/d(sigma, tau_g, lambda,
+// tau_f) to out (synchronises).
+int take_grads(lbm_handle* h, double* out) {
+  AdScratch s = carve(h);
+  double raw[kNParam];
+  cudaError_t e = cudaMemcpyAsync(raw, s.sums, sizeof raw, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.sums, 0, sizeof raw, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  to_param_grads(h->params[0], raw, out);
+  return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -593,7 +608,16 @@ int lbm_adjoint_attach(lbm_handle* h, void* d_scratch, size_t bytes) {
   if (bytes < lbm_adjoint_workspace_bytes(h)) return fail(LBM_ERR_WORKSPACE, "adjoint scratch too small");
   h->adj_ws = (char*)d_scratch;
   h->adj_ws_bytes = bytes;
+  cudaError_t e = cudaMemsetAsync(carve(h).sums, 0, kNParam * sizeof(double), h->stream);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   return LBM_OK;
+}
+
+int lbm_adjoint_take_param_grads(lbm_handle* h, double* h_param_grads) {
+  int rc = check_handle(h, true);
+  if (rc) return rc;
+  if (!h_param_grads) return fail(LBM_ERR_ARG, "h_param_grads is null");
+  return take_grads(h, h_param_grads);
 }
 
 int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, double* d_adj_state) {
@@ -654,13 +678,7 @@ int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, doubl
   ad_sum_partials<<<1, 32, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
-  if (h_param_grads) {
-    double raw[kNParam];
-    e = cudaMemcpyAsync(raw, s.sums, sizeof raw, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
-    to_param_grads(p, raw, h_param_grads);
-  }
+  if (h_param_grads) return take_grads(h, h_param_grads);
   return LBM_OK;
 }
 
@@ -692,13 +710,7 @@ int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
   ad_sum_partials<<<1, 32, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
-  if (h_param_grads) {
-    double raw[kNParam];
-    e = cudaMemcpyAsync(raw, s.sums, sizeof raw, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
-    to_param_grads(p, raw, h_param_grads);
-  }
+  if (h_param_grads) return take_grads(h, h_param_grads);
   return LBM_OK;
 }
 

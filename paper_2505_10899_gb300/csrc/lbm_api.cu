@@ -986,7 +986,8 @@ int lbm_set_time(lbm_handle* h, int64_t t) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (t < 0) return fail(LBM_ERR_ARG, "t < 0");
   h->t = t;
-  return set_clock(h);
+  LBM_CUDA(lbmk::launch_set_clock(h->t_dev, t, h->stream));  // asynchronous
+  return LBM_OK;
 }
 
 int lbm_status(lbm_handle* h) {

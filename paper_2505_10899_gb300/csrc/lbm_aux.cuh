@@ -191,5 +191,8 @@ __global__ void volume_final(const CaseDev<T>* __restrict__ cases, int ncases,
 static __global__ void clock_kernel(int64_t* t, int64_t n) {
   if (threadIdx.x == 0 && blockIdx.x == 0) *t += n;
 }
+static __global__ void set_clock_kernel(int64_t* t, int64_t value) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *t = value;
+}
 
 }  // namespace lbmk

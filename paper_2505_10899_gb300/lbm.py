@@ -90,6 +90,7 @@ def _load():
         "lbm_adjoint_attach": ([_H, _VP, ctypes.c_size_t], ctypes.c_int),
         "lbm_adjoint_seed_phi": ([_H, _VP, _VP], ctypes.c_int),
         "lbm_adjoint_init": ([_H, _VP, _VP, _VP, _VP, _D], ctypes.c_int),
+        "lbm_adjoint_take_param_grads": ([_H, _D], ctypes.c_int),
         "lbm_snapshot_bytes": ([_H, ctypes.c_int32], ctypes.c_size_t),
         "lbm_snapshot": ([_H, ctypes.c_int32, _VP], ctypes.c_int),
         "lbm_restore": ([_H, ctypes.c_int32, _VP], ctypes.c_int),
@@ -318,6 +319,10 @@ def lbm_adjoint_step(h, d_in: int, d_out: int, grads=None):
     """Returns the status; adds d/d(sigma, tau_g, lambda, tau_f) into grads (numpy[4])."""
     gp = _dp(grads) if grads is not None else None
     return int(_lib.lbm_adjoint_step(h, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), gp))
+
+
+def lbm_adjoint_take_param_grads(h, grads):
+    return _check(_lib.lbm_adjoint_take_param_grads(h, _dp(grads)), "lbm_adjoint_take_param_grads")
 
 
 def lbm_adjoint_init(h, d_phi0: int, d_u0: int, d_adj: int, d_out: int, grads=None):
