@@ -83,6 +83,40 @@ cudaError_t launch_step<LBM_T>(const StepArgs<LBM_T>& a, int bx, bool coupled, i
   }
 }
 
+template <int BX, bool COUPLED>
+cudaError_t persist_bx(const StepArgs<LBM_T>& a, int n_items, int nsteps, int flip,
+                       unsigned int* count, unsigned int* gen, cudaStream_t s) {
+  auto kern = step_kernel_persistent<LBM_T, BX, COUPLED>;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BX, 0);
+  if (e != cudaSuccess) return e;
+  int grid = per_sm * nsm;
+  if (grid > n_items) grid = n_items;
+  if (grid < 1) return cudaErrorInvalidConfiguration;
+  StepArgs<LBM_T> args = a;
+  GridBar bar{count, gen};
+  void* params[] = {(void*)&args, (void*)&n_items, (void*)&nsteps, (void*)&flip, (void*)&bar};
+  return cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(BX), params, 0, s);
+}
+
+template <>
+cudaError_t launch_persistent<LBM_T>(const StepArgs<LBM_T>& a, int bx, bool coupled, int n_items,
+                                     int nsteps, int flip, unsigned int* count,
+                                     unsigned int* gen, cudaStream_t s) {
+  if (n_items <= 0 || nsteps <= 0) return cudaSuccess;
+  switch (bx) {
+    case 32: return coupled ? persist_bx<32, true>(a, n_items, nsteps, flip, count, gen, s)
+                            : persist_bx<32, false>(a, n_items, nsteps, flip, count, gen, s);
+    case 64: return coupled ? persist_bx<64, true>(a, n_items, nsteps, flip, count, gen, s)
+                            : persist_bx<64, false>(a, n_items, nsteps, flip, count, gen, s);
+    case 128: return coupled ? persist_bx<128, true>(a, n_items, nsteps, flip, count, gen, s)
+                             : persist_bx<128, false>(a, n_items, nsteps, flip, count, gen, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <>
 cudaError_t prepare_tma<LBM_T>() {
   cudaError_t e;

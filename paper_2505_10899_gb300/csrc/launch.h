@@ -17,6 +17,14 @@ template <typename T>
 cudaError_t launch_step(const StepArgs<T>& a, int bx, bool coupled, int mode, bool tma,
                         int n_items, cudaStream_t s);
 
+// Persistent register-path kernel (cooperative launch): nsteps steps in one
+// launch; grid = min(n_items, co-resident CTAs).  count/gen: grid-barrier
+// words (zero-initialised, device).
+template <typename T>
+cudaError_t launch_persistent(const StepArgs<T>& a, int bx, bool coupled, int n_items,
+                              int nsteps, int flip, unsigned int* count, unsigned int* gen,
+                              cudaStream_t s);
+
 // Allow the dynamic shared memory of every TMA kernel variant on the current
 // device (call once per device before the first launch or graph capture).
 template <typename T>

@@ -298,6 +298,19 @@ bool use_tma(const lbm_handle* h) {
   return h->kernel == 2 || (h->kernel == 0 && h->tma_ok);
 }
 
+// Batches small enough for one persistent cooperative launch to pay off.
+constexpr int64_t kPersistMaxNodes = 4 << 20;
+
+int64_t total_nodes(const lbm_handle* h) {
+  int64_t n = 0;
+  for (const lbm_params& p : h->params) n += (int64_t)p.nx * p.ny;
+  return n;
+}
+
+unsigned int* bar_count(lbm_handle* h) { return (unsigned int*)(h->ws + h->L.hdr + 32); }
+unsigned int* bar_gen(lbm_handle* h) { return (unsigned int*)(h->ws + h->L.hdr + 36); }
+
+
 template <typename T>
 StepArgs<T> step_args(const lbm_handle* h, int parity, int64_t t_off) {
   StepArgs<T> a{};
@@ -309,6 +322,20 @@ StepArgs<T> step_args(const lbm_handle* h, int parity, int64_t t_off) {
   a.parity = parity;
   a.flags = h->flags;
   return a;
+}
+
+int launch_persist(lbm_handle* h, cudaStream_t s, int parity, int nsteps, int flip) {
+  const bool coupled = h->flow == LBM_FLOW_COUPLED;
+  const int n = (int)h->items.size();
+  cudaError_t e;
+  if (h->precision == LBM_F32)
+    e = lbmk::launch_persistent<float>(step_args<float>(h, parity, 0), h->tile.bx, coupled, n,
+                                       nsteps, flip, bar_count(h), bar_gen(h), s);
+  else
+    e = lbmk::launch_persistent<double>(step_args<double>(h, parity, 0), h->tile.bx, coupled, n,
+                                        nsteps, flip, bar_count(h), bar_gen(h), s);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+  return LBM_OK;
 }
 
 // Enqueue `count` consecutive steps starting from source buffer `parity`,
@@ -615,6 +642,19 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
 int lbm_step(lbm_handle* h, int64_t nsteps) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps < 0");
+  if (h->kernel == 3 && !h->track) {
+    // persistent kernel: chunks of at most 65536 steps per cooperative launch
+    while (nsteps > 0) {
+      const int cnt = (int)std::min<int64_t>(nsteps, 65536);
+      int rc = launch_persist(h, h->stream, h->parity, cnt, 1);
+      if (rc) return rc;
+      LBM_CUDA(lbmk::launch_clock(h->t_dev, cnt, h->stream));
+      h->parity ^= (cnt & 1);
+      h->t += cnt;
+      nsteps -= cnt;
+    }
+    return LBM_OK;
+  }
   while (nsteps > 0) {
     if (nsteps >= kGraphSteps) {
       if (!h->gexec || h->graph_parity != h->parity) {
@@ -677,9 +717,11 @@ int32_t lbm_num_regions(const lbm_handle* h) { return h ? h->total_regions : 0; 
 
 int lbm_set_kernel(lbm_handle* h, int32_t variant) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
-  if (variant < 0 || variant > 2) return fail(LBM_ERR_ARG, "kernel variant must be 0, 1 or 2");
+  if (variant < 0 || variant > 3) return fail(LBM_ERR_ARG, "kernel variant must be 0, 1, 2 or 3");
   if (variant == 2 && !h->tma_ok)
     return fail(LBM_ERR_ARG, "bulk-copy kernel needs nx a multiple of 16 bytes and nx >= 4");
+  if (variant == 3 && total_nodes(h) > kPersistMaxNodes)
+    return fail(LBM_ERR_ARG, "persistent kernel is for batches of at most 4 Mi nodes");
   if (variant != h->kernel) drop_graph(h);
   h->kernel = variant;
   return LBM_OK;
@@ -687,6 +729,7 @@ int lbm_set_kernel(lbm_handle* h, int32_t variant) {
 
 int32_t lbm_get_kernel(const lbm_handle* h) {
   if (!h) return -1;
+  if (h->kernel == 3) return 3;
   return use_tma(h) ? 2 : 1;
 }
 
@@ -723,16 +766,25 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel, int32_t* b
   Tiling best_t = keep_tile;
   int best_k = use_tma(h) ? 2 : 1;
   int rc = LBM_OK;
-  for (int kv : {2, 1}) {
+  for (int kv : {2, 1, 3}) {
     if (kv == 2 && !h->tma_ok) continue;
+    if (kv == 3 && total_nodes(h) > kPersistMaxNodes) continue;
     for (int bx : {128, 64, 32}) {
       for (int rows : {4, 8, 16, 32, 64}) {
         h->kernel = kv;
         rc = lbm_set_tiling(h, bx, rows);
         if (rc != LBM_OK) break;
-        cudaError_t e = trial(1);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-        if (e == cudaSuccess) e = trial(trials);
+        cudaError_t e = cudaSuccess;
+        if (kv == 3) {  // one launch of `trials` steps without flipping buffers
+          rc = launch_persist(h, h->stream, h->parity, 1, 0);
+          if (rc == LBM_OK) e = cudaEventRecord(e0, h->stream);
+          if (rc == LBM_OK && e == cudaSuccess) rc = launch_persist(h, h->stream, h->parity, trials, 0);
+          if (rc != LBM_OK) break;
+        } else {
+          e = trial(1);
+          if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+          if (e == cudaSuccess) e = trial(trials);
+        }
         if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;

@@ -23,20 +23,28 @@ namespace lbmk {
 // (x - c_ix, row - c_iy).  o0/om/op are the offsets of rows row, row-1,
 // row+1 (periodic), xm/xp the columns x-1, x+1 (periodic).  Eq. 19 order:
 // c = (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).
-template <typename T>
+// Global load: read-only path, or L2-coherent (bypassing L1) when the data
+// may have been written by other CTAs of the same launch (persistent kernel).
+template <bool COHERENT, typename T>
+__device__ __forceinline__ T ld(const T* p) {
+  if (COHERENT) return __ldcg(p);
+  return __ldg(p);
+}
+
+template <bool COHERENT = false, typename T>
 __device__ __forceinline__ void pull9(const T* __restrict__ b, uint32_t P,
                                       uint32_t o0, uint32_t om, uint32_t op,
                                       uint32_t x, uint32_t xm, uint32_t xp, T v[9]) {
   // 32-bit element offsets: a buffer of 9 planes holds < 2^31 elements
-  v[0] = __ldg(b + (o0 + x));
-  v[1] = __ldg(b + (P + o0 + xm));
-  v[2] = __ldg(b + (2u * P + om + x));
-  v[3] = __ldg(b + (3u * P + o0 + xp));
-  v[4] = __ldg(b + (4u * P + op + x));
-  v[5] = __ldg(b + (5u * P + om + xm));
-  v[6] = __ldg(b + (6u * P + om + xp));
-  v[7] = __ldg(b + (7u * P + op + xp));
-  v[8] = __ldg(b + (8u * P + op + xm));
+  v[0] = ld<COHERENT>(b + (o0 + x));
+  v[1] = ld<COHERENT>(b + (P + o0 + xm));
+  v[2] = ld<COHERENT>(b + (2u * P + om + x));
+  v[3] = ld<COHERENT>(b + (3u * P + o0 + xp));
+  v[4] = ld<COHERENT>(b + (4u * P + op + x));
+  v[5] = ld<COHERENT>(b + (5u * P + om + xm));
+  v[6] = ld<COHERENT>(b + (6u * P + om + xp));
+  v[7] = ld<COHERENT>(b + (7u * P + op + xp));
+  v[8] = ld<COHERENT>(b + (8u * P + op + xm));
 }
 
 // CTA reduction of the fused phase volume: warp shuffles, then warps in order.
@@ -56,12 +64,10 @@ __device__ __forceinline__ void write_volume_partial(double vacc, double* vred, 
 //   COUPLED: f and g (true) or g only with the prescribed vortex (false).
 //   MODE:    kModeStep collides and stores; kModeFields writes phi, u, p.
 // ---------------------------------------------------------------------------
-template <typename T, int BX, bool COUPLED, int MODE>
-__global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
-  __shared__ Ring<T, BX> ring;
-  __shared__ double vred[BX / 32];
-
-  const Item it = a.items[blockIdx.x];
+template <typename T, int BX, bool COUPLED, int MODE, bool COHERENT>
+__device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T, BX>& ring,
+                                          double* vred) {
+  const Item it = a.items[item];
   const CaseDev<T>* __restrict__ cdp = a.cases + it.c;
   const int nx = cdp->nx, ny = cdp->ny;
   const uint32_t P = (uint32_t)cdp->plane;
@@ -115,24 +121,24 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
     const int rr = wrap(r);
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
-    pull9(gs, P, o0, om, op, xc, xm, xp, R.G);
-    if (COUPLED) pull9(fs, P, o0, om, op, xc, xm, xp, R.F);
+    pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G);
+    if (COUPLED) pull9<COHERENT>(fs, P, o0, om, op, xc, xm, xp, R.F);
     if (MODE == kModeStep) {  // phi*u of the previous step at the own node
-      R.J[0] = Js[o0 + xc];
-      R.J[1] = Js[P + o0 + xc];
+      R.J[0] = ld<COHERENT>(Js + (o0 + xc));
+      R.J[1] = ld<COHERENT>(Js + (P + o0 + xc));
     }
   };
   auto fetch_g = [&](int r, Regs& R) {
     const int rr = wrap(r);
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
-    pull9(gs, P, o0, om, op, xc, xm, xp, R.G);
+    pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G);
   };
   auto fetch_halo = [&](int r, T H[9]) {
     const int rr = wrap(r);
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
-    pull9(gs, P, o0, om, op, hc, hcm, hcp, H);
+    pull9<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, H);
   };
   // write phi/psi of local row k (k >= -1) into the ring
   auto put_row = [&](int k, const T G[9], const T H[9]) {
@@ -204,7 +210,77 @@ __global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
     if (k + 2 < nrows) stage(k + 2, Rq, Rn);
   }
 
-  if (do_vol) write_volume_partial<BX>(vacc, vred, a.vol_part + (int64_t)blockIdx.x * kMaxRegions);
+  if (do_vol) write_volume_partial<BX>(vacc, vred, a.vol_part + (int64_t)item * kMaxRegions);
+  __syncthreads();  // the ring is reused by the next item of a persistent CTA
+}
+
+template <typename T, int BX, bool COUPLED, int MODE>
+__global__ void __launch_bounds__(BX) step_kernel(const StepArgs<T> a) {
+  __shared__ Ring<T, BX> ring;
+  __shared__ double vred[BX / 32];
+  step_item<T, BX, COUPLED, MODE, false>(a, blockIdx.x, ring, vred);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent variant for small grids: one cooperative launch advances nsteps
+// steps.  Every CTA takes the items blockIdx.x, blockIdx.x + gridDim.x, ...
+// of each step, then all CTAs meet at a grid barrier before the next step
+// reads what the previous one wrote (loads are L2-coherent, see ld()).  With
+// flip = 0 the source buffer stays the same for every step (autotuning
+// trials: the state is not changed).
+// The barrier is a counter and a generation word in the workspace header;
+// its wait is bounded and raises kFlagTimeout when it expires.
+// ---------------------------------------------------------------------------
+struct GridBar {
+  unsigned int* count;
+  unsigned int* gen;
+};
+
+__device__ __forceinline__ bool grid_barrier(const GridBar& b, int32_t* flags) {
+  __shared__ int ok_s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g = *(volatile unsigned int*)b.gen;
+    __threadfence();  // this CTA's stores are visible before it arrives
+    const unsigned int arrived = atomicAdd(b.count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(b.count, 0u);
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*(volatile unsigned int*)b.gen == g) {
+        if (clock64() - t0 > 4000000000LL) {  // ~2 s
+          atomicOr(flags, kFlagTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok_s = ok;
+  }
+  __syncthreads();
+  return ok_s != 0;
+}
+
+template <typename T, int BX, bool COUPLED>
+__global__ void __launch_bounds__(BX) step_kernel_persistent(const StepArgs<T> a, int n_items,
+                                                             int nsteps, int flip, GridBar bar) {
+  __shared__ Ring<T, BX> ring;
+  __shared__ double vred[BX / 32];
+  for (int s = 0; s < nsteps; ++s) {
+    StepArgs<T> as = a;
+    if (flip) {
+      as.parity = a.parity ^ (s & 1);
+      as.t_off = a.t_off + s;
+    }
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x)
+      step_item<T, BX, COUPLED, kModeStep, true>(as, item, ring, vred);
+    if (s + 1 < nsteps && !grid_barrier(bar, a.flags)) return;
+  }
 }
 
 }  // namespace lbmk

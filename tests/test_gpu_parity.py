@@ -323,3 +323,32 @@ def test_translating_droplet_fp32(L, ratio):
     err = maxdiff(s.fields(0)[0], o.fields()[0])
     print(f"ratio {ratio}: max |phi_f32 - phi_oracle| = {err:.3e}")
     assert err <= TOL32_PHI
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_persistent_kernel(L, prec):
+    # one cooperative launch for all steps, grid barrier between steps
+    case, phi0, u0, _, _ = W.two_droplets(noise=1e-3)
+    o = oracle.Oracle(case, phi0, u0).step(150)
+    s = L.Sim(case, phi0, u0, precision=prec)
+    s.set_kernel(3)
+    assert s.kernel() == 3
+    s.step(77)
+    s.step(73)
+    tol = TOL64 if prec == "f64" else TOL32_PHI
+    assert maxdiff(s.fields(0)[0], o.fields()[0]) <= tol
+    assert s.status() == L.LBM_OK
+    # vortex flow: the step clock advances inside the launch
+    vcase, vphi0, _ = W.single_vortex(n=64, W=3.0, U=0.02, T=256)
+    vphi0 = vphi0 + W.uniform(9, vphi0.shape, -1e-3, 1e-3)
+    ov = oracle.Oracle(vcase, vphi0).step(100)
+    sv = L.Sim(vcase, vphi0, None, precision=prec)
+    sv.set_kernel(3)
+    sv.step(100)
+    assert maxdiff(sv.fields(0)[0], ov.fields()[0]) <= tol
+    # autotuning may pick the persistent kernel; it must not change the state
+    before = sv.get_state(0)
+    sv.autotune(1)
+    after = sv.get_state(0)
+    for x, y in zip(before[:3], after[:3]):
+        assert np.array_equal(x, y)
