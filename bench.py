@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register, 2 bulk-copy")
     ap.add_argument("--tiling", type=str, default=None, help="BX,ROWS (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--only-adjoint", action="store_true",
+                    help="print the reverse-mode timing only (profiling aid)")
     return ap.parse_args()
 
 
@@ -399,6 +401,7 @@ def run_extras(args, cases, dev):
         ms = timed(s, 16384)
         phi = s.fields(0)[0]
         fin[prec] = phi
+        vort[f"{prec}_kernel"] = {"variant": s.kernel(), "bx": s.tiling()[0], "rows": s.tiling()[1]}
         vort[f"{prec}_mlups"] = round(256 * 256 * 16384 / (ms * 1e-3) / 1e6, 1)
         vort[f"{prec}_shape_error"] = float(np.abs(phi - vphi0).sum() / vphi0.sum())
         vort[f"{prec}_volume_drift"] = float(s.volume()[0] / v0 - 1.0)
@@ -540,6 +543,10 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.only_adjoint:
+        import torch
+        print(json.dumps({"adjoint": adjoint_timing(torch.device("cuda", 0))}), flush=True)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
