@@ -24,18 +24,22 @@ _lock = threading.Lock()
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-O2, no FMA contraction, OpenMP)."""
+def build(force: bool = False, plant: int = 0) -> str:
+    """Compile the oracle with gcc (-O2, no FMA contraction, OpenMP).
+
+    plant > 0 builds a copy with one deliberately wrong formula (ORC_PLANT in
+    lbm_oracle.c), used only by the mutation test of the pins."""
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_SO)
-            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
-        return _SO
-    tmp = _SO + f".tmp{os.getpid()}"
+    so = _SO if plant == 0 else _SO.replace(".so", f"_plant{plant}.so")
+    if (not force and os.path.exists(so)
+            and os.path.getmtime(so) >= os.path.getmtime(_SRC)):
+        return so
+    tmp = so + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+           f"-DORC_PLANT={int(plant)}", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
 
 
 class Params(ctypes.Structure):
@@ -62,7 +66,7 @@ def lib():
     global _lib
     with _lock:
         if _lib is None:
-            so = build()
+            so = build(plant=int(os.environ.get("ORACLE_PLANT", "0")))
             L = ctypes.CDLL(so)
             P = ctypes.POINTER(Params)
             L.orc_lattice.argtypes = [_I32, _I32, _D]

@@ -48,6 +48,12 @@
 #define M_PI 3.14159265358979323846
 #endif
 
+/* ORC_PLANT selects a deliberately wrong variant of one formula, for the
+ * mutation test that shows the pins catch it (0 = the oracle as written). */
+#ifndef ORC_PLANT
+#define ORC_PLANT 0
+#endif
+
 /* ---- D2Q9 lattice, Eq. 19 evaluated (c = 1), and its weights ---------- */
 static const int CX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int CY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -153,12 +159,15 @@ void orc_force(double ux, double uy, double Fx, double Fy, double grx,
   double u[2] = {ux, uy}, gr[2] = {grx, gry};
   for (int i = 0; i < 9; ++i) {
     double c[2] = {(double)CX[i], (double)CY[i]};
-    double u_gr = ux * grx + uy * gry;
+    double u_gr = ux * grx + uy * gry; /* not const: see ORC_PLANT 1 */
     double c_F = c[0] * Fx + c[1] * Fy;
     double tens = 0.0; /* (u grad rho) : (c_i c_i - c_s^2 I) */
     for (int a = 0; a < 2; ++a)
       for (int b = 0; b < 2; ++b)
         tens += u[a] * gr[b] * (c[a] * c[b] - CS2 * (a == b ? 1.0 : 0.0));
+#if ORC_PLANT == 1
+    u_gr = 0.0;
+#endif
     out[i] = WT[i] * (u_gr + c_F / CS2 + tens / CS2);
   }
 }
@@ -167,7 +176,11 @@ void orc_force(double ux, double uy, double Fx, double Fy, double grx,
 void orc_geq(double phi, double mu, double lambda, double ux, double uy,
              double *out) {
   double lam = mu + lambda * phi;
+#if ORC_PLANT == 3
+  out[0] = phi + WT[0] * lam;
+#else
   out[0] = phi + (WT[0] - 1.0) * lam;
+#endif
   for (int i = 1; i < 9; ++i)
     out[i] = WT[i] * lam + WT[i] * (CX[i] * phi * ux + CY[i] * phi * uy) / CS2;
 }
@@ -175,9 +188,16 @@ void orc_geq(double phi, double mu, double lambda, double ux, double uy,
 /* Eq. 32: source of the phase-field LB; (dJx,dJy) = d_t(phi u),
  * (nx_,ny_) = grad(psi)/|grad(psi)|. */
 void orc_gsrc(double dJx, double dJy, double lambda, double W, double psi,
-              double nx_, double ny_, double *out) {
+              double nx_, double ny_, double *out) { /* arguments reassigned by ORC_PLANT 6 */
   double th = tanh(2.0 * psi / W);
+#if ORC_PLANT == 10
+  double sharp = -(lambda / W) * (1.0 - th * th);
+#else
   double sharp = (lambda / W) * (1.0 - th * th);
+#endif
+#if ORC_PLANT == 6
+  dJx = dJy = 0.0;
+#endif
   double vx = dJx / CS2 + sharp * nx_;
   double vy = dJy / CS2 + sharp * ny_;
   for (int i = 0; i < 9; ++i) out[i] = WT[i] * (CX[i] * vx + CY[i] * vy);
@@ -185,13 +205,21 @@ void orc_gsrc(double dJx, double dJy, double lambda, double W, double psi,
 
 /* Eq. 37 with the clip of phi to [0,1] stated after it. */
 double orc_psi(double phi, double W, double xi) {
+#if ORC_PLANT == 8
+  double pc = phi;
+#else
   double pc = phi < 0.0 ? 0.0 : (phi > 1.0 ? 1.0 : phi);
+#endif
   return 0.25 * W * log((pc + xi) / (1.0 - pc + xi));
 }
 
 /* Eq. 2 */
 double orc_chem(double phi, double lap_phi, double W, double sigma) {
+#if ORC_PLANT == 7
+  double beta = 12.0 * sigma / W, kappa = 3.0 * sigma * W;
+#else
   double beta = 12.0 * sigma / W, kappa = 1.5 * sigma * W; /* Sec. 2 */
+#endif
   return 4.0 * beta * phi * (phi - 1.0) * (phi - 0.5) - kappa * lap_phi;
 }
 
@@ -203,7 +231,11 @@ void orc_mrt(const double *f, const double *feq, const double *F,
   for (int k = 0; k < 9; ++k) {
     m[k] = meq[k] = mF[k] = 0.0;
     for (int j = 0; j < 9; ++j) {
+#if ORC_PLANT == 4
+      m[k] += MM[j][k] * f[j];
+#else
       m[k] += MM[k][j] * f[j];
+#endif
       meq[k] += MM[k][j] * feq[j];
       mF[k] += MM[k][j] * F[j];
     }
@@ -226,7 +258,11 @@ static void stencil(const double *chi, int nx, int ny, int x, int y,
     int yn = ((y + CY[i]) % ny + ny) % ny;
     double v = chi[(size_t)yn * nx + xn];
     sx += WT[i] * CX[i] * v / CS2;
+#if ORC_PLANT == 2
+    sy -= WT[i] * CY[i] * v / CS2;
+#else
     sy += WT[i] * CY[i] * v / CS2;
+#endif
     sl += 2.0 * WT[i] * (v - c0) / CS2;
   }
   if (gx) *gx = sx;
@@ -325,11 +361,20 @@ static void node_macros(const orc_params *p, const double *f, size_t n,
       jy += CY[i] * f[i * n + k];
       if (i != 0) sum_nz += f[i * n + k];
     }
+#if ORC_PLANT == 5
+    o->ux = (jx + o->Fx) / o->rho;
+    o->uy = (jy + o->Fy) / o->rho;
+#else
     o->ux = (jx + 0.5 * o->Fx) / o->rho; /* Eq. 28 */
     o->uy = (jy + 0.5 * o->Fy) / o->rho;
+#endif
     double u_gr = o->ux * o->grx + o->uy * o->gry;
+#if ORC_PLANT == 9
+    o->p = CS2 / (1.0 - WT[0]) * (sum_nz + 0.5 * u_gr);
+#else
     o->p = CS2 / (1.0 - WT[0]) *
            (sum_nz + 0.5 * u_gr + o->rho * s_u(0, o->ux, o->uy)); /* Eq. 29 */
+#endif
   } else {
     vortex_u(p, x, y, t, &o->ux, &o->uy);
     o->p = 0.0;

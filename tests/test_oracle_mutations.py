@@ -1,0 +1,37 @@
+"""The pins catch plausible mistakes: each ORC_PLANT variant of the oracle (a
+dropped term, a wrong sign, weight, factor or index, a transposed matrix, a
+missing clip) must fail the oracle's pin suite, while the unplanted oracle
+passes it (the rest of this directory)."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+from conftest import ROOT
+
+PLANTS = {
+    1: "u.grad(rho) dropped from the forcing term (Eq. 21)",
+    2: "sign of the y-gradient stencil flipped (Sec. 3.2)",
+    3: "weight of g_eq at i = 0 wrong (Eq. 31)",
+    4: "transposed M in the collision (Eqs. 24-25)",
+    5: "F instead of F/2 in the velocity (Eq. 28)",
+    6: "d_t(phi u) dropped from the source (Eq. 32)",
+    7: "kappa doubled (Sec. 2)",
+    8: "no clip of phi before psi (Eq. 37)",
+    9: "rho s_0(u) dropped from the pressure (Eq. 29)",
+    10: "sign of the sharpening flux flipped (Eq. 32)",
+}
+PIN_FILES = ["tests/test_oracle_lattice.py", "tests/test_oracle_node.py",
+             "tests/test_oracle_stencil.py", "tests/test_oracle_physics.py"]
+
+
+@pytest.mark.parametrize("plant", sorted(PLANTS), ids=lambda k: f"plant{k}")
+def test_planted_mistake_is_caught(plant):
+    import oracle
+    oracle.build(plant=plant)
+    env = dict(os.environ, ORACLE_PLANT=str(plant))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        *PIN_FILES], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {PLANTS[plant]}\n{r.stdout[-2000:]}"

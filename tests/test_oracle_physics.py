@@ -156,3 +156,19 @@ def test_small_droplet_volume_modified_vs_classical():
         loss[lam] = (o.volume(lab, 2) - v0) / v0
     assert loss[0.0][1] < 0 and loss[0.5][1] < 0
     assert abs(loss[0.5][1]) < 0.5 * abs(loss[0.0][1])
+
+
+def test_uniform_translation_is_fixed_point():
+    # phi const, u const, no force: f = f_eq(p = 0, u) and g = g_eq stay put
+    # exactly (Galilean uniform flow; p from Eq. 29 is 0 for f_eq(p = 0, u)).
+    case = W.base_case(6, 5, sigma=1e-2, rho_l=2.0)
+    phi0 = np.full((5, 6), 0.4)
+    u0 = np.zeros((2, 5, 6))
+    u0[0], u0[1] = 0.03, -0.02
+    o = oracle.Oracle(case, phi0, u0)
+    f0, g0 = o.f.copy(), o.g.copy()
+    o.step(20)
+    phi, ux, uy, p = o.fields()
+    assert np.abs(p).max() < 1e-15
+    assert np.abs(ux - 0.03).max() < 1e-15 and np.abs(uy + 0.02).max() < 1e-15
+    assert np.abs(o.f - f0).max() < 1e-15 and np.abs(o.g - g0).max() < 1e-15
