@@ -260,3 +260,184 @@ class Oracle:
 
     def phi(self):
         return self.g.sum(axis=0)
+
+
+# ---------------------------------------------------------------------------
+# Three-dimensional extension (D3Q19 flow, D3Q7 phase field, SRT limit of
+# Eqs. 25 and 33); arithmetic in lbm_oracle3d.c.
+
+_SRC3 = os.path.join(_HERE, "lbm_oracle3d.c")
+_SO3 = os.path.join(_BUILD, "liblbm_oracle3d.so")
+_lib3 = None
+
+
+def build3(force: bool = False, plant: int = 0) -> str:
+    """Compile the 3-D oracle (same flags as build())."""
+    os.makedirs(_BUILD, exist_ok=True)
+    so = _SO3 if plant == 0 else _SO3.replace(".so", f"_plant{plant}.so")
+    if (not force and os.path.exists(so)
+            and os.path.getmtime(so) >= os.path.getmtime(_SRC3)):
+        return so
+    tmp = so + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           f"-DORC_PLANT={int(plant)}", "-fPIC", "-shared", "-o", tmp, _SRC3, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, so)
+    return so
+
+
+class Params3(ctypes.Structure):
+    """Mirror of ``orc3_params`` in lbm_oracle3d.c."""
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("nz", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("W", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("lam", ctypes.c_double), ("xi", ctypes.c_double),
+        ("tau_g", ctypes.c_double),
+        ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double),
+        ("tau_f_l", ctypes.c_double), ("tau_f_g", ctypes.c_double),
+    ]
+
+
+def lib3():
+    global _lib3
+    with _lock:
+        if _lib3 is None:
+            L = ctypes.CDLL(build3(plant=int(os.environ.get("ORACLE_PLANT", "0"))))
+            P = ctypes.POINTER(Params3)
+            L.orc3_lattices.argtypes = [_I32, _D, _I32, _D]
+            L.orc3_feq.argtypes = [ctypes.c_double, ctypes.c_double, _D, _D]
+            L.orc3_force.argtypes = [_D, _D, _D, _D]
+            L.orc3_geq.argtypes = [ctypes.c_double] * 3 + [_D, _D]
+            L.orc3_gsrc.argtypes = [_D, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, _D, _D]
+            L.orc3_stencil.argtypes = [P, _D, _D, _D, _D, _D]
+            L.orc3_init.argtypes = [P, _D, _D, _D, _D, _D]
+            L.orc3_step.argtypes = [P, _D, _D, _D, ctypes.c_int64]
+            L.orc3_fields.argtypes = [P, _D, _D, _D, _D, _D]
+            _lib3 = L
+    return _lib3
+
+
+def make_params3(case: dict) -> Params3:
+    p = Params3()
+    p.nx, p.ny, p.nz = int(case["nx"]), int(case["ny"]), int(case["nz"])
+    p.W = case["W"]
+    p.sigma = case["sigma"]
+    p.lam = case.get("lambda", 0.5)
+    p.xi = case.get("xi", 1e-10)
+    p.tau_g = case["tau_g"]
+    p.rho_l = case.get("rho_l", 1.0)
+    p.rho_g = case.get("rho_g", 1.0)
+    p.tau_f_l = case.get("tau_f_l", 1.0)
+    p.tau_f_g = case.get("tau_f_g", case.get("tau_f_l", 1.0))
+    return p
+
+
+def _vec(v, n):
+    return np.ascontiguousarray(np.broadcast_to(np.asarray(v, np.float64), (n,)))
+
+
+def lattices3():
+    """(c19 [19,3], w19 [19], c7 [7,3], w7 [7]) as the 3-D oracle uses them."""
+    c19 = (ctypes.c_int32 * 57)()
+    w19 = (ctypes.c_double * 19)()
+    c7 = (ctypes.c_int32 * 21)()
+    w7 = (ctypes.c_double * 7)()
+    lib3().orc3_lattices(c19, w19, c7, w7)
+    return (np.array(c19[:]).reshape(19, 3), np.array(w19[:]),
+            np.array(c7[:]).reshape(7, 3), np.array(w7[:]))
+
+
+def feq3(p, rho, u):
+    out = np.zeros(19)
+    lib3().orc3_feq(p, rho, _dp(_vec(u, 3)), _dp(out))
+    return out
+
+
+def force3(u, F, grad_rho):
+    out = np.zeros(19)
+    lib3().orc3_force(_dp(_vec(u, 3)), _dp(_vec(F, 3)), _dp(_vec(grad_rho, 3)), _dp(out))
+    return out
+
+
+def geq3(phi, mu, lam, u):
+    out = np.zeros(7)
+    lib3().orc3_geq(phi, mu, lam, _dp(_vec(u, 3)), _dp(out))
+    return out
+
+
+def gsrc3(dJ, lam, W, psi, n):
+    out = np.zeros(7)
+    lib3().orc3_gsrc(_dp(_vec(dJ, 3)), lam, W, psi, _dp(_vec(n, 3)), _dp(out))
+    return out
+
+
+def stencil3(chi):
+    """Isotropic D3Q19 gradient and Laplacian of a periodic [nz][ny][nx] field."""
+    chi = np.ascontiguousarray(chi, dtype=np.float64)
+    nz, ny, nx = chi.shape
+    p = Params3()
+    p.nx, p.ny, p.nz = nx, ny, nz
+    p.W, p.tau_g, p.rho_l, p.rho_g, p.tau_f_l, p.tau_f_g = 4.0, 1.0, 1.0, 1.0, 1.0, 1.0
+    gx, gy, gz, lap = (np.zeros_like(chi) for _ in range(4))
+    _check(lib3().orc3_stencil(ctypes.byref(p), _dp(chi), _dp(gx), _dp(gy), _dp(gz),
+                               _dp(lap)), "stencil3")
+    return gx, gy, gz, lap
+
+
+class Oracle3:
+    """State holder around the 3-D oracle: f [19][z][y][x], g [7][z][y][x],
+    phi*u of the previous step [3][z][y][x], after streaming at step t."""
+
+    def __init__(self, case: dict, phi0=None, u0=None, state=None):
+        self.case = dict(case)
+        self.p = make_params3(case)
+        nx, ny, nz = self.p.nx, self.p.ny, self.p.nz
+        self.shape = (nz, ny, nx)
+        if state is not None:
+            f, g, j, t = state
+            self.f = np.ascontiguousarray(f, np.float64).copy()
+            self.g = np.ascontiguousarray(g, np.float64).copy()
+            self.j = np.ascontiguousarray(j, np.float64).copy()
+            self.t = int(t)
+            return
+        self.f = np.zeros((19,) + self.shape)
+        self.g = np.zeros((7,) + self.shape)
+        self.j = np.zeros((3,) + self.shape)
+        self.t = 0
+        phi0 = np.ascontiguousarray(phi0, dtype=np.float64)
+        assert phi0.shape == self.shape
+        u0p = None
+        if u0 is not None:
+            u0 = np.ascontiguousarray(u0, dtype=np.float64)
+            assert u0.shape == (3,) + self.shape
+            u0p = _dp(u0)
+        _check(lib3().orc3_init(ctypes.byref(self.p), _dp(phi0), u0p, _dp(self.f),
+                                _dp(self.g), _dp(self.j)), "init3")
+
+    def step(self, nsteps: int):
+        _check(lib3().orc3_step(ctypes.byref(self.p), _dp(self.f), _dp(self.g),
+                                _dp(self.j), int(nsteps)), "step3")
+        self.t += int(nsteps)
+        return self
+
+    def fields(self):
+        """phi [z][y][x], u [3][z][y][x], p [z][y][x] (Eqs. 28, 29, 35)."""
+        phi = np.zeros(self.shape)
+        u = np.zeros((3,) + self.shape)
+        pr = np.zeros(self.shape)
+        _check(lib3().orc3_fields(ctypes.byref(self.p), _dp(self.f), _dp(self.g),
+                                  _dp(phi), _dp(u), _dp(pr)), "fields3")
+        return phi, u, pr
+
+    def phi(self):
+        return self.g.sum(axis=0)
+
+    def volume(self, labels=None, nregions=1):
+        """Phase volumes sum(phi) per label (FP64), Eq. 35 summed over nodes."""
+        phi = self.phi().ravel()
+        if labels is None:
+            return np.array([phi.sum()])
+        lab = np.asarray(labels).ravel()
+        return np.array([phi[lab == k].sum() for k in range(int(nregions))])

@@ -1,4 +1,4 @@
-"""The pins catch plausible mistakes: each ORC_PLANT variant of the oracle (a
+"""The pins catch plausible mistakes: each ORC_PLANT variant of the oracles (a
 dropped term, a wrong sign, weight, factor or index, a transposed matrix, a
 missing clip) must fail the oracle's pin suite, while the unplanted oracle
 passes it (the rest of this directory)."""
@@ -35,3 +35,28 @@ def test_planted_mistake_is_caught(plant):
                         *PIN_FILES], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode != 0, f"pins did not catch: {PLANTS[plant]}\n{r.stdout[-2000:]}"
+
+
+PLANTS3 = {
+    11: "-c_s^2 I dropped from the forcing tensor (Eq. 21, D3Q19)",
+    12: "D3Q19 sound speed used in the D3Q7 g_eq (Eq. 31)",
+    13: "sign of the z-gradient stencil flipped (Sec. 3.2, D3Q19)",
+    14: "F instead of F/2 in the velocity (Eq. 28)",
+    15: "d_t(phi u) dropped from the source (Eq. 32)",
+    16: "sign of the sharpening flux flipped (Eq. 32)",
+    17: "D2Q9 weight w_0 in the pressure prefactor (Eq. 29)",
+    18: "wrong face-diagonal weight in the stencils (Sec. 3.2)",
+    19: "g streamed against c_z",
+    20: "tau_f from mu(phi)/rho_l instead of mu(phi)/rho(phi) (Eq. 27)",
+}
+
+
+@pytest.mark.parametrize("plant", sorted(PLANTS3), ids=lambda k: f"plant{k}")
+def test_planted_mistake_is_caught_3d(plant):
+    import oracle
+    oracle.build3(plant=plant)
+    env = dict(os.environ, ORACLE_PLANT=str(plant))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not slow", "tests/test_oracle3d.py"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch: {PLANTS3[plant]}\n{r.stdout[-2000:]}"

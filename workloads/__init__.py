@@ -170,3 +170,59 @@ def case_fields(case):
     u0[0] = case["u0"][0]
     u0[1] = case["u0"][1]
     return phi0, u0
+
+
+# ---------------------------------------------------------------------------
+# Three-dimensional inputs ([z][y][x] fields, x fastest).
+
+def base_case3(nx, ny, nz, **kw):
+    c = dict(nx=int(nx), ny=int(ny), nz=int(nz), W=4.0, sigma=1e-3,
+             **{"lambda": 0.5}, xi=1e-10, tau_g=0.8, rho_l=1.0, rho_g=1.0,
+             tau_f_l=1.0, tau_f_g=1.0)
+    c.update(kw)
+    return c
+
+
+def tanh_ball(nx, ny, nz, cx, cy, cz, R, W):
+    """0.5[1 + tanh(2(R - d)/W)], d the distance from (cx, cy, cz) to the
+    nearest periodic image of node (i, j, k)."""
+    def axis(n, c):
+        d = np.arange(n, dtype=np.float64) - c
+        return d - n * np.round(d / n)
+    dx = axis(nx, cx)[None, None, :]
+    dy = axis(ny, cy)[None, :, None]
+    dz = axis(nz, cz)[:, None, None]
+    d = np.sqrt(dx * dx + dy * dy + dz * dz)
+    return 0.5 * (1.0 + np.tanh(2.0 * (R - d) / W))
+
+
+def liquid_column(nx, ny, nz, R, W, eps=0.0, wavelength=None):
+    """A liquid column along z, centred at (nx/2, ny/2), of radius
+    R (1 + eps cos(2 pi z / wavelength)): the perturbed column of the
+    Rayleigh-Plateau set-up (Sec. 4.3, here in three dimensions)."""
+    wl = float(nz if wavelength is None else wavelength)
+    dx = np.arange(nx, dtype=np.float64)[None, :] - 0.5 * nx
+    dy = np.arange(ny, dtype=np.float64)[:, None] - 0.5 * ny
+    r = np.sqrt(dx * dx + dy * dy)[None, :, :]
+    Rz = R * (1.0 + eps * np.cos(2.0 * np.pi * np.arange(nz) / wl))[:, None, None]
+    return 0.5 * (1.0 + np.tanh(2.0 * (Rz - r) / W))
+
+
+def rayleigh_plateau(nx=256, ny=256, nz=1024, R=32.0, eps=0.05, W=4.0,
+                     rho_ratio=10.0, sigma=1e-3, tau_g=0.8, tau_f=1.0, lam=0.5):
+    """Periodic box with a sinusoidally perturbed liquid column, at rest.
+    Returns (case, phi0)."""
+    case = base_case3(nx, ny, nz, W=W, sigma=sigma, tau_g=tau_g, rho_l=rho_ratio,
+                      rho_g=1.0, tau_f_l=tau_f, tau_f_g=tau_f, **{"lambda": lam})
+    return case, liquid_column(nx, ny, nz, R, W, eps)
+
+
+def random_state3(nx, ny, nz, seed, phi_lo=-0.05, phi_hi=1.05):
+    """A random, well-conditioned post-streaming 3-D state for parity tests:
+    g_i = (D3Q7 weight) * phi plus noise, f_i small, phi*u small."""
+    w7 = np.array([0.25] + [0.125] * 6)
+    phi = uniform(seed, (nz, ny, nx), phi_lo, phi_hi)
+    g = w7[:, None, None, None] * phi[None] + uniform(seed + 1, (7, nz, ny, nx), -2e-3, 2e-3)
+    f = uniform(seed + 2, (19, nz, ny, nx), -2e-3, 2e-3)
+    j = uniform(seed + 3, (3, nz, ny, nx), -1e-3, 1e-3)
+    return f, g, j
