@@ -1,6 +1,6 @@
 """Build the CUDA library liblbm_gb300.so in-tree with nvcc for sm_103a.
 
-Three translation units (FP32 kernels, FP64 kernels, host runtime + C ABI)
+The translation units (2-D and 3-D kernels per precision, host runtimes + C ABI)
 are compiled in parallel and linked into one shared library under
 ``paper_2505_10899_gb300/_lib``.  Usage: ``python -m paper_2505_10899_gb300.build``.
 """
@@ -19,7 +19,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 OBJDIR = os.path.join(LIBDIR, "obj")
 SO_NAME = "liblbm_gb300.so"
 SO_PATH = os.path.join(LIBDIR, SO_NAME)
-SOURCES = ["kern_f32.cu", "kern_f64.cu", "lbm_api.cu", "lbm_adjoint.cu", "lbm_noalloc.cu"]
+SOURCES = ["kern_f32.cu", "kern_f64.cu", "lbm_api.cu", "lbm_adjoint.cu", "lbm_noalloc.cu",
+           "kern3_f64.cu", "kern3_f32.cu", "kern3_f16.cu", "lbm3_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

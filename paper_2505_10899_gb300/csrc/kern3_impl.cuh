@@ -1,0 +1,90 @@
+// Launch wrappers of the three-dimensional kernels (see launch3.h).
+#pragma once
+#include "launch3.h"
+#include "lbm3_kernels.cuh"
+
+namespace lbmk3 {
+
+template <typename T, typename S>
+static Args3<T, S> make_args(const Bufs& b, const Host3& h, int parity) {
+  Args3<T, S> a{};
+  for (int k = 0; k < 2; ++k) {
+    a.f[k] = static_cast<S*>(b.f[k]);
+    a.g[k] = static_cast<S*>(b.g[k]);
+    a.g0[k] = static_cast<T*>(b.g0[k]);
+    a.J[k] = static_cast<T*>(b.J[k]);
+  }
+  a.plane = h.plane;
+  a.nx = h.nx, a.ny = h.ny, a.nz = h.nz;
+  a.parity = parity;
+  a.var_tau = h.var_tau;
+  a.beta4 = (T)h.beta4, a.kappa = (T)h.kappa, a.lambda = (T)h.lambda;
+  a.lamW = (T)h.lamW, a.xi = (T)h.xi, a.tfac = (T)h.tfac;
+  a.wg = (T)h.wg, a.hg = (T)h.hg, a.wf = (T)h.wf, a.hf = (T)h.hf;
+  a.rho_g = (T)h.rho_g, a.drho = (T)h.drho, a.mu_g = (T)h.mu_g, a.dmu = (T)h.dmu;
+  return a;
+}
+
+template <typename T, typename S, int BX, int BY, int MODE>
+static cudaError_t launch_tile(const Args3<T, S>& a, cudaStream_t st) {
+  const dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + a.zc - 1) / a.zc);
+  const int par = a.parity, dst = par ^ 1;
+  step3_kernel<T, S, BX, BY, MODE><<<grid, BX * BY, 0, st>>>(
+      a, a.g0[par], a.g[par], a.f[par], a.J[par], a.g0[dst], a.g[dst], a.f[dst], a.J[dst]);
+  return cudaGetLastError();
+}
+
+template <typename T, typename S>
+cudaError_t K3<T, S>::step(const Bufs& b, const Host3& h, int parity, int bx, int by, int zc,
+                           int mode, int32_t* flags, double* vol_part, double* out, int which,
+                           cudaStream_t st) {
+  Args3<T, S> a = make_args<T, S>(b, h, parity);
+  a.zc = zc;
+  a.flags = flags;
+  a.vol_part = vol_part;
+  a.out = out;
+  a.out_which = which;
+  if (mode == kModeFields) return launch_tile<T, S, 32, 8, kModeFields>(a, st);
+  if (bx == 32 && by == 4) return launch_tile<T, S, 32, 4, kModeStep>(a, st);
+  if (bx == 32 && by == 8) return launch_tile<T, S, 32, 8, kModeStep>(a, st);
+  if (bx == 32 && by == 16) return launch_tile<T, S, 32, 16, kModeStep>(a, st);
+  if (bx == 64 && by == 4) return launch_tile<T, S, 64, 4, kModeStep>(a, st);
+  return cudaErrorInvalidValue;
+}
+
+static inline int aux_blocks(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return (int)(b < 152 * 32 ? (b < 1 ? 1 : b) : 152 * 32);
+}
+
+template <typename T, typename S>
+cudaError_t K3<T, S>::init(const Bufs& b, const Host3& h, int parity, const double* d_phi0,
+                           const double* d_u0, cudaStream_t st) {
+  const Args3<T, S> a = make_args<T, S>(b, h, parity);
+  const int64_t n = (int64_t)h.nx * h.ny * h.nz;
+  init3_kernel<T, S><<<aux_blocks(n), 256, 0, st>>>(a, h.beta4, h.kappa, h.lambda, h.rho_g,
+                                                     h.drho, d_phi0, d_u0);
+  init3_rest_kernel<T, S><<<aux_blocks(n), 256, 0, st>>>(a, d_phi0);
+  return cudaGetLastError();
+}
+
+template <typename T, typename S>
+cudaError_t K3<T, S>::plane(const Bufs& b, const Host3& h, int parity, int kind, int i,
+                            double* d_buf, int to_device, cudaStream_t st) {
+  const Args3<T, S> a = make_args<T, S>(b, h, parity);
+  const int64_t n = (int64_t)h.nx * h.ny * h.nz;
+  plane3_kernel<T, S><<<aux_blocks(n), 256, 0, st>>>(a, kind, i, d_buf, to_device);
+  return cudaGetLastError();
+}
+
+template <typename T, typename S>
+cudaError_t K3<T, S>::volume(const Bufs& b, const Host3& h, int parity, const int8_t* labels,
+                             int nregions, double* part, int nparts, double* out,
+                             cudaStream_t st) {
+  const Args3<T, S> a = make_args<T, S>(b, h, parity);
+  volume3_kernel<T, S><<<nparts, 256, 0, st>>>(a, labels, nregions, part);
+  volume3_final<<<nregions, 32, 0, st>>>(part, nparts, kMaxRegions, nregions, out);
+  return cudaGetLastError();
+}
+
+}  // namespace lbmk3

@@ -1,6 +1,8 @@
 """The C ABI library loads on a machine without a GPU and exports every entry
-point that include/lbm_api.h declares; parameter validation needs no device."""
+point that the headers under include/ declare; parameter validation needs no
+device."""
 import ctypes
+import glob
 import os
 import re
 
@@ -8,7 +10,7 @@ import pytest
 
 from conftest import ROOT
 
-HEADER = os.path.join(ROOT, "include", "lbm_api.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 @pytest.fixture(scope="module")
@@ -19,10 +21,12 @@ def L():
     return lbm
 
 
-def declared_symbols():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*[\w\s\*]+?\b(lbm_\w+)\s*\(", src, flags=re.M)))
+def declared_symbols(path=None):
+    names = set()
+    for h in ([path] if path else HEADERS):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"^\s*[\w\s\*]+?\b(lbm3?_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -31,6 +35,10 @@ def test_header_declares_the_boundary():
                      "lbm_workspace_bytes", "lbm_destroy"):
         assert required in names
     assert len(names) >= 20
+    names3 = declared_symbols(os.path.join(ROOT, "include", "lbm3_api.h"))
+    for required in ("lbm3_init", "lbm3_step", "lbm3_volume", "lbm3_workspace_bytes",
+                     "lbm3_destroy"):
+        assert required in names3
 
 
 def test_library_exports_every_declared_symbol(L):
@@ -91,3 +99,19 @@ def test_init_rejects_bad_workspace_without_touching_the_device(L):
 def test_status_strings(L):
     for s in (0, -1, -2, -3, -4, -5, -6):
         assert L.lib().lbm_status_string(s)
+
+
+def test_params3_layout_and_validation(L):
+    from paper_2505_10899_gb300 import lbm3
+    import workloads as W
+    assert ctypes.sizeof(lbm3.lbm3_params) == 6 * 4 + 9 * 8
+    good = lbm3.make_params(W.base_case3(40, 24, 20), "f32")
+    n32 = lbm3.lbm3_workspace_bytes(good)
+    n16 = lbm3.lbm3_workspace_bytes(lbm3.make_params(W.base_case3(40, 24, 20), "f16"))
+    n64 = lbm3.lbm3_workspace_bytes(lbm3.make_params(W.base_case3(40, 24, 20), "f64"))
+    n = 40 * 24 * 20
+    assert n16 < n32 < n64 and n32 > n * (2 * 26 * 4 + 2 * 3 * 4)
+    for bad in (dict(tau_g=0.5), dict(W=0.0), dict(rho_l=-1.0), dict(tau_f_l=0.4),
+                dict(nz=0), dict(nx=1 << 16, ny=1 << 16, nz=2)):
+        case = {**W.base_case3(40, 24, 20), **bad}
+        assert lbm3.lbm3_workspace_bytes(lbm3.make_params(case, "f32")) == 0
