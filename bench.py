@@ -37,6 +37,8 @@ sys.path.insert(0, ROOT)
 import workloads as W  # noqa: E402
 
 BYTES_PER_NODE = {"f32": 160, "f64": 320}  # f, g read+write, phi*u read+write
+# 3-D: 19 f + 7 g read+write, phi*u (3) read+write; FP16 storage keeps phi*u in FP32
+BYTES_PER_NODE_3D = {"f32": 232, "f16": 128, "f64": 464}
 WORKLOAD_NAME = ("batched droplets: 512 independent 2-D cases, square edges from "
                  "{64,96,128,192,256,384,512}, R in [0.05,0.3]*edge, translation "
                  "speed in [0,0.02] lu/step, density ratio 1:1..1:10, W=4, "
@@ -59,6 +61,13 @@ def parse():
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register, 2 bulk-copy")
     ap.add_argument("--tiling", type=str, default=None, help="BX,ROWS (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--only-3d", action="store_true",
+                    help="only the 3-D Rayleigh-Plateau numbers (D3Q19 + D3Q7)")
+    ap.add_argument("--grid3", type=str, default="256,256,1024", help="NX,NY,NZ of the 3-D box")
+    ap.add_argument("--prec3", type=str, default="f32,f16,f64", help="3-D storage precisions")
+    ap.add_argument("--steps3", type=int, default=50, help="timed 3-D steps (FP64: a fifth)")
+    ap.add_argument("--tiling3", type=str, default=None,
+                    help="VARIANT,BX,BY,ZC for the 3-D step (default: autotuned)")
     ap.add_argument("--only-adjoint", action="store_true",
                     help="print the reverse-mode timing only (profiling aid)")
     return ap.parse_args()
@@ -409,6 +418,77 @@ def run_extras(args, cases, dev):
     vort["phi_maxdiff_f32_vs_f64"] = float(np.abs(fin["f32"] - fin["f64"]).max())
     out["single_vortex"] = vort
     out["adjoint"] = adjoint_timing(dev)
+    out["rayleigh_plateau_3d"] = rp3d_timing(dev, steps=args.steps3)
+    return out
+
+
+def rp3d_timing(dev, grid=(256, 256, 1024), precisions=("f32", "f16", "f64"), steps=50,
+                tiling=None):
+    """3-D Rayleigh-Plateau column (D3Q19 flow + D3Q7 phase field, SRT limit of
+    the model): MLUPS per storage precision in the autotuned launch with its
+    HBM roofline, the phase-volume drift over the timed steps, and the largest
+    |phi| difference of each precision from the FP64 GPU path over the whole
+    box after 20 steps (the FP64 path itself matches the FP64 oracle to 1e-12
+    in the GPU tests, at this size on sampled blocks)."""
+    import torch
+    from paper_2505_10899_gb300 import lbm3
+
+    nx, ny, nz = grid
+    R = 32.0 * min(nx, ny) / 256.0
+    case, phi0 = W.rayleigh_plateau(nx, ny, nz, R=R)
+    n = nx * ny * nz
+    peak, peak_kind = measured_peaks()
+    out = {"grid": f"{nx}x{ny}x{nz}", "nodes": n, "R": R, "eps": 0.05, "W": case["W"],
+           "rho_ratio": case["rho_l"] / case["rho_g"], "sigma": case["sigma"],
+           "tau_g": case["tau_g"], "tau_f": case["tau_f_l"], "l2": "state far larger than L2"}
+    ref = None
+    order = sorted(precisions, key=lambda p: p != "f64")  # FP64 first: the reference
+    for prec in order:
+        s = lbm3.Sim3(case, phi0, None, precision=prec)
+        s.step(20)
+        phi20 = s.fields()[0]
+        if prec == "f64":
+            ref = phi20
+        err = None if ref is None else float(np.abs(phi20 - ref).max())
+        del phi20
+        s.close()
+        s = lbm3.Sim3(case, phi0, None, precision=prec)
+        if tiling:
+            v, bx, by, zc = tiling
+            s.set_kernel(0)
+            s.set_tiling(bx, by, zc)
+            s.set_kernel(v)
+        else:
+            s.autotune(2 if prec != "f64" else 1)
+        s.step(3)
+        v0 = s.volume()[0]
+        K = steps if prec != "f64" else max(2, steps // 5)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        a.record(s.stream)
+        s.step(K)
+        b.record(s.stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / K
+        v1 = s.volume()[0]
+        bpn = BYTES_PER_NODE_3D[prec]
+        achieved = bpn * n / (ms * 1e-3) / 1e9
+        var = {1: "step3_kernel", 2: "step3_async_kernel<2 stages>",
+               3: "step3_async_kernel<3 stages>"}[s.kernel()]
+        out[prec] = {
+            "mlups": round(n / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 4),
+            "steps": K, "kernel": var, "tiling": dict(zip(("bx", "by", "zc", "ctas"), s.tiling())),
+            "chosen_by": "fixed" if tiling else "autotune",
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "algorithmic_bytes_per_node": bpn, "peak_kind": peak_kind},
+            "volume_drift_rel": float(v1 / v0 - 1.0),
+            "phi_maxdiff_vs_f64_20steps": err,
+            "status": s.status(),
+        }
+        s.close()
+        del s
+        torch.cuda.empty_cache()
     return out
 
 
@@ -546,6 +626,14 @@ def main():
     if args.only_adjoint:
         import torch
         print(json.dumps({"adjoint": adjoint_timing(torch.device("cuda", 0))}), flush=True)
+        return
+    if args.only_3d:
+        import torch
+        grid = tuple(int(v) for v in args.grid3.split(","))
+        til = tuple(int(v) for v in args.tiling3.split(",")) if args.tiling3 else None
+        print(json.dumps({"rayleigh_plateau_3d": rp3d_timing(
+            torch.device("cuda", 0), grid, tuple(args.prec3.split(",")), args.steps3, til)}),
+            flush=True)
         return
     if args.impl == "reference":
         run_reference(args)

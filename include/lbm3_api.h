@@ -39,10 +39,15 @@ extern "C" {
 
 typedef struct lbm3_handle lbm3_handle; /* opaque; freed by lbm3_destroy */
 
-/* Storage precision of the populations.  LBM3_F16: f and the six moving g
- * populations stored as IEEE binary16, arithmetic, g_0, phi*u and all sums
- * in FP32; g_0 is formed from the rounded movers so that sum g = phi holds
- * to FP32 rounding (the phase volume is not eroded by the FP16 rounding). */
+/* Storage precision of the populations.
+ *   LBM3_F64: everything FP64.
+ *   LBM3_F32: populations and phi*u FP32, arithmetic FP32.
+ *   LBM3_F16: f and the six moving g populations stored as IEEE binary16,
+ *     arithmetic and phi*u FP32.
+ * Under FP32 arithmetic (F32, F16) the rest population g_0 is stored as an
+ * unevaluated sum of two FP32 values and formed exactly from phi minus the
+ * stored (rounded) movers, so that sum g = phi, hence the phase volume, is
+ * kept to ~2^-48 per node and step whatever the rounding of the movers. */
 enum { LBM3_F64 = LBM_F64, LBM3_F32 = LBM_F32, LBM3_F16 = 2 };
 
 typedef struct {
@@ -118,12 +123,22 @@ int lbm3_set_tiling(lbm3_handle* h, int32_t bx, int32_t by, int32_t zc);
 int lbm3_get_tiling(const lbm3_handle* h, int32_t* bx, int32_t* by, int32_t* zc,
                     int32_t* n_ctas);
 
-/* Time every allowed (bx, by) with a few zc choices (`trials` launches each,
- * CUDA events) and keep the fastest.  Trial launches write only the buffers
- * the next step overwrites; the state and the step index do not change.
- * Outputs may be NULL.  Synchronises. */
-int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* bx, int32_t* by,
-                  int32_t* zc, double* best_ms);
+/* Step-kernel variant: 0 = automatic (the register kernel until
+ * lbm3_autotune picks the fastest), 1 = register-pipelined loads (any
+ * precision and tiling), 2 / 3 = asynchronous 4-byte copies (cp.async)
+ * through shared memory, 2 / 3 stages deep (LBM3_F32 only; tiles (32, 4),
+ * (32, 8), (64, 4)).  All variants run the same per-node arithmetic.
+ * lbm3_get_kernel returns the variant in use (1, 2 or 3). */
+int lbm3_set_kernel(lbm3_handle* h, int32_t variant);
+int32_t lbm3_get_kernel(const lbm3_handle* h);
+
+/* Time every allowed (variant, bx, by) with a few zc choices (`trials`
+ * launches each, CUDA events) and keep the fastest; with a variant set by
+ * lbm3_set_kernel only that variant is tried.  Trial launches write only the
+ * buffers the next step overwrites; the state and the step index do not
+ * change.  Outputs may be NULL.  Synchronises. */
+int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* variant, int32_t* bx,
+                  int32_t* by, int32_t* zc, double* best_ms);
 
 /* Synchronise and report device error flags (LBM_OK, LBM_ERR_NONFINITE,
  * LBM_ERR_CUDA); clears them. */

@@ -1,6 +1,9 @@
 // Launch wrappers of the three-dimensional kernels (see launch3.h).
 #pragma once
+#include <type_traits>
+
 #include "launch3.h"
+#include "lbm3_async.cuh"
 #include "lbm3_kernels.cuh"
 
 namespace lbmk3 {
@@ -12,6 +15,7 @@ static Args3<T, S> make_args(const Bufs& b, const Host3& h, int parity) {
     a.f[k] = static_cast<S*>(b.f[k]);
     a.g[k] = static_cast<S*>(b.g[k]);
     a.g0[k] = static_cast<T*>(b.g0[k]);
+    a.g0lo[k] = static_cast<T*>(b.g0lo[k]);
     a.J[k] = static_cast<T*>(b.J[k]);
   }
   a.plane = h.plane;
@@ -30,14 +34,51 @@ static cudaError_t launch_tile(const Args3<T, S>& a, cudaStream_t st) {
   const dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + a.zc - 1) / a.zc);
   const int par = a.parity, dst = par ^ 1;
   step3_kernel<T, S, BX, BY, MODE><<<grid, BX * BY, 0, st>>>(
-      a, a.g0[par], a.g[par], a.f[par], a.J[par], a.g0[dst], a.g[dst], a.f[dst], a.J[dst]);
+      a, a.g0[par], a.g0lo[par], a.g[par], a.f[par], a.J[par], a.g0[dst], a.g0lo[dst], a.g[dst],
+      a.f[dst], a.J[dst]);
+  return cudaGetLastError();
+}
+
+template <int BX, int BY, int NST>
+static cudaError_t launch_async(const Args3<float, float>& a, cudaStream_t st) {
+  constexpr size_t bytes = async_smem_bytes<BX, BY, NST>();
+  static bool attr_set = false;  // per instantiation, per process (one device)
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(step3_async_kernel<BX, BY, NST>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const dim3 grid((a.nx + BX - 1) / BX, (a.ny + BY - 1) / BY, (a.nz + a.zc - 1) / a.zc);
+  const int par = a.parity, dst = par ^ 1;
+  step3_async_kernel<BX, BY, NST><<<grid, BX * BY, bytes, st>>>(
+      a, a.g0[par], a.g0lo[par], a.g[par], a.f[par], a.J[par], a.g0[dst], a.g0lo[dst], a.g[dst],
+      a.f[dst], a.J[dst]);
   return cudaGetLastError();
 }
 
 template <typename T, typename S>
-cudaError_t K3<T, S>::step(const Bufs& b, const Host3& h, int parity, int bx, int by, int zc,
-                           int mode, int32_t* flags, double* vol_part, double* out, int which,
-                           cudaStream_t st) {
+static cudaError_t step_async(const Args3<T, S>& a, int variant, int bx, int by,
+                              cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value) {
+    if (variant == kVarAsync2) {
+      if (bx == 32 && by == 4) return launch_async<32, 4, 2>(a, st);
+      if (bx == 32 && by == 8) return launch_async<32, 8, 2>(a, st);
+      if (bx == 64 && by == 4) return launch_async<64, 4, 2>(a, st);
+    } else if (variant == kVarAsync3) {
+      if (bx == 32 && by == 4) return launch_async<32, 4, 3>(a, st);
+      if (bx == 32 && by == 8) return launch_async<32, 8, 3>(a, st);
+      if (bx == 64 && by == 4) return launch_async<64, 4, 3>(a, st);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename T, typename S>
+cudaError_t K3<T, S>::step(const Bufs& b, const Host3& h, int parity, int variant, int bx,
+                           int by, int zc, int mode, int32_t* flags, double* vol_part,
+                           double* out, int which, cudaStream_t st) {
   Args3<T, S> a = make_args<T, S>(b, h, parity);
   a.zc = zc;
   a.flags = flags;
@@ -45,6 +86,7 @@ cudaError_t K3<T, S>::step(const Bufs& b, const Host3& h, int parity, int bx, in
   a.out = out;
   a.out_which = which;
   if (mode == kModeFields) return launch_tile<T, S, 32, 8, kModeFields>(a, st);
+  if (variant != kVarRegs) return step_async(a, variant, bx, by, st);
   if (bx == 32 && by == 4) return launch_tile<T, S, 32, 4, kModeStep>(a, st);
   if (bx == 32 && by == 8) return launch_tile<T, S, 32, 8, kModeStep>(a, st);
   if (bx == 32 && by == 16) return launch_tile<T, S, 32, 16, kModeStep>(a, st);

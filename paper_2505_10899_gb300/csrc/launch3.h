@@ -12,6 +12,7 @@ struct Bufs {
   void* f[2];
   void* g[2];
   void* g0[2];
+  void* g0lo[2];  // null under FP64 arithmetic
   void* J[2];
 };
 
@@ -30,11 +31,22 @@ inline int64_t n_ctas(int nx, int ny, int nz, int bx, int by, int zc) {
   return (int64_t)((nx + bx - 1) / bx) * ((ny + by - 1) / by) * ((nz + zc - 1) / zc);
 }
 
+// Step-kernel variants: register-pipelined loads (any precision), or
+// asynchronous copies through shared memory with 2 or 3 stages (FP32 only).
+enum { kVarRegs = 1, kVarAsync2 = 2, kVarAsync3 = 3 };
+
+inline bool variant_ok(int variant, int precision_is_f32, int bx, int by) {
+  if (variant == kVarRegs) return tile_ok(bx, by);
+  if (variant == kVarAsync2 || variant == kVarAsync3)
+    return precision_is_f32 && ((bx == 32 && (by == 4 || by == 8)) || (bx == 64 && by == 4));
+  return false;
+}
+
 template <typename T, typename S>
 struct K3 {
-  static cudaError_t step(const Bufs& b, const Host3& h, int parity, int bx, int by, int zc,
-                          int mode, int32_t* flags, double* vol_part, double* out, int which,
-                          cudaStream_t st);
+  static cudaError_t step(const Bufs& b, const Host3& h, int parity, int variant, int bx, int by,
+                          int zc, int mode, int32_t* flags, double* vol_part, double* out,
+                          int which, cudaStream_t st);
   static cudaError_t init(const Bufs& b, const Host3& h, int parity, const double* d_phi0,
                           const double* d_u0, cudaStream_t st);
   static cudaError_t plane(const Bufs& b, const Host3& h, int parity, int kind, int i,

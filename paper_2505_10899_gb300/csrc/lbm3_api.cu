@@ -37,6 +37,8 @@ struct lbm3_handle {
   double* staging = nullptr;
   double* track = nullptr;
   int bx = 32, by = 8, zc = 32;
+  int variant = lbmk3::kVarRegs;  // step-kernel variant in use
+  int variant_req = 0;            // requested: 0 automatic
   int64_t t = 0;
   int parity = 0;
   cudaGraphExec_t gexec = nullptr;
@@ -89,7 +91,7 @@ int check(const lbm3_params* p) {
 int zc_min(const lbm3_params& p) { return std::min(8, p.nz); }
 
 struct Carve {
-  size_t f, g, g0, J, lab, part, vol, staging, total;
+  size_t f, g, g0, g0lo, J, lab, part, vol, staging, total;
   int64_t plane, part_cap;
 };
 
@@ -105,6 +107,8 @@ Carve carve(const lbm3_params& p) {
   o = align_up(o + 2 * 6 * (size_t)c.plane * ss);
   c.g0 = o;
   o = align_up(o + 2 * (size_t)c.plane * es);
+  c.g0lo = o;  // FP32 arithmetic only: low part of g_0
+  if (p.precision != LBM3_F64) o = align_up(o + 2 * (size_t)c.plane * es);
   c.J = o;
   o = align_up(o + 2 * 3 * (size_t)c.plane * es);
   c.lab = o;
@@ -162,8 +166,8 @@ cudaError_t launch_step(lbm3_handle* h, cudaStream_t s, int parity, int mode, do
   const int64_t nc = lbmk3::n_ctas(h->prm.nx, h->prm.ny, h->prm.nz, h->bx, h->by, h->zc);
   double* vp = (mode == lbmk3::kModeStep && track) ? h->part : nullptr;
   cudaError_t e = dispatch(h->prm.precision, [&](auto k) {
-    return decltype(k)::step(h->b, h->hp, parity, h->bx, h->by, h->zc, mode, h->flags, vp, out,
-                             which, s);
+    return decltype(k)::step(h->b, h->hp, parity, h->variant, h->bx, h->by, h->zc, mode,
+                             h->flags, vp, out, which, s);
   });
   if (e == cudaSuccess && vp) e = lbmk3::volume3_final_launch(h->part, (int)nc, 1, 1, h->track, s);
   return e;
@@ -256,6 +260,7 @@ int lbm3_init(const lbm3_params* p, void* d_ws, size_t ws_bytes, const double* h
     h->b.f[k] = h->ws + c.f + (size_t)k * 19 * c.plane * ss;
     h->b.g[k] = h->ws + c.g + (size_t)k * 6 * c.plane * ss;
     h->b.g0[k] = h->ws + c.g0 + (size_t)k * c.plane * es;
+    h->b.g0lo[k] = p->precision == LBM3_F64 ? nullptr : h->ws + c.g0lo + (size_t)k * c.plane * es;
     h->b.J[k] = h->ws + c.J + (size_t)k * 3 * c.plane * es;
   }
   h->flags = reinterpret_cast<int32_t*>(h->ws);
@@ -409,13 +414,31 @@ int lbm3_set_tiling(lbm3_handle* h, int32_t bx, int32_t by, int32_t zc) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (!lbmk3::tile_ok(bx, by)) return fail(LBM_ERR_ARG, "unsupported (bx, by)");
   if (zc < zc_min(h->prm) || zc > h->prm.nz) return fail(LBM_ERR_ARG, "zc out of range");
+  const int f32 = h->prm.precision == LBM3_F32;
+  if (h->variant_req && !lbmk3::variant_ok(h->variant_req, f32, bx, by))
+    return fail(LBM_ERR_ARG, "tiling not available for the requested kernel variant");
   h->bx = bx, h->by = by, h->zc = zc;
+  if (!lbmk3::variant_ok(h->variant, f32, bx, by)) h->variant = lbmk3::kVarRegs;
   drop_graph(h);
   return LBM_OK;
 }
 
-int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* obx, int32_t* oby, int32_t* ozc,
-                  double* best_ms) {
+int lbm3_set_kernel(lbm3_handle* h, int32_t variant) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (variant < 0 || variant > lbmk3::kVarAsync3) return fail(LBM_ERR_ARG, "variant in [0, 3]");
+  const int f32 = h->prm.precision == LBM3_F32;
+  if (variant && !lbmk3::variant_ok(variant, f32, h->bx, h->by))
+    return fail(LBM_ERR_ARG, "variant not available for this precision or tiling");
+  h->variant_req = variant;
+  h->variant = variant ? variant : lbmk3::kVarRegs;
+  drop_graph(h);
+  return LBM_OK;
+}
+
+int32_t lbm3_get_kernel(const lbm3_handle* h) { return h ? h->variant : -1; }
+
+int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* ovar, int32_t* obx, int32_t* oby,
+                  int32_t* ozc, double* best_ms) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (trials < 1 || trials > 100) return fail(LBM_ERR_ARG, "trials must lie in [1, 100]");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -424,41 +447,48 @@ int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* obx, int32_t* oby, in
     cudaEventDestroy(e0);
     return fail(LBM_ERR_CUDA, "event create failed");
   }
-  const int kb = h->bx, kby = h->by, kz = h->zc;
+  const int f32 = h->prm.precision == LBM3_F32;
+  const int kv = h->variant, kb = h->bx, kby = h->by, kz = h->zc;
   double best = 1e300;
-  int bb = kb, bby = kby, bz = kz;
+  int bv = kv, bb = kb, bby = kby, bz = kz;
   int rc = LBM_OK;
   const int tiles[4][2] = {{32, 4}, {32, 8}, {32, 16}, {64, 4}};
-  for (const auto& tl : tiles) {
-    for (int zc : {8, 16, 32, 64}) {
-      const int z = std::min(std::max(zc, zc_min(h->prm)), h->prm.nz);
-      if (zc > 8 && z != zc) continue;  // nz too small for this zc
-      h->bx = tl[0], h->by = tl[1], h->zc = z;
-      // trial steps read the current source buffers and write the other set,
-      // which the next real step overwrites: the state does not change
-      cudaError_t e = launch_step(h, h->stream, h->parity, lbmk3::kModeStep, nullptr, 0, false);
-      if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-      for (int k = 0; k < trials && e == cudaSuccess; ++k)
-        e = launch_step(h, h->stream, h->parity, lbmk3::kModeStep, nullptr, 0, false);
-      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-      float ms = 0.f;
-      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-      if (e != cudaSuccess) {
-        rc = fail(LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-        break;
+  for (int v = lbmk3::kVarRegs; v <= lbmk3::kVarAsync3 && rc == LBM_OK; ++v) {
+    if (h->variant_req && v != h->variant_req) continue;
+    for (const auto& tl : tiles) {
+      if (!lbmk3::variant_ok(v, f32, tl[0], tl[1])) continue;
+      for (int zc : {8, 16, 32, 64}) {
+        const int z = std::min(std::max(zc, zc_min(h->prm)), h->prm.nz);
+        if (zc > 8 && z != zc) continue;  // nz too small for this zc
+        h->variant = v, h->bx = tl[0], h->by = tl[1], h->zc = z;
+        // trial steps read the current source buffers and write the other
+        // set, which the next real step overwrites: the state does not change
+        cudaError_t e = launch_step(h, h->stream, h->parity, lbmk3::kModeStep, nullptr, 0, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int k = 0; k < trials && e == cudaSuccess; ++k)
+          e = launch_step(h, h->stream, h->parity, lbmk3::kModeStep, nullptr, 0, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+          rc = fail(LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+          break;
+        }
+        if (ms / trials < best) best = ms / trials, bv = v, bb = tl[0], bby = tl[1], bz = z;
       }
-      if (ms / trials < best) best = ms / trials, bb = tl[0], bby = tl[1], bz = z;
+      if (rc != LBM_OK) break;
     }
-    if (rc != LBM_OK) break;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  h->variant = rc == LBM_OK ? bv : kv;
   h->bx = rc == LBM_OK ? bb : kb;
   h->by = rc == LBM_OK ? bby : kby;
   h->zc = rc == LBM_OK ? bz : kz;
   drop_graph(h);
   if (rc != LBM_OK) return rc;
+  if (ovar) *ovar = bv;
   if (obx) *obx = bb;
   if (oby) *oby = bby;
   if (ozc) *ozc = bz;

@@ -14,6 +14,15 @@
 // The ring has 4 slots, so one barrier per plane separates A(z+1) from B(z)
 // and B(z) from A(z+3).  The pulled g of the tile nodes stay in registers
 // from A (as the next plane) to B.
+//
+// Phase volume in FP32 arithmetic: phi is conserved node by node only if the
+// stored rest population is exactly phi minus the stored movers.  A rounded
+// FP32 g_0 leaves a rounding error per node and step whose bias (the slowly
+// varying interface values round the same way step after step) accumulates
+// into a volume drift.  So under FP32 arithmetic g_0 is kept as an unevaluated
+// sum of two floats (hi + lo), and the sums phi = sum g and S = sum of the
+// stored movers are formed exactly with error-free transformations (TwoSum,
+// Knuth, TAOCP vol. 2, 4.2.2); g_0 = phi - S is then exact to ~2^-48.
 #pragma once
 #include <cstdint>
 #include <cuda_fp16.h>
@@ -103,12 +112,14 @@ __device__ __forceinline__ uint32_t src_of(const Offs& o) {
   return o.z[1 - Lat::cz[I]] + o.y[1 - Lat::cy[I]] + o.x[1 - Lat::cx[I]];
 }
 
-// Pull the 7 phase-field populations of one node: g0 from its own position,
-// the 6 movers from plane i-1 of gm at the source node.
+// Pull the 7 phase-field populations of one node: g0 (and its low part) from
+// its own position, the 6 movers from plane i-1 of gm at the source node.
 template <typename T, typename S>
-__device__ __forceinline__ void pull_g(const T* __restrict__ g0, const S* __restrict__ gm,
-                                       int64_t P, const Offs& o, T (&G)[7]) {
+__device__ __forceinline__ void pull_g(const T* __restrict__ g0, const T* __restrict__ g0lo,
+                                       const S* __restrict__ gm, int64_t P, const Offs& o,
+                                       T (&G)[7], T& Glo) {
   G[0] = g0[src_of<0>(o)];
+  Glo = g0lo ? g0lo[src_of<0>(o)] : T(0);
   G[1] = Conv<T, S>::ld(gm + 0 * P + src_of<1>(o));
   G[2] = Conv<T, S>::ld(gm + 1 * P + src_of<2>(o));
   G[3] = Conv<T, S>::ld(gm + 2 * P + src_of<3>(o));
@@ -120,6 +131,40 @@ __device__ __forceinline__ void pull_g(const T* __restrict__ g0, const S* __rest
 template <typename T>
 __device__ __forceinline__ T sum7(const T (&G)[7]) {
   return ((G[0] + (G[1] + G[2])) + (G[3] + G[4])) + (G[5] + G[6]);
+}
+
+// Error-free sum: s + e == a + b exactly (TwoSum, no ordering condition).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// phi = sum g as a float pair (hi, lo): exact up to the rounding of lo.
+__device__ __forceinline__ void sum_g_ff(const float (&G)[7], float glo, float& hi, float& lo) {
+  float s, e;
+  two_sum(G[0], G[1], s, e);
+  lo = e + glo;
+#pragma unroll
+  for (int i = 2; i < 7; ++i) {
+    two_sum(s, G[i], s, e);
+    lo += e;
+  }
+  hi = s;
+}
+
+// phi of one node from its pulled populations, and its float-pair parts.
+template <typename T>
+__device__ __forceinline__ T phi_of(const T (&G)[7], T glo, T& hi, T& lo) {
+  hi = sum7(G);
+  lo = T(0);
+  return hi;
+}
+template <>
+__device__ __forceinline__ float phi_of<float>(const float (&G)[7], float glo, float& hi,
+                                               float& lo) {
+  sum_g_ff(G, glo, hi, lo);
+  return hi + lo;
 }
 
 template <int I, typename T, typename S>
@@ -201,8 +246,9 @@ struct Out3 {
 };
 
 template <typename T, typename S, int MODE>
-__device__ __forceinline__ Out3<T> node3(const Args3<T, S>& a, T (&F)[19], T (&G)[7],
-                                         const T (&jp)[3], const St3<T>& P, const St3<T>& Q) {
+__device__ __forceinline__ Out3<T> node3(const Args3<T, S>& a, T (&F)[19], T (&G)[7], T& Glo,
+                                         T phh, T phl, const T (&jp)[3], const St3<T>& P,
+                                         const St3<T>& Q) {
   const T phi = P.C;
   T gpx, gpy, gpz;
   grad12(P, gpx, gpy, gpz);
@@ -287,18 +333,36 @@ __device__ __forceinline__ Out3<T> node3(const Args3<T, S>& a, T (&F)[19], T (&G
 #pragma unroll
   for (int i = 1; i < 7; ++i) G[i] = Conv<T, S>::round(G[i]);
   // rest population from the conserved zeroth moment: sum g* = phi
-  G[0] = phi - (((G[1] + G[2]) + (G[3] + G[4])) + (G[5] + G[6]));
+  if (sizeof(T) == 8) {
+    G[0] = phi - (((G[1] + G[2]) + (G[3] + G[4])) + (G[5] + G[6]));
+    Glo = T(0);
+  } else {
+    // float pair: g0 = (phh + phl) - S with S the exact sum of the stored movers
+    float sh, sl, e;
+    two_sum((float)G[1], (float)G[2], sh, sl);
+#pragma unroll
+    for (int i = 3; i < 7; ++i) {
+      two_sum(sh, (float)G[i], sh, e);
+      sl += e;
+    }
+    float dh, de;
+    two_sum((float)phh, -sh, dh, de);
+    const float dl = (de + ((float)phl - sl));
+    float hi, lo;
+    two_sum(dh, dl, hi, lo);
+    G[0] = (T)hi;
+    Glo = (T)lo;
+  }
   return o;
 }
 
 // ---- the step kernel --------------------------------------------------------
 template <typename T, typename S, int BX, int BY, int MODE>
-__global__ void __launch_bounds__(BX* BY) step3_kernel(const Args3<T, S> a, const T* __restrict__ g0s,
-                                                       const S* __restrict__ gms,
-                                                       const S* __restrict__ fs,
-                                                       const T* __restrict__ js, T* __restrict__ g0d,
-                                                       S* __restrict__ gmd, S* __restrict__ fd,
-                                                       T* __restrict__ jd) {
+__global__ void __launch_bounds__(BX* BY) step3_kernel(
+    const Args3<T, S> a, const T* __restrict__ g0s, const T* __restrict__ g0ls,
+    const S* __restrict__ gms, const S* __restrict__ fs, const T* __restrict__ js,
+    T* __restrict__ g0d, T* __restrict__ g0ld, S* __restrict__ gmd, S* __restrict__ fd,
+    T* __restrict__ jd) {
   constexpr int NH = 2 * (BX + 2) + 2 * BY;  // halo ring of the tile
   static_assert(NH <= BX * BY, "tile too small for its halo");
   __shared__ Ring3<T, BX, BY> ring;
@@ -331,32 +395,35 @@ __global__ void __launch_bounds__(BX* BY) step3_kernel(const Args3<T, S> a, cons
   const int zb = blockIdx.z * a.zc;
   const int ze = min(zb + a.zc, nz);
 
-  // phase A for plane zl into ring slot s; own pulled g returned in G
-  auto phaseA = [&](int zl, int s, T (&G)[7]) {
+  // phase A for plane zl into ring slot s; own pulled g returned in G, Glo and
+  // phi as the float pair (ph, pl)
+  auto phaseA = [&](int zl, int s, T (&G)[7], T& Glo, T& ph, T& pl) {
     const int zw = zl < 0 ? zl + nz : (zl >= nz ? zl - nz : zl);
     set_z(own, zw, nz, nxy);
-    pull_g(g0s, gms, P, own, G);
-    T H[7];
+    pull_g(g0s, g0ls, gms, P, own, G, Glo);
+    T H[7], Hlo;
     if (has_h) {
       set_z(hal, zw, nz, nxy);
-      pull_g(g0s, gms, P, hal, H);
+      pull_g(g0s, g0ls, gms, P, hal, H, Hlo);
     }
-    const T phi = sum7(G);
+    const T phi = phi_of(G, Glo, ph, pl);
     typename N3<T>::pair v;
     v.x = phi;
     v.y = psi3(phi, a.xi);
     ring.pq[s][ty + 1][tx + 1] = v;
     if (has_h) {
-      const T ph = sum7(H);
-      v.x = ph;
-      v.y = psi3(ph, a.xi);
+      // a halo node's phi only enters this tile's stencils: the plain sum
+      // (within an ulp of the owner's value) is enough there
+      const T phh = sum7(H) + Hlo;
+      v.x = phh;
+      v.y = psi3(phh, a.xi);
       ring.pq[s][hy + 1][hx + 1] = v;
     }
   };
 
-  T Gc[7], Gn[7];
-  phaseA(zb - 1, (zb + 3) & 3, Gn);
-  phaseA(zb, zb & 3, Gc);
+  T Gc[7], Gn[7], Gcl, Gnl, pch, pcl, pnh, pnl;
+  phaseA(zb - 1, (zb + 3) & 3, Gn, Gnl, pnh, pnl);
+  phaseA(zb, zb & 3, Gc, Gcl, pch, pcl);
   double vsum = 0.0;
   for (int z = zb; z < ze; ++z) {
     // independent loads of this plane first
@@ -370,20 +437,21 @@ __global__ void __launch_bounds__(BX* BY) step3_kernel(const Args3<T, S> a, cons
       jp[1] = js[P + node];
       jp[2] = js[2 * P + node];
     }
-    phaseA(z + 1, (z + 1) & 3, Gn);
+    phaseA(z + 1, (z + 1) & 3, Gn, Gnl, pnh, pnl);
     __syncthreads();
     if (valid) {
       St3<T> SP, SQ;
       read_st(ring, (z + 3) & 3, z & 3, (z + 1) & 3, ty + 1, tx + 1, SP, SQ);
-      const Out3<T> o = node3<T, S, MODE>(a, F, Gc, jp, SP, SQ);
+      const Out3<T> o = node3<T, S, MODE>(a, F, Gc, Gcl, pch, pcl, jp, SP, SQ);
       const T phi = SP.C;
       if (!(isfinite(phi) && isfinite(o.ux + o.uy + o.uz))) atomicOr(a.flags, kFlagNonFinite);
       if (MODE == kModeStep) {
-        vsum += (double)phi;
+        if (a.vol_part) vsum += (double)phi;
         jd[node] = phi * o.ux;
         jd[P + node] = phi * o.uy;
         jd[2 * P + node] = phi * o.uz;
         g0d[node] = Gc[0];
+        if (g0ld) g0ld[node] = Gcl;
 #pragma unroll
         for (int i = 1; i < 7; ++i) gmd[(i - 1) * P + node] = Conv<T, S>::st(Gc[i]);
 #pragma unroll
@@ -399,6 +467,7 @@ __global__ void __launch_bounds__(BX* BY) step3_kernel(const Args3<T, S> a, cons
     }
 #pragma unroll
     for (int i = 0; i < 7; ++i) Gc[i] = Gn[i];
+    Gcl = Gnl, pch = pnh, pcl = pnl;
   }
   if (MODE == kModeStep && a.vol_part) {
     // fixed-order block reduction of the phi this CTA collided
@@ -497,7 +566,10 @@ __global__ void init3_rest_kernel(Args3<T, S> a, const double* __restrict__ phi0
     double s = 0.0;
     for (int i = 1; i < 7; ++i)
       s += (double)Conv<T, S>::ld(gm + (i - 1) * P + pull_pos(i, x, y, z, nx, ny, nz));
-    a.g0[a.parity][k] = (T)(phi0[k] - s);
+    const double g0 = phi0[k] - s;
+    const T hi = (T)g0;
+    a.g0[a.parity][k] = hi;
+    if (a.g0lo[a.parity]) a.g0lo[a.parity][k] = (T)(g0 - (double)hi);
   }
 }
 
@@ -514,10 +586,21 @@ __global__ void plane3_kernel(Args3<T, S> a, int kind, int i, double* __restrict
        k += (int64_t)gridDim.x * blockDim.x) {
     int x, y, z;
     node_xyz(k, nx, ny, x, y, z);
-    if (kind == 2 || (kind == 1 && i == 0)) {
-      T* p = kind == 2 ? a.J[par] + i * P + k : a.g0[par] + k;
+    if (kind == 2) {
+      T* p = a.J[par] + i * P + k;
       if (to_device) *p = (T)buf[k];
       else buf[k] = (double)*p;
+      continue;
+    }
+    if (kind == 1 && i == 0) {  // g_0 = hi + lo
+      T* lo = a.g0lo[par];
+      if (to_device) {
+        const T hi = (T)buf[k];
+        a.g0[par][k] = hi;
+        if (lo) lo[k] = (T)(buf[k] - (double)hi);
+      } else {
+        buf[k] = (double)a.g0[par][k] + (lo ? (double)lo[k] : 0.0);
+      }
       continue;
     }
     const int64_t m = pull_pos(i, x, y, z, nx, ny, nz);
@@ -545,6 +628,7 @@ __global__ void __launch_bounds__(256) volume3_kernel(Args3<T, S> a,
     int x, y, z;
     node_xyz(k, nx, ny, x, y, z);
     double phi = (double)a.g0[a.parity][k];
+    if (a.g0lo[a.parity]) phi += (double)a.g0lo[a.parity][k];
     for (int i = 1; i < 7; ++i)
       phi += (double)Conv<T, S>::ld(gm + (i - 1) * P + pull_pos(i, x, y, z, nx, ny, nz));
     const int r = labels ? labels[k] : 0;

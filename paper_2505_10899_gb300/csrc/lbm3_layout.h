@@ -31,6 +31,8 @@ struct Args3 {
   S* f[2];          // 19 planes per buffer
   S* g[2];          // the 6 moving phase-field populations (i = 1..6 -> plane i-1)
   T* g0[2];         // the rest population g_0, kept in the arithmetic type
+  T* g0lo[2];       // FP32 arithmetic: low part of g_0 (g_0 = g0 + g0lo, a float
+                    // pair), so that sum g = phi holds to ~2^-48; null in FP64
   T* J[2];          // phi*u of the previous step, 3 planes per buffer
   int64_t plane;    // elements per plane (n rounded up)
   int32_t nx, ny, nz, zc;  // grid; planes per CTA along z

@@ -48,7 +48,9 @@ for _name, (_args, _res) in {
     "lbm3_time": ([_H], ctypes.c_int64),
     "lbm3_set_tiling": ([_H, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "lbm3_get_tiling": ([_H, _I32P, _I32P, _I32P, _I32P], ctypes.c_int),
-    "lbm3_autotune": ([_H, ctypes.c_int32, _I32P, _I32P, _I32P, _D], ctypes.c_int),
+    "lbm3_autotune": ([_H, ctypes.c_int32, _I32P, _I32P, _I32P, _I32P, _D], ctypes.c_int),
+    "lbm3_set_kernel": ([_H, ctypes.c_int32], ctypes.c_int),
+    "lbm3_get_kernel": ([_H], ctypes.c_int32),
     "lbm3_status": ([_H], ctypes.c_int),
     "lbm3_destroy": ([_H], None),
 }.items():
@@ -161,11 +163,21 @@ def lbm3_get_tiling(h):
 
 
 def lbm3_autotune(h, trials: int = 3):
-    bx, by, zc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    var, bx, by, zc = (ctypes.c_int32() for _ in range(4))
     ms = ctypes.c_double()
-    _check(_lib.lbm3_autotune(h, int(trials), ctypes.byref(bx), ctypes.byref(by),
-                              ctypes.byref(zc), ctypes.byref(ms)), "lbm3_autotune")
-    return {"bx": int(bx.value), "by": int(by.value), "zc": int(zc.value), "ms": float(ms.value)}
+    _check(_lib.lbm3_autotune(h, int(trials), ctypes.byref(var), ctypes.byref(bx),
+                              ctypes.byref(by), ctypes.byref(zc), ctypes.byref(ms)),
+           "lbm3_autotune")
+    return {"kernel": int(var.value), "bx": int(bx.value), "by": int(by.value),
+            "zc": int(zc.value), "ms": float(ms.value)}
+
+
+def lbm3_set_kernel(h, variant: int):
+    return _check(_lib.lbm3_set_kernel(h, int(variant)), "lbm3_set_kernel")
+
+
+def lbm3_get_kernel(h) -> int:
+    return int(_lib.lbm3_get_kernel(h))
 
 
 def lbm3_status(h) -> int:
@@ -239,6 +251,12 @@ class Sim3:
 
     def autotune(self, trials=3):
         return lbm3_autotune(self.h, trials)
+
+    def set_kernel(self, variant):
+        lbm3_set_kernel(self.h, variant)
+
+    def kernel(self):
+        return lbm3_get_kernel(self.h)
 
     @property
     def t(self):

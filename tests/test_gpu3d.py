@@ -115,6 +115,40 @@ def test_fp32_parity_100_steps(L3):
     assert s.status() == 0
 
 
+@pytest.mark.parametrize("variant,tiling", [(2, (32, 4, 8)), (2, (32, 8, 13)), (3, (64, 4, 8)),
+                                            (3, (32, 4, 20))])
+def test_fp32_async_copy_variants(L3, variant, tiling):
+    # the cp.async kernel runs the same per-node arithmetic as the register
+    # kernel: equal up to FMA contraction, and within the FP32 bar of the oracle
+    case, phi0, u0 = two_phase(70, 21, 20, rho_l=3.0, tau_f_l=0.7)
+    a = L3.Sim3(case, phi0, u0, precision="f32")
+    a.set_tiling(*tiling)
+    a.set_kernel(variant)
+    assert a.kernel() == variant
+    b = L3.Sim3(case, phi0, u0, precision="f32")
+    b.set_tiling(*tiling)
+    b.set_kernel(1)
+    a.step(100)
+    b.step(100)
+    fa, fb = a.get_state(), b.get_state()
+    for x, y in zip(fa[:3], fb[:3]):
+        assert md(x, y) <= 2e-6
+    o = oracle.Oracle3(case, phi0, u0).step(100)
+    assert md(a.fields()[0], o.fields()[0]) <= 1e-5
+    assert a.status() == 0
+
+
+def test_async_variant_rejected_where_unavailable(L3):
+    case, phi0, u0 = two_phase(40, 24, 20)
+    s = L3.Sim3(case, phi0, u0, precision="f64")
+    with pytest.raises(L3.LbmError):
+        s.set_kernel(2)
+    t = L3.Sim3(case, phi0, u0, precision="f32")
+    t.set_tiling(32, 16, 8)
+    with pytest.raises(L3.LbmError):
+        t.set_kernel(3)
+
+
 def test_fp16_storage_parity_and_volume(L3):
     case, phi0, u0 = two_phase(40, 24, 20, rho_l=3.0, tau_f_l=0.7)
     o, s = pair(L3, case, phi0, u0, 100, "f16")
@@ -183,6 +217,7 @@ def test_autotune_keeps_state(L3):
     for x, y in zip(before[:3], after[:3]):
         assert np.array_equal(x, y)
     assert s.tiling()[:3] == (best["bx"], best["by"], best["zc"])
+    assert s.kernel() == best["kernel"] in (1, 2, 3)
     s.step(5)
     o = oracle.Oracle3(case, phi0, u0).step(8)
     assert md(s.fields()[0], o.fields()[0]) <= 1e-5

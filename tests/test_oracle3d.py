@@ -333,3 +333,25 @@ def test_laplace_law_sphere():
     dp = p[n // 2, n // 2, n // 2] - p[0, 0, 0]
     assert abs(dp / (2 * sigma / R_eff) - 1) < 0.05
     assert np.abs(u).max() < 5e-5
+
+
+def test_dependency_radius_of_k_steps():
+    # phi after k steps at a node depends on phi0 within 1 + 2k nodes: a
+    # periodic block of phi0 reproduces the whole-box result exactly there
+    # (the basis of the sampled full-size parity test)
+    case, phi0 = W.rayleigh_plateau(24, 24, 32, R=6.0)
+    k, half = 2, 8
+    r = 1 + 2 * k
+    phi = oracle.Oracle3(case, phi0).step(k).fields()[0]
+    for (cz, cy, cx) in [(0, 12, 18), (20, 6, 12), (31, 23, 0)]:
+        iz, iy, ix = (np.arange(c - half, c + half) % n for c, n in ((cz, 32), (cy, 24), (cx, 24)))
+        bc = dict(case, nx=2 * half, ny=2 * half, nz=2 * half)
+        o = oracle.Oracle3(bc, phi0[np.ix_(iz, iy, ix)]).step(k)
+        inner = o.fields()[0][r:-r, r:-r, r:-r]
+        assert np.array_equal(inner, phi[np.ix_(iz[r:-r], iy[r:-r], ix[r:-r])])
+        # the bound is nearly tight: two nodes closer to the block face the
+        # block result differs somewhere (one closer still agrees here, as the
+        # initial Laplacian reaches phi only through the rounding of sum g_eq)
+        e = r - 2
+        edge = o.fields()[0][e:-e, e:-e, e:-e]
+        assert not np.array_equal(edge, phi[np.ix_(iz[e:-e], iy[e:-e], ix[e:-e])])
