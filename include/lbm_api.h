@@ -63,7 +63,12 @@ enum {
   LBM_ERR_UNIMPLEMENTED = -6  /* entry point declared but not built */
 };
 
-enum { LBM_F64 = 0, LBM_F32 = 1 };                 /* storage and arithmetic */
+/* Storage and arithmetic precision.  Under LBM_F32 the rest population g_0
+ * is kept as an unevaluated sum of two FP32 values, formed exactly from phi
+ * minus the stored movers, so that the populations of every node sum to the
+ * phi that entered it to ~2^-48 and FP32 rounding does not drift the phase
+ * volumes (Sec. 4.1 measures exactly these volumes). */
+enum { LBM_F64 = 0, LBM_F32 = 1 };
 enum { LBM_FLOW_COUPLED = 0, LBM_FLOW_VORTEX = 1 }; /* see lbm_params.flow */
 
 /* Parameters of one case (one periodic grid). */
@@ -142,8 +147,10 @@ int lbm_volume_async(lbm_handle* h, double* d_out);
  * reduces phi (Eq. 35, the state entering the step) over each case in FP64
  * inside the step kernel and writes the per-case totals to d_out[ncases]
  * (device memory, overwritten every step, so after lbm_step(n) it holds the
- * volumes at time t+n-1).  Only for batches whose cases all have one region
- * (no labels): LBM_ERR_ARG otherwise.  d_out = NULL switches tracking off. */
+ * volumes at time t+n-1).  Under LBM_F32 the fused sum may leave out the low
+ * part of g_0 (below 2^-24 g_0 per node); lbm_volume counts it.  Only for
+ * batches whose cases all have one region (no labels): LBM_ERR_ARG
+ * otherwise.  d_out = NULL switches tracking off. */
 int lbm_track_volume(lbm_handle* h, double* d_out);
 
 /* Work tiling of the step kernel: each CTA owns a strip of bx columns
@@ -199,7 +206,8 @@ int lbm_set_state(lbm_handle* h, int32_t c, const double* h_f,
 int64_t lbm_time(const lbm_handle* h);
 
 /* Checkpoint / resume: the raw device state of the batch (populations in
- * device precision, phi*u, step index), bitwise.  lbm_save synchronises. */
+ * device precision, under LBM_F32 with the low part of g_0, phi*u, step
+ * index), bitwise.  lbm_save synchronises. */
 size_t lbm_checkpoint_bytes(const lbm_handle* h);
 int lbm_save(lbm_handle* h, void* h_buf, size_t bytes);
 int lbm_load(lbm_handle* h, const void* h_buf, size_t bytes);
@@ -212,8 +220,10 @@ int lbm_status(lbm_handle* h);
  * [f*: 9 planes][g*: 9 planes][phi*u: 2 planes], each nx*ny elements of the
  * device precision, in the pull layout (plane i, position x holds the
  * post-collision value that streams to x + c_i; f planes are zero in vortex
- * mode).  lbm_restore writes such a buffer back as the current state; the
- * step index is set separately with lbm_set_time.  All three are
+ * mode; under LBM_F32 the g_0 plane holds the high part of the float pair
+ * only, and lbm_restore clears the low part).  lbm_restore writes such a
+ * buffer back as the current state; the step index is set separately with
+ * lbm_set_time.  All three are
  * asynchronous on the handle's stream. */
 size_t lbm_snapshot_bytes(const lbm_handle* h, int32_t c);
 int lbm_snapshot(lbm_handle* h, int32_t c, void* d_buf);
@@ -269,7 +279,10 @@ int lbm_adjoint_take_param_grads(lbm_handle* h, double* h_param_grads);
  *   d_labels: device int8 [ny][nx], region of each node in [0, nregions) or
  *        -1 (none); NULL = one region, the whole grid.
  *   d_out: device FP64 [nregions], V_r = sum over region r of
- *        phi = sum_i g_i (Eq. 35), reduced in a fixed order.
+ *        phi = sum_i g_i (Eq. 35), reduced in a fixed order.  The nine planes
+ *        are summed as given: for an LBM_F32 state of this library, whose g_0
+ *        carries a low part outside these planes, the result differs from
+ *        lbm_volume by at most half an FP32 ulp of g_0 per node.
  *   stream: cudaStream_t (NULL = legacy default stream); the call enqueues
  *        two kernels and does not synchronise.
  * Limits: 1 <= nregions <= 8, plane_stride >= nx*ny, nx <= 524288 columns

@@ -182,6 +182,19 @@ cudaError_t launch_copy_to_f64<LBM_T>(double* dst, const LBM_T* src, int64_t n, 
 }
 
 template <>
+cudaError_t launch_add_lo_f64<LBM_T>(double* v, const LBM_T* lo, int64_t n, cudaStream_t s) {
+  add_lo_f64<LBM_T><<<grid_for(n, 256), 256, 0, s>>>(v, lo, n);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_lo_from_f64<LBM_T>(LBM_T* lo, const LBM_T* hi, const double* v, int64_t n,
+                                      cudaStream_t s) {
+  lo_from_f64<LBM_T><<<grid_for(n, 256), 256, 0, s>>>(lo, hi, v, n);
+  return cudaGetLastError();
+}
+
+template <>
 cudaError_t launch_volume<LBM_T>(const CaseDev<LBM_T>* cases, int ncases,
                                  const Item* items, int n_items, int bx, int parity,
                                  double* part, double* out, cudaStream_t s) {

@@ -50,6 +50,10 @@ template <typename T>
 cudaError_t launch_copy_to_T(T* dst, const double* src, int64_t n, cudaStream_t s);
 template <typename T>
 cudaError_t launch_copy_to_f64(double* dst, const T* src, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_add_lo_f64(double* v, const T* lo, int64_t n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lo_from_f64(T* lo, const T* hi, const double* v, int64_t n, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_volume(const CaseDev<T>* cases, int ncases,

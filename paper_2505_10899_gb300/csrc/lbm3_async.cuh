@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(BX* BY) step3_async_kernel(
   };
 
   // phi, psi of one node from 8 values (7 populations + low part of g_0)
-  auto put = [&](int slot, int j, int i, const float (&G)[7], float glo, float& ph, float& pl) {
-    const float phi = phi_of(G, glo, ph, pl);
+  auto put = [&](int slot, int j, int i, const float (&G)[7], float glo) {
+    const float phi = phi_of(G, glo);
     float2 v;
     v.x = phi;
     v.y = psi3(phi, a.xi);
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(BX* BY) step3_async_kernel(
   };
 
   // planes zb - 1 and zb: direct loads (no prefetch yet)
-  float Gc[7], Gn[7], Gcl, Gnl, pch, pcl, pnh, pnl;
+  float Gc[7], Gn[7], Gcl, Gnl;
   {
     float H[7], Hl;
     for (int q = 0; q < 2; ++q) {
@@ -161,10 +161,10 @@ __global__ void __launch_bounds__(BX* BY) step3_async_kernel(
       set_z(o, zwrap(zl), nz, nxy);
       if (q == 0) {
         pull_g(g0s, g0ls, gms, P, o, Gn, Gnl);
-        put(zl & 3, ty + 1, tx + 1, Gn, Gnl, pnh, pnl);
+        put(zl & 3, ty + 1, tx + 1, Gn, Gnl);
       } else {
         pull_g(g0s, g0ls, gms, P, o, Gc, Gcl);
-        put(zl & 3, ty + 1, tx + 1, Gc, Gcl, pch, pcl);
+        put(zl & 3, ty + 1, tx + 1, Gc, Gcl);
       }
       if (has_h) {
         Offs oh = hal;
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(BX* BY) step3_async_kernel(
 #pragma unroll
       for (int i = 0; i < 7; ++i) Gn[i] = *sG(s, i);
       Gnl = *sG(s, 7);
-      put((z + 1) & 3, ty + 1, tx + 1, Gn, Gnl, pnh, pnl);
+      put((z + 1) & 3, ty + 1, tx + 1, Gn, Gnl);
       if (has_h) {  // halo phi: plain sum, as in step3_kernel
         float H[7];
 #pragma unroll
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(BX* BY) step3_async_kernel(
       for (int c = 0; c < 3; ++c) jp[c] = *sJ(s, c);
       St3<float> SP, SQ;
       read_st(ring, (z + 3) & 3, z & 3, (z + 1) & 3, ty + 1, tx + 1, SP, SQ);
-      const Out3<float> o = node3<float, float, kModeStep>(a, F, Gc, Gcl, pch, pcl, jp, SP, SQ);
+      const Out3<float> o = node3<float, float, kModeStep>(a, F, Gc, Gcl, jp, SP, SQ);
       const float phi = SP.C;
       if (!(isfinite(phi) && isfinite(o.ux + o.uy + o.uz))) atomicOr(a.flags, kFlagNonFinite);
       const uint32_t node = (uint32_t)z * nxy + own.y[1] + own.x[1];
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(BX* BY) step3_async_kernel(
     }
 #pragma unroll
     for (int i = 0; i < 7; ++i) Gc[i] = Gn[i];
-    Gcl = Gnl, pch = pnh, pcl = pnl;
+    Gcl = Gnl;
     s = (s + 1) % NST;
   }
   cp_wait<0>();

@@ -16,13 +16,15 @@
 // from A (as the next plane) to B.
 //
 // Phase volume in FP32 arithmetic: phi is conserved node by node only if the
-// stored rest population is exactly phi minus the stored movers.  A rounded
-// FP32 g_0 leaves a rounding error per node and step whose bias (the slowly
-// varying interface values round the same way step after step) accumulates
-// into a volume drift.  So under FP32 arithmetic g_0 is kept as an unevaluated
-// sum of two floats (hi + lo), and the sums phi = sum g and S = sum of the
-// stored movers are formed exactly with error-free transformations (TwoSum,
-// Knuth, TAOCP vol. 2, 4.2.2); g_0 = phi - S is then exact to ~2^-48.
+// stored rest population is phi minus the stored movers.  A rounded FP32 g_0
+// leaves an error of up to half an ulp of g_0 per node and step whose sign the
+// slowly varying interface values repeat step after step, so the volume
+// drifts.  Under FP32 arithmetic g_0 is therefore kept as a float pair
+// (hi + lo) and advanced by the exact identity
+//   g_0* = g_0 + lo + sum_{i>0} (g_i - g*_i)
+// (pulled minus stored movers), the differences summed in plain FP32 (their
+// rounding is 2^-24 of the collision change, not of g_0) and added to g_0 with
+// an error-free TwoSum (Knuth, TAOCP vol. 2, 4.2.2).
 #pragma once
 #include <cstdint>
 #include <cuda_fp16.h>
@@ -140,31 +142,10 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// phi = sum g as a float pair (hi, lo): exact up to the rounding of lo.
-__device__ __forceinline__ void sum_g_ff(const float (&G)[7], float glo, float& hi, float& lo) {
-  float s, e;
-  two_sum(G[0], G[1], s, e);
-  lo = e + glo;
-#pragma unroll
-  for (int i = 2; i < 7; ++i) {
-    two_sum(s, G[i], s, e);
-    lo += e;
-  }
-  hi = s;
-}
-
-// phi of one node from its pulled populations, and its float-pair parts.
+// phi of one node from its pulled populations (plus the low part of g_0).
 template <typename T>
-__device__ __forceinline__ T phi_of(const T (&G)[7], T glo, T& hi, T& lo) {
-  hi = sum7(G);
-  lo = T(0);
-  return hi;
-}
-template <>
-__device__ __forceinline__ float phi_of<float>(const float (&G)[7], float glo, float& hi,
-                                               float& lo) {
-  sum_g_ff(G, glo, hi, lo);
-  return hi + lo;
+__device__ __forceinline__ T phi_of(const T (&G)[7], T glo) {
+  return sum7(G) + glo;
 }
 
 template <int I, typename T, typename S>
@@ -247,8 +228,7 @@ struct Out3 {
 
 template <typename T, typename S, int MODE>
 __device__ __forceinline__ Out3<T> node3(const Args3<T, S>& a, T (&F)[19], T (&G)[7], T& Glo,
-                                         T phh, T phl, const T (&jp)[3], const St3<T>& P,
-                                         const St3<T>& Q) {
+                                         const T (&jp)[3], const St3<T>& P, const St3<T>& Q) {
   const T phi = P.C;
   T gpx, gpy, gpz;
   grad12(P, gpx, gpy, gpz);
@@ -323,6 +303,11 @@ __device__ __forceinline__ Out3<T> node3(const Args3<T, S>& a, T (&F)[19], T (&G
   const T Vz = (Jz - jp[2]) + T(0.25) * sh * qz;
   const T L8 = T(0.125) * (mu + a.lambda * phi);  // w_i (hbar + lambda phi)
   const T wg = a.wg, hg2 = T(0.5) * a.hg;         // G_i = w_i c.V / c_s^2 = (1/2) c.V
+  T Gin[7];  // FP32: the pulled populations, for the rest population below
+  if constexpr (sizeof(T) == 4) {
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Gin[i] = G[i];
+  }
   // g_eq,+- = L8 +- (1/2) c.J (Eq. 31)
   G[1] = G[1] + wg * ((L8 + T(0.5) * Jx) - G[1]) + hg2 * Vx;
   G[2] = G[2] + wg * ((L8 - T(0.5) * Jx) - G[2]) - hg2 * Vx;
@@ -333,23 +318,15 @@ __device__ __forceinline__ Out3<T> node3(const Args3<T, S>& a, T (&F)[19], T (&G
 #pragma unroll
   for (int i = 1; i < 7; ++i) G[i] = Conv<T, S>::round(G[i]);
   // rest population from the conserved zeroth moment: sum g* = phi
-  if (sizeof(T) == 8) {
+  if constexpr (sizeof(T) == 8) {
     G[0] = phi - (((G[1] + G[2]) + (G[3] + G[4])) + (G[5] + G[6]));
     Glo = T(0);
   } else {
-    // float pair: g0 = (phh + phl) - S with S the exact sum of the stored movers
-    float sh, sl, e;
-    two_sum((float)G[1], (float)G[2], sh, sl);
-#pragma unroll
-    for (int i = 3; i < 7; ++i) {
-      two_sum(sh, (float)G[i], sh, e);
-      sl += e;
-    }
-    float dh, de;
-    two_sum((float)phh, -sh, dh, de);
-    const float dl = (de + ((float)phl - sl));
+    const float d = (((float)Gin[1] - (float)G[1]) + ((float)Gin[2] - (float)G[2])) +
+                    ((((float)Gin[3] - (float)G[3]) + ((float)Gin[4] - (float)G[4])) +
+                     (((float)Gin[5] - (float)G[5]) + ((float)Gin[6] - (float)G[6])));
     float hi, lo;
-    two_sum(dh, dl, hi, lo);
+    two_sum((float)Gin[0], (float)Glo + d, hi, lo);
     G[0] = (T)hi;
     Glo = (T)lo;
   }
@@ -395,9 +372,8 @@ __global__ void __launch_bounds__(BX* BY) step3_kernel(
   const int zb = blockIdx.z * a.zc;
   const int ze = min(zb + a.zc, nz);
 
-  // phase A for plane zl into ring slot s; own pulled g returned in G, Glo and
-  // phi as the float pair (ph, pl)
-  auto phaseA = [&](int zl, int s, T (&G)[7], T& Glo, T& ph, T& pl) {
+  // phase A for plane zl into ring slot s; own pulled g returned in G, Glo
+  auto phaseA = [&](int zl, int s, T (&G)[7], T& Glo) {
     const int zw = zl < 0 ? zl + nz : (zl >= nz ? zl - nz : zl);
     set_z(own, zw, nz, nxy);
     pull_g(g0s, g0ls, gms, P, own, G, Glo);
@@ -406,24 +382,22 @@ __global__ void __launch_bounds__(BX* BY) step3_kernel(
       set_z(hal, zw, nz, nxy);
       pull_g(g0s, g0ls, gms, P, hal, H, Hlo);
     }
-    const T phi = phi_of(G, Glo, ph, pl);
+    const T phi = phi_of(G, Glo);
     typename N3<T>::pair v;
     v.x = phi;
     v.y = psi3(phi, a.xi);
     ring.pq[s][ty + 1][tx + 1] = v;
     if (has_h) {
-      // a halo node's phi only enters this tile's stencils: the plain sum
-      // (within an ulp of the owner's value) is enough there
-      const T phh = sum7(H) + Hlo;
+      const T phh = phi_of(H, Hlo);
       v.x = phh;
       v.y = psi3(phh, a.xi);
       ring.pq[s][hy + 1][hx + 1] = v;
     }
   };
 
-  T Gc[7], Gn[7], Gcl, Gnl, pch, pcl, pnh, pnl;
-  phaseA(zb - 1, (zb + 3) & 3, Gn, Gnl, pnh, pnl);
-  phaseA(zb, zb & 3, Gc, Gcl, pch, pcl);
+  T Gc[7], Gn[7], Gcl, Gnl;
+  phaseA(zb - 1, (zb + 3) & 3, Gn, Gnl);
+  phaseA(zb, zb & 3, Gc, Gcl);
   double vsum = 0.0;
   for (int z = zb; z < ze; ++z) {
     // independent loads of this plane first
@@ -437,12 +411,12 @@ __global__ void __launch_bounds__(BX* BY) step3_kernel(
       jp[1] = js[P + node];
       jp[2] = js[2 * P + node];
     }
-    phaseA(z + 1, (z + 1) & 3, Gn, Gnl, pnh, pnl);
+    phaseA(z + 1, (z + 1) & 3, Gn, Gnl);
     __syncthreads();
     if (valid) {
       St3<T> SP, SQ;
       read_st(ring, (z + 3) & 3, z & 3, (z + 1) & 3, ty + 1, tx + 1, SP, SQ);
-      const Out3<T> o = node3<T, S, MODE>(a, F, Gc, Gcl, pch, pcl, jp, SP, SQ);
+      const Out3<T> o = node3<T, S, MODE>(a, F, Gc, Gcl, jp, SP, SQ);
       const T phi = SP.C;
       if (!(isfinite(phi) && isfinite(o.ux + o.uy + o.uz))) atomicOr(a.flags, kFlagNonFinite);
       if (MODE == kModeStep) {
@@ -467,7 +441,7 @@ __global__ void __launch_bounds__(BX* BY) step3_kernel(
     }
 #pragma unroll
     for (int i = 0; i < 7; ++i) Gc[i] = Gn[i];
-    Gcl = Gnl, pch = pnh, pcl = pnl;
+    Gcl = Gnl;
   }
   if (MODE == kModeStep && a.vol_part) {
     // fixed-order block reduction of the phi this CTA collided

@@ -178,6 +178,7 @@ Layout make_layout(const lbm_params* c, int n, int n_items, int total_regions) {
   off = align_up(off + (size_t)maxp * 4 * sizeof(double));
   L.f.resize(n);
   L.g.resize(n);
+  L.glo.resize(n);
   L.J.resize(n);
   L.lab.resize(n);
   L.plane.resize(n);
@@ -196,6 +197,8 @@ Layout make_layout(const lbm_params* c, int n, int n_items, int total_regions) {
     }
     L.J[k] = off;  // two buffers of 2 planes
     off = align_up(off + 4 * pb);
+    L.glo[k] = off;  // FP32: low part of g_0, one plane per buffer
+    if (es == 4) off = align_up(off + 2 * pb);
     L.lab[k] = off;
     off = align_up(off + (size_t)plane);
   }
@@ -241,6 +244,8 @@ CaseDev<T> make_case(const lbm_handle* h, int k) {
   }
   c.J[0] = (T*)(h->ws + L.J[k]);
   c.J[1] = (T*)(h->ws + L.J[k] + 2 * pb);
+  c.g0lo[0] = sizeof(T) == 4 ? (T*)(h->ws + L.glo[k]) : nullptr;
+  c.g0lo[1] = sizeof(T) == 4 ? (T*)(h->ws + L.glo[k] + pb) : nullptr;
   c.labels = nullptr;
   c.plane = L.plane[k];
   c.nx = p.nx;
@@ -444,6 +449,8 @@ int do_get_state(lbm_handle* h, int c, double* f, double* g, double* j) {
     if (!out || !buf) continue;
     for (int i = 0; i < 9; ++i) {
       cudaError_t e = lbmk::launch_plane_export<T>(st, buf + i * cd.plane, i, p.nx, p.ny, h->stream);
+      if (e == cudaSuccess && which == 0 && i == 0 && cd.g0lo[h->parity])
+        e = lbmk::launch_add_lo_f64<T>(st, cd.g0lo[h->parity], n, h->stream);  // g_0 = hi + lo
       if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
       LBM_CUDA(cudaMemcpyAsync(out + i * n, st, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
       LBM_CUDA(cudaStreamSynchronize(h->stream));
@@ -473,6 +480,8 @@ int do_set_state(lbm_handle* h, int c, const double* f, const double* g, const d
     for (int i = 0; i < 9; ++i) {
       LBM_CUDA(cudaMemcpyAsync(st, in + i * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
       cudaError_t e = lbmk::launch_plane_import<T>(buf + i * cd.plane, st, i, p.nx, p.ny, h->stream);
+      if (e == cudaSuccess && which == 0 && i == 0 && cd.g0lo[h->parity])
+        e = lbmk::launch_lo_from_f64<T>(cd.g0lo[h->parity], buf, st, n, h->stream);
       if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
       LBM_CUDA(cudaStreamSynchronize(h->stream));
     }
@@ -505,7 +514,7 @@ struct CkptHeader {
 size_t state_bytes_case(const lbm_handle* h, int k) {
   const size_t es = elem_size(h->precision);
   const int64_t n = (int64_t)h->params[k].nx * h->params[k].ny;
-  const int planes = (h->flow == LBM_FLOW_COUPLED ? 18 : 9) + 2;
+  const int planes = (h->flow == LBM_FLOW_COUPLED ? 18 : 9) + 2 + (es == 4 ? 1 : 0);
   return (size_t)planes * n * es;
 }
 
@@ -929,7 +938,7 @@ int lbm_save(lbm_handle* h, void* h_buf, size_t bytes) {
   if (!h || !h_buf) return fail(LBM_ERR_ARG, "null argument");
   if (bytes < lbm_checkpoint_bytes(h)) return fail(LBM_ERR_ARG, "buffer too small");
   CkptHeader hd{};
-  memcpy(hd.magic, "LBMCKPT1", 8);
+  memcpy(hd.magic, "LBMCKPT2", 8);
   hd.abi = LBM_ABI_VERSION;
   hd.precision = h->precision;
   hd.flow = h->flow;
@@ -954,6 +963,11 @@ int lbm_save(lbm_handle* h, void* h_buf, size_t bytes) {
                                cudaMemcpyDeviceToHost,
                                h->stream));
     p += 2 * n * es;
+    if (es == 4) {  // low part of g_0
+      LBM_CUDA(cudaMemcpyAsync(p, h->ws + h->L.glo[k] + h->parity * pb, n * es,
+                               cudaMemcpyDeviceToHost, h->stream));
+      p += n * es;
+    }
   }
   LBM_CUDA(cudaStreamSynchronize(h->stream));
   return LBM_OK;
@@ -964,7 +978,7 @@ int lbm_load(lbm_handle* h, const void* h_buf, size_t bytes) {
   if (bytes < lbm_checkpoint_bytes(h)) return fail(LBM_ERR_ARG, "buffer too small");
   CkptHeader hd;
   memcpy(&hd, h_buf, sizeof hd);
-  if (memcmp(hd.magic, "LBMCKPT1", 8) != 0 || hd.abi != LBM_ABI_VERSION ||
+  if (memcmp(hd.magic, "LBMCKPT2", 8) != 0 || hd.abi != LBM_ABI_VERSION ||
       hd.precision != h->precision || hd.flow != h->flow || hd.ncases != h->ncases ||
       hd.payload != lbm_checkpoint_bytes(h) - sizeof(CkptHeader))
     return fail(LBM_ERR_ARG, "checkpoint does not match this handle");
@@ -985,6 +999,11 @@ int lbm_load(lbm_handle* h, const void* h_buf, size_t bytes) {
                                cudaMemcpyHostToDevice,
                                h->stream));
     p += 2 * n * es;
+    if (es == 4) {
+      LBM_CUDA(cudaMemcpyAsync(h->ws + h->L.glo[k] + h->parity * pb, p, n * es,
+                               cudaMemcpyHostToDevice, h->stream));
+      p += n * es;
+    }
   }
   h->t = hd.t;
   return set_clock(h);
@@ -1031,6 +1050,8 @@ int lbm_restore(lbm_handle* h, int32_t c, const void* d_buf) {
                              cudaMemcpyDeviceToDevice, h->stream));
   LBM_CUDA(cudaMemcpy2DAsync(h->ws + h->L.J[c] + h->parity * 2 * pb, pb, in + 18 * nb, nb, nb, 2,
                              cudaMemcpyDeviceToDevice, h->stream));
+  if (es == 4)  // FP32: the snapshot holds g_0 rounded to its high part
+    LBM_CUDA(cudaMemsetAsync(h->ws + h->L.glo[c] + h->parity * pb, 0, nb, h->stream));
   return LBM_OK;
 }
 

@@ -70,6 +70,8 @@ __global__ void init_kernel(CaseDev<T> cd, double beta4, double kappa,
       const double gi = (i == 0) ? p + (w - 1.0) * lam : w * lam + 3.0 * w * cJ;
       const int64_t dst = (int64_t)i * cd.plane + pull_src(i, x, y, nx, ny);
       gb[dst] = (T)gi;
+      // FP32: the rest population is a float pair (high part + low part)
+      if (i == 0 && cd.g0lo[par]) cd.g0lo[par][k] = (T)(gi - (double)(T)gi);
       if (fb) fb[dst] = (T)(rho * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2));
     }
     cd.J[par][k] = (T)Jx;
@@ -99,6 +101,23 @@ __global__ void plane_export(double* __restrict__ dst, const T* __restrict__ src
     const int x = (int)(k % nx), y = (int)(k / nx);
     dst[k] = (double)src_plane[pull_src(i, x, y, nx, ny)];
   }
+}
+
+// The low part of g_0 (FP32 float pair, own node, unshifted): added to an
+// exported FP64 plane, or split off an imported FP64 plane whose high part
+// the import rounded.
+template <typename T>
+__global__ void add_lo_f64(double* __restrict__ v, const T* __restrict__ lo, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    v[k] += (double)lo[k];
+}
+template <typename T>
+__global__ void lo_from_f64(T* __restrict__ lo, const T* __restrict__ hi,
+                            const double* __restrict__ v, int64_t n) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    lo[k] = (T)(v[k] - (double)hi[k]);
 }
 
 // Plain (unshifted) plane copies with precision change, for phi*u.
@@ -139,6 +158,7 @@ __global__ void __launch_bounds__(BX) volume_partial(const CaseDev<T>* __restric
       const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
       const int64_t o0 = (int64_t)y * nx, om = (int64_t)ym * nx, op = (int64_t)yp * nx;
       double phi = (double)gs[o0 + x];
+      if (cd.g0lo[parity]) phi += (double)cd.g0lo[parity][o0 + x];
       phi += (double)gs[P + o0 + xm];
       phi += (double)gs[2 * P + om + x];
       phi += (double)gs[3 * P + o0 + xp];

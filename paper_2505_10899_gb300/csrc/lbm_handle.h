@@ -16,6 +16,7 @@ namespace lbmk {
 struct Layout {
   size_t hdr = 0, cases = 0, items = 0, part = 0, vol = 0, staging = 0;
   std::vector<size_t> f, g, J, lab;  // per-case offsets (f: 2 buffers back to back)
+  std::vector<size_t> glo;           // FP32: low part of g_0, 2 planes per case
   std::vector<int64_t> plane;
   size_t total = 0;
 };

@@ -85,6 +85,10 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
   T* __restrict__ fd = COUPLED ? cdp->f[a.parity ^ 1] : nullptr;
   const T* __restrict__ Js = cdp->J[a.parity];
   T* __restrict__ Jd = cdp->J[a.parity ^ 1];
+  // FP32: low part of g_0 at the own node (null in FP64)
+  const T* __restrict__ los = cdp->g0lo[a.parity];
+  T* __restrict__ lod = cdp->g0lo[a.parity ^ 1];
+  constexpr bool LO = sizeof(T) == 4;
 
   // Halo columns: thread 0 serves the column left of the strip, thread BX-1
   // the column right of the last active one.
@@ -112,7 +116,7 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
 
   // register sets of the pipeline: rows k (current), k+1 (next), k+2 (fetch)
   struct Regs {
-    T F[9], G[9], J[2];
+    T F[9], G[9], J[2], lo;
   };
   Regs Rc, Rn, Rq;
   T hq[9];  // halo-column g of the row being fetched
@@ -122,6 +126,7 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
     pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G);
+    R.lo = LO ? ld<COHERENT>(los + (o0 + xc)) : T(0);
     if (COUPLED) pull9<COHERENT>(fs, P, o0, om, op, xc, xm, xp, R.F);
     if (MODE == kModeStep) {  // phi*u of the previous step at the own node
       R.J[0] = ld<COHERENT>(Js + (o0 + xc));
@@ -140,7 +145,9 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
     pull9<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, H);
   };
-  // write phi/psi of local row k (k >= -1) into the ring
+  // write phi/psi of local row k (k >= -1) into the ring.  phi is the plain
+  // sum of the nine pulled values (FP32: the low part of g_0 enters only the
+  // rest-population update, as in the bulk-copy kernel)
   auto put_row = [&](int k, const T G[9], const T H[9]) {
     const int s = (k + 4) & 3;
     if (act) {
@@ -188,10 +195,11 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
       const int y = wrap(y0 + k);
       const Stencil<T> S = read_stencil(ring, k, tid + 1);
       if (do_vol) vacc += (double)S.p;
-      const NodeOut<T> o = node_update<T, COUPLED, MODE>(a.ph, K, C.F, C.G, C.J[0], C.J[1], S, y);
+      const NodeOut<T> o =
+          node_update<T, COUPLED, MODE>(a.ph, K, C.F, C.G, C.lo, C.J[0], C.J[1], S, y);
       const uint32_t node = rowoff(y) + (uint32_t)xc;
       if (MODE == kModeStep) {
-        store_node<T, COUPLED>(fd, gd, Jd, P, node, C.F, C.G, o);
+        store_node<T, COUPLED>(fd, gd, Jd, lod, P, node, C.F, C.G, C.lo, o);
         if (!isfinite(S.p + o.ux + o.uy + o.p)) atomicOr(a.flags, kFlagNonFinite);
       } else {
         a.out_phi[node] = (double)S.p;

@@ -51,7 +51,8 @@ struct TmaShape {
 };
 
 template <typename T, int BX, bool COUPLED, int MODE, int S>
-__global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
+__global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
+    step_kernel_tma(const StepArgs<T> a) {
   using SH = TmaShape<T, BX, COUPLED, MODE, S>;
   constexpr int SEG = SH::SEG, NPL = SH::NPL, NJ = SH::NJ, STAGE = SH::STAGE;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -76,6 +77,11 @@ __global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
   T* __restrict__ fd = COUPLED ? cdp->f[a.parity ^ 1] : nullptr;
   const T* __restrict__ Js = cdp->J[a.parity];
   T* __restrict__ Jd = cdp->J[a.parity ^ 1];
+  // FP32: low part of g_0, read at the own node only (not staged: the ring's
+  // phi is the plain sum of the nine staged values; the exact rest
+  // population in node_update uses it)
+  const T* __restrict__ los = cdp->g0lo[a.parity];
+  T* __restrict__ lod = cdp->g0lo[a.parity ^ 1];
 
   // halo columns of the phi/psi ring: local column -1 (thread 0) and wact
   // (thread BX-1), both inside the staged segments
@@ -134,8 +140,8 @@ __global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
         bulk_g2s(dst + j, row + g0, (uint32_t)len * sizeof(T), bar);
         bulk_g2s(dst + j + len, row, 4 * sizeof(T), bar);
       }
-    } else if (lane >= 18 && lane < 18 + nj) {
-      const int q = lane - 18;
+    } else if (lane >= NPL && lane < NPL + nj) {
+      const int q = lane - NPL;
       bulk_g2s(st + NPL * SEG + q * BX, Js + (size_t)q * P + (size_t)r * nx + x0,
                (uint32_t)wact * sizeof(T), bar);
     }
@@ -175,7 +181,15 @@ __global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
   if (!bad) put_row(0);
 
   int issued_last = min(S - 2, nrows);  // highest row issued so far
+  // FP32: low part of g_0 of the own node, loaded one row ahead
+  auto lo_of = [&](int k) -> T {
+    if (sizeof(T) != 4 || !act || k >= nrows) return T(0);
+    return __ldg(los + ((uint32_t)wrap(y0 + k) * (uint32_t)nx + (uint32_t)xc));
+  };
+  T lo_next = lo_of(0);
   for (int k = 0; k < nrows; ++k) {
+    T glo = lo_next;
+    lo_next = lo_of(k + 1);
     // row k+1 (own row or the halo row below the item) into the ring
     bad = bad || !mbar_wait_bounded(&bars[slot_of(k + 1)], parity_of(k + 1), kWaitCycles);
     if (!bad) put_row(k + 1);
@@ -209,12 +223,14 @@ __global__ void __launch_bounds__(BX) step_kernel_tma(const StepArgs<T> a) {
         jpy = st[NPL * SEG + BX + tid];
       }
       const int y = wrap(y0 + k);
-      const Stencil<T> Sn = read_stencil(ring, k, tid + 1);
-      if (do_vol) vacc += (double)Sn.p;
-      const NodeOut<T> o = node_update<T, COUPLED, MODE>(a.ph, K, F, G, jpx, jpy, Sn, y);
       const uint32_t node = (uint32_t)y * (uint32_t)nx + (uint32_t)xc;
+      const Stencil<T> Sn = read_stencil(ring, k, tid + 1);
+      // fused volume: the plain phi (the low part of g_0, below 2^-24 g_0 per
+      // node, is left out here; lbm_volume counts it)
+      if (do_vol) vacc += (double)Sn.p;
+      const NodeOut<T> o = node_update<T, COUPLED, MODE>(a.ph, K, F, G, glo, jpx, jpy, Sn, y);
       if (MODE == kModeStep) {
-        store_node<T, COUPLED>(fd, gd, Jd, P, node, F, G, o);
+        store_node<T, COUPLED>(fd, gd, Jd, lod, P, node, F, G, glo, o);
         if (!isfinite(Sn.p + o.ux + o.uy + o.p)) atomicOr(a.flags, kFlagNonFinite);
       } else {
         a.out_phi[node] = (double)Sn.p;

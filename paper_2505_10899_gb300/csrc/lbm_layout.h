@@ -18,6 +18,8 @@ struct CaseDev {
   T* f[2];               // hydrodynamic populations, 9 planes per buffer
   T* g[2];               // phase-field populations, 9 planes per buffer
   T* J[2];               // phi*u of the previous step, 2 planes per buffer
+  T* g0lo[2];            // FP32: low part of the rest population, g_0 = g[0] + g0lo
+                         // (a float pair formed exactly, see node_update); null in FP64
   const int8_t* labels;  // volume regions, [y][x]; nullptr = one region
   int64_t plane;         // elements per plane (nx*ny rounded up)
   int32_t nx, ny;

@@ -54,6 +54,29 @@ __device__ __forceinline__ T sum9(const T v[9]) {
   return (((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]))) + v[8];
 }
 
+// Error-free sum s + e == a + b (TwoSum, Knuth, TAOCP vol. 2, 4.2.2).
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Rest population under FP32 arithmetic.  The populations of a node must
+// sum to the phi that entered it, or the phase volume drifts: a rounded FP32
+// g_0 = phi - sum(movers*) leaves an error of up to half an ulp of g_0 per node
+// and step, and slowly varying interface values repeat its sign step after
+// step.  So g_0 is kept as a float pair (g_0 + lo) and advanced by the exact
+// identity  g_0* = g_0 + lo + sum_{i>0} (g_i - g*_i),  where g_i are the pulled
+// and g*_i the stored post-collision movers: the 8 differences are summed in
+// plain FP32 (their rounding is 2^-24 of the collision change, not of g_0) and
+// added to g_0 with an error-free TwoSum, the low part kept.
+__device__ __forceinline__ void rest_pair(const float Gin[9], float lo, const float G[9],
+                                          float& g0, float& glo) {
+  const float d = ((Gin[1] - G[1]) + (Gin[2] - G[2])) + ((Gin[3] - G[3]) + (Gin[4] - G[4])) +
+                  (((Gin[5] - G[5]) + (Gin[6] - G[6])) + ((Gin[7] - G[7]) + (Gin[8] - G[8])));
+  two_sum_f(Gin[0], lo + d, g0, glo);
+}
+
 // psi of Eq. 37 (up to the factor W/4 and the log base), phi clipped to [0,1].
 template <typename T>
 __device__ __forceinline__ T psi_of(T phi, T xi) {
@@ -213,8 +236,8 @@ struct NodeOut {
 
 template <typename T, bool COUPLED, int MODE>
 __device__ __forceinline__ NodeOut<T> node_update(const Phys<T>& ph, const CaseK<T>& K,
-                                                  T (&Fc)[9], T (&Gc)[9], T jpx, T jpy,
-                                                  const Stencil<T>& S, int y) {
+                                                  T (&Fc)[9], T (&Gc)[9], T& Glo, T jpx,
+                                                  T jpy, const Stencil<T>& S, int y) {
   const T phi = S.p;
   // isotropic stencils (Sec. 3.2): grad = (1/3) axis + (1/12) diagonal
   // differences; lap = (2/3) axis + (1/6) diagonal second differences
@@ -298,6 +321,11 @@ __device__ __forceinline__ NodeOut<T> node_update(const Phys<T>& ph, const CaseK
     const T Vy = T(3) * dJy + sh * qy;
     const T Lam = mu + ph.lambda * phi;
     const Mom<T> mg = moments(Gc);
+    T Gin[9];  // FP32: the pulled populations, for the rest population below
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) Gin[i] = Gc[i];
+    }
     // M g_eq = (phi, 2Lam - 4phi, 4phi - 3Lam, Jx, -Jx, Jy, -Jy, 0, 0);
     // M G    = (0, 0, 0, Vx/3, -Vx/3, Vy/3, -Vy/3, 0, 0)
     const T e1 = ph.gsD[1] * (mg.m1 - (T(2) * Lam - T(4) * phi));
@@ -310,7 +338,11 @@ __device__ __forceinline__ NodeOut<T> node_update(const Phys<T>& ph, const CaseK
     const T e8 = ph.gsD[8] * mg.m8;
     add_back(Gc, T(0), e1, e2, e3, e4, e5, e6, e7, e8);
     // rest population from the conserved zeroth moment: sum g* = phi
-    Gc[0] = phi - (((Gc[1] + Gc[2]) + (Gc[3] + Gc[4])) + ((Gc[5] + Gc[6]) + (Gc[7] + Gc[8])));
+    if constexpr (sizeof(T) == 4) {
+      rest_pair(Gin, Glo, Gc, Gc[0], Glo);
+    } else {
+      Gc[0] = phi - (((Gc[1] + Gc[2]) + (Gc[3] + Gc[4])) + ((Gc[5] + Gc[6]) + (Gc[7] + Gc[8])));
+    }
   }
   return o;
 }
@@ -318,9 +350,10 @@ __device__ __forceinline__ NodeOut<T> node_update(const Phys<T>& ph, const CaseK
 // Store the post-collision state of one node (pull layout: own position).
 template <typename T, bool COUPLED>
 __device__ __forceinline__ void store_node(T* __restrict__ fd, T* __restrict__ gd,
-                                           T* __restrict__ Jd, uint32_t P, uint32_t node,
-                                           const T (&Fc)[9], const T (&Gc)[9],
-                                           const NodeOut<T>& o) {
+                                           T* __restrict__ Jd, T* __restrict__ lod, uint32_t P,
+                                           uint32_t node, const T (&Fc)[9], const T (&Gc)[9],
+                                           T Glo, const NodeOut<T>& o) {
+  if (sizeof(T) == 4) lod[node] = Glo;
   Jd[node] = o.Jx;
   Jd[P + node] = o.Jy;
 #pragma unroll

@@ -50,3 +50,19 @@ def test_batched_512_sampled_against_oracle(L):
         ophi, oux, ouy, op = o.fields()
         assert np.abs(phi - ophi).max() <= 1e-5, k
         assert np.abs(ux - oux).max() <= 1e-6 and np.abs(uy - ouy).max() <= 1e-6, k
+
+
+def test_batched_512_fp32_volume_drift_1e4_steps(L):
+    # The FP32 bar on the benchmark workload: every case's phase volume
+    # (FP64 sum of the FP32 state, g_0 a float pair) stays within 1e-6
+    # relative of its initial value over 10^4 steps.
+    cases = W.batched_droplets(512, seed=2026)
+    phis, us = zip(*(W.case_fields(c) for c in cases))
+    s = L.Sim(cases, list(phis), list(us), precision="f32")
+    s.autotune(1)
+    v0 = s.volume().copy()
+    s.step(10000)
+    assert s.status() == L.LBM_OK
+    v = s.volume()
+    assert np.all(np.isfinite(v))
+    assert np.abs(v / v0 - 1.0).max() <= 1e-6
