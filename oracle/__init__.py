@@ -46,7 +46,7 @@ class Params(ctypes.Structure):
     """Mirror of ``orc_params`` in lbm_oracle.c."""
     _fields_ = [
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
-        ("flow", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("flow", ctypes.c_int32), ("walls", ctypes.c_int32),
         ("W", ctypes.c_double), ("sigma", ctypes.c_double),
         ("lam", ctypes.c_double), ("xi", ctypes.c_double),
         ("tau_g", ctypes.c_double),
@@ -54,6 +54,7 @@ class Params(ctypes.Structure):
         ("tau_f_l", ctypes.c_double), ("tau_f_g", ctypes.c_double),
         ("s_f", ctypes.c_double * 9), ("s_g", ctypes.c_double * 9),
         ("vortex_U", ctypes.c_double), ("vortex_T", ctypes.c_double),
+        ("u_top", ctypes.c_double), ("u_bot", ctypes.c_double),
     ]
 
 
@@ -124,6 +125,9 @@ def make_params(case: dict) -> Params:
         p.s_g[k] = sg[k]
     p.vortex_U = case.get("vortex_U", 0.0)
     p.vortex_T = case.get("vortex_T", 1.0)
+    p.walls = int(case.get("walls", 0))
+    p.u_top = case.get("u_top", 0.0)
+    p.u_bot = case.get("u_bot", 0.0)
     return p
 
 

@@ -22,7 +22,8 @@
  * State convention: f, g hold the distributions f_i(x,t), g_i(x,t) *after*
  * streaming, i.e. the left-hand sides of Eqs. 20 and 30 at time t; jprev
  * holds phi*u at t-1 for the backward difference of d_t(phi u) (Sec. 3.2).
- * Arrays are [component][y][x] with x fastest; the grid is periodic.
+ * Arrays are [component][y][x] with x fastest; the grid is periodic in x,
+ * and in y either periodic or closed by walls (walls = 1).
  *
  * Readings where the paper is silent (listed with reasons in the design
  * notes of the repository):
@@ -37,7 +38,13 @@
  *   - prescribed single-vortex velocity: u = -U sin^2(pi X) sin(2 pi Y)
  *     cos(pi t/T), v = U sin^2(pi Y) sin(2 pi X) cos(pi t/T) with node-centred
  *     X = (x+1/2)/nx, Y = (y+1/2)/ny and t the step index (Eqs. 43-44 with
- *     the sign of the benchmark configuration; U < 0 gives the paper's sign).
+ *     the sign of the benchmark configuration; U < 0 gives the paper's sign);
+ *   - walls (the shear-flow set-up of Sec. 4.4; the paper gives no boundary
+ *     scheme): halfway bounce-back below y = 0 and above y = ny - 1; f gains
+ *     the moving-wall term 2 w_i rho (c_i . u_w)/c_s^2 with rho = rho(phi) of
+ *     the receiving node after streaming; g bounces back without a term (no
+ *     flux of phi through a wall); the stencils see a ghost row that mirrors
+ *     the wall row (zero normal gradient: neutral wetting, 90 degrees).
  */
 #include <math.h>
 #include <stdint.h>
@@ -48,7 +55,7 @@
 #define M_PI 3.14159265358979323846
 #endif
 
-/* ORC_PLANT selects a deliberately wrong variant of one formula, for the
+/* ORC_PLANT (1-10, 21-22) selects a deliberately wrong variant of one formula, for the
  * mutation test that shows the pins catch it (0 = the oracle as written). */
 #ifndef ORC_PLANT
 #define ORC_PLANT 0
@@ -106,8 +113,8 @@ static void build_minv(void) {
 /* ---- Parameters ---------------------------------------------------------- */
 typedef struct {
   int32_t nx, ny;
-  int32_t flow; /* 0: coupled f-g step; 1: g only, prescribed single vortex */
-  int32_t pad_;
+  int32_t flow;  /* 0: coupled f-g step; 1: g only, prescribed single vortex */
+  int32_t walls; /* 0: periodic in y; 1: walls below y = 0 and above y = ny-1 */
   double W;      /* interface width */
   double sigma;  /* surface tension (gamma in Sec. 2) */
   double lambda; /* penalty constant, Eq. 6; 0 gives the classical model */
@@ -117,6 +124,7 @@ typedef struct {
   double tau_f_l, tau_f_g; /* f relaxation times in the two bulks, Eq. 27 */
   double s_f[9], s_g[9];   /* MRT rates, Eq. 26; tied entries overwritten */
   double vortex_U, vortex_T;
+  double u_top, u_bot; /* wall velocities along x (walls = 1) */
 } orc_params;
 
 void orc_lattice(int32_t *cx, int32_t *cy, double *w) {
@@ -248,14 +256,24 @@ void orc_mrt(const double *f, const double *feq, const double *F,
   }
 }
 
-/* Isotropic gradient and Laplacian of Sec. 3.2 (Thampi et al.), periodic. */
-static void stencil(const double *chi, int nx, int ny, int x, int y,
-                    double *gx, double *gy, double *lap) {
+/* Isotropic gradient and Laplacian of Sec. 3.2 (Thampi et al.), periodic in
+ * x; in y periodic, or with walls a ghost row that mirrors the wall row
+ * (chi(x, -1) = chi(x, 0), chi(x, ny) = chi(x, ny-1): zero normal gradient). */
+static void stencil_w(const double *chi, int nx, int ny, int walls, int x, int y,
+                      double *gx, double *gy, double *lap) {
   double c0 = chi[(size_t)y * nx + x];
   double sx = 0.0, sy = 0.0, sl = 0.0;
   for (int i = 1; i < 9; ++i) {
     int xn = ((x + CX[i]) % nx + nx) % nx;
-    int yn = ((y + CY[i]) % ny + ny) % ny;
+    int yn = y + CY[i];
+#if ORC_PLANT == 22
+    if (0)
+#else
+    if (walls)
+#endif
+      yn = yn < 0 ? 0 : (yn >= ny ? ny - 1 : yn);
+    else
+      yn = (yn % ny + ny) % ny;
     double v = chi[(size_t)yn * nx + xn];
     sx += WT[i] * CX[i] * v / CS2;
 #if ORC_PLANT == 2
@@ -268,6 +286,11 @@ static void stencil(const double *chi, int nx, int ny, int x, int y,
   if (gx) *gx = sx;
   if (gy) *gy = sy;
   if (lap) *lap = sl;
+}
+
+static void stencil(const double *chi, int nx, int ny, int x, int y, double *gx,
+                    double *gy, double *lap) {
+  stencil_w(chi, nx, ny, 0, x, y, gx, gy, lap);
 }
 
 void orc_stencil(const double *chi, int32_t nx, int32_t ny, double *gx,
@@ -333,8 +356,8 @@ static void phase_fields(const orc_params *p, const double *g, work_t *w) {
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       size_t k = (size_t)y * nx + x;
-      stencil(w->phi, nx, ny, x, y, w->gpx + k, w->gpy + k, w->lap + k);
-      stencil(w->psi, nx, ny, x, y, w->gsx + k, w->gsy + k, NULL);
+      stencil_w(w->phi, nx, ny, p->walls, x, y, w->gpx + k, w->gpy + k, w->lap + k);
+      stencil_w(w->psi, nx, ny, p->walls, x, y, w->gsx + k, w->gsy + k, NULL);
     }
 }
 
@@ -401,6 +424,7 @@ static int check_params(const orc_params *p) {
                        !(p->tau_f_l > 0.5) || !(p->tau_f_g > 0.5)))
     return -1;
   if (p->flow == 1 && !(p->vortex_T != 0.0)) return -1;
+  if (p->walls != 0 && (p->walls != 1 || p->flow != 0)) return -1;
   return 0;
 }
 
@@ -419,7 +443,7 @@ int orc_init(const orc_params *p, const double *phi0, const double *u0,
   if (!lap) return -2;
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x)
-      stencil(phi0, nx, ny, x, y, NULL, NULL, lap + (size_t)y * nx + x);
+      stencil_w(phi0, nx, ny, p->walls, x, y, NULL, NULL, lap + (size_t)y * nx + x);
   for (int y = 0; y < ny; ++y)
     for (int x = 0; x < nx; ++x) {
       size_t k = (size_t)y * nx + x;
@@ -443,6 +467,35 @@ int orc_init(const orc_params *p, const double *phi0, const double *u0,
     }
   free(lap);
   return 0;
+}
+
+/* Opposite directions of Eq. 19. */
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+/* Moving-wall term of the halfway bounce-back for f: a population returning
+ * from a wall moving at u_w along x gains 2 w_i rho_w (c_i . u_w) / c_s^2,
+ * with rho_w = rho(phi) of the receiving wall node after streaming (phi from
+ * its g, which bounce back without a term: no flux of phi through a wall). */
+static void wall_momentum(const orc_params *p, double *f, const double *g) {
+  int nx = p->nx, ny = p->ny;
+  size_t n = (size_t)nx * ny;
+  for (int side = 0; side < 2; ++side) {
+    int y = side == 0 ? 0 : ny - 1;
+    int cy_in = side == 0 ? 1 : -1; /* directions entering from the wall */
+    double uw = side == 0 ? p->u_bot : p->u_top;
+    for (int x = 0; x < nx; ++x) {
+      size_t k = (size_t)y * nx + x;
+      double phi = 0.0;
+      for (int i = 0; i < 9; ++i) phi += g[i * n + k];
+      double rho = rho_of(p, phi);
+      for (int i = 0; i < 9; ++i)
+#if ORC_PLANT == 21
+        if (CY[i] == cy_in) f[i * n + k] -= 2.0 * WT[i] * rho * (CX[i] * uw) / CS2;
+#else
+        if (CY[i] == cy_in) f[i * n + k] += 2.0 * WT[i] * rho * (CX[i] * uw) / CS2;
+#endif
+    }
+  }
 }
 
 /* One collision at one node, given its macroscopic context. */
@@ -516,17 +569,24 @@ int orc_step(const orc_params *p, double *f, double *g, double *jprev,
         jprev[k] = jn[0];
         jprev[n + k] = jn[1];
       }
-    /* Streaming, left-hand sides of Eqs. 20 and 30: value moves to x + c_i. */
+    /* Streaming, left-hand sides of Eqs. 20 and 30: value moves to x + c_i.
+     * With walls, a value that would cross y = -1/2 or y = ny - 1/2 returns to
+     * its node in the opposite direction (halfway bounce-back). */
     for (int i = 0; i < 9; ++i)
       for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
           int xd = ((x + CX[i]) % nx + nx) % nx;
-          int yd = ((y + CY[i]) % ny + ny) % ny;
+          int yd = y + CY[i];
           size_t src = (size_t)i * n + (size_t)y * nx + x;
-          size_t dst = (size_t)i * n + (size_t)yd * nx + xd;
+          size_t dst;
+          if (p->walls && (yd < 0 || yd >= ny))
+            dst = (size_t)OPP[i] * n + (size_t)y * nx + x;
+          else
+            dst = (size_t)i * n + (size_t)((yd % ny + ny) % ny) * nx + xd;
           if (p->flow == 0) f[dst] = fs[src];
           g[dst] = gs[src];
         }
+    if (p->walls) wall_momentum(p, f, g);
   }
   free(w.phi);
   free(fs);

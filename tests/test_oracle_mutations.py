@@ -21,9 +21,12 @@ PLANTS = {
     8: "no clip of phi before psi (Eq. 37)",
     9: "rho s_0(u) dropped from the pressure (Eq. 29)",
     10: "sign of the sharpening flux flipped (Eq. 32)",
+    21: "sign of the moving-wall momentum term flipped (halfway bounce-back)",
+    22: "periodic ghost row at the walls instead of the mirrored one",
 }
 PIN_FILES = ["tests/test_oracle_lattice.py", "tests/test_oracle_node.py",
-             "tests/test_oracle_stencil.py", "tests/test_oracle_physics.py"]
+             "tests/test_oracle_stencil.py", "tests/test_oracle_physics.py",
+             "tests/test_oracle_walls.py"]
 
 
 @pytest.mark.parametrize("plant", sorted(PLANTS), ids=lambda k: f"plant{k}")
