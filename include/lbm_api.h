@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define LBM_ABI_VERSION 1
+#define LBM_ABI_VERSION 2
 
 typedef struct lbm_handle lbm_handle; /* opaque; freed by lbm_destroy */
 
@@ -71,7 +71,8 @@ enum {
 enum { LBM_F64 = 0, LBM_F32 = 1 };
 enum { LBM_FLOW_COUPLED = 0, LBM_FLOW_VORTEX = 1 }; /* see lbm_params.flow */
 
-/* Parameters of one case (one periodic grid). */
+/* Parameters of one case (one grid, periodic in x; in y periodic or closed
+ * by moving walls). */
 typedef struct {
   int32_t abi_version; /* must be LBM_ABI_VERSION */
   int32_t nx, ny;      /* nodes in x and y, each >= 1 */
@@ -84,7 +85,16 @@ typedef struct {
    * X = (x + 1/2)/nx, Y = (y + 1/2)/ny, t the step index; U < 0 gives the
    * sign printed in Eqs. 43-44. */
   int32_t flow;
-  int32_t reserved; /* set to 0 */
+  /* 0: periodic in y.  1: walls half a node below y = 0 and above y = ny-1,
+   * moving along x at u_wall_bottom and u_wall_top (the sheared cavity of
+   * Sec. 4.4; the paper gives no boundary scheme, so the reading is):
+   * halfway bounce-back; a returning f_i gains 2 w_i rho (c_i . u_w)/c_s^2
+   * with rho = rho(phi) of the receiving node; g bounces back without a
+   * term (no flux of phi through a wall: the phase volume is kept); the
+   * stencils see a ghost row mirroring the wall row (zero normal gradient
+   * of phi and psi: neutral wetting, 90-degree contact angle).
+   * LBM_FLOW_COUPLED only. */
+  int32_t walls;
   double W;         /* interface width (Eq. 4) */
   double sigma;     /* surface tension; beta = 12 sigma/W, kappa = 3 sigma W/2 (Sec. 2) */
   double lambda;    /* penalty constant (Eq. 6; 0.5 in the paper); 0 = classical C-H */
@@ -98,6 +108,7 @@ typedef struct {
    * usual choice) and must lie in (0, 2). */
   double s_f[9], s_g[9];
   double vortex_U, vortex_T; /* flow == LBM_FLOW_VORTEX only */
+  double u_wall_top, u_wall_bottom; /* walls == 1 only: wall velocities along x */
 } lbm_params;
 
 /* Device bytes the caller must provide for this batch (0 on bad params). */

@@ -156,16 +156,26 @@ cudaError_t launch_init<LBM_T>(const CaseDev<LBM_T>& cd, double beta4, double ka
 }
 
 template <>
-cudaError_t launch_plane_import<LBM_T>(LBM_T* dst, const double* src, int i, int nx,
-                                       int ny, cudaStream_t s) {
-  plane_import<LBM_T><<<grid_for((int64_t)nx * ny, 256), 256, 0, s>>>(dst, src, i, nx, ny);
+cudaError_t launch_plane_import<LBM_T>(LBM_T* buf, int64_t P, const double* src, int i, int nx,
+                                       int ny, int walls, cudaStream_t s) {
+  plane_import<LBM_T><<<grid_for((int64_t)nx * ny, 256), 256, 0, s>>>(buf, P, src, i, nx, ny,
+                                                                      walls);
   return cudaGetLastError();
 }
 
 template <>
-cudaError_t launch_plane_export<LBM_T>(double* dst, const LBM_T* src, int i, int nx,
-                                       int ny, cudaStream_t s) {
-  plane_export<LBM_T><<<grid_for((int64_t)nx * ny, 256), 256, 0, s>>>(dst, src, i, nx, ny);
+cudaError_t launch_plane_export<LBM_T>(double* dst, const LBM_T* buf, int64_t P, int i, int nx,
+                                       int ny, int walls, cudaStream_t s) {
+  plane_export<LBM_T><<<grid_for((int64_t)nx * ny, 256), 256, 0, s>>>(dst, buf, P, i, nx, ny,
+                                                                      walls);
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_wall_f_fix<LBM_T>(double* v, const CaseDev<LBM_T>& cd, int par, int i,
+                                     double sign, cudaStream_t s) {
+  wall_f_fix<LBM_T><<<grid_for(2 * (int64_t)cd.nx, 256), 256, 0, s>>>(
+      v, cd, par, i, (double)cd.rho_g, (double)cd.drho, sign);
   return cudaGetLastError();
 }
 

@@ -40,12 +40,17 @@ cudaError_t launch_init(const CaseDev<T>& cd, double beta4, double kappa,
                         const double* phi0, const double* u0, int vortex,
                         double vU, int parity, cudaStream_t s);
 
+// buf: the 9-plane buffer with plane stride P (walls: bounce-back positions)
 template <typename T>
-cudaError_t launch_plane_import(T* dst_plane, const double* src, int i, int nx,
-                                int ny, cudaStream_t s);
+cudaError_t launch_plane_import(T* buf, int64_t P, const double* src, int i, int nx, int ny,
+                                int walls, cudaStream_t s);
 template <typename T>
-cudaError_t launch_plane_export(double* dst, const T* src_plane, int i, int nx,
-                                int ny, cudaStream_t s);
+cudaError_t launch_plane_export(double* dst, const T* buf, int64_t P, int i, int nx, int ny,
+                                int walls, cudaStream_t s);
+// moving-wall term of f plane i at the wall rows, added (sign 1) or removed (-1)
+template <typename T>
+cudaError_t launch_wall_f_fix(double* v, const CaseDev<T>& cd, int par, int i, double sign,
+                              cudaStream_t s);
 template <typename T>
 cudaError_t launch_copy_to_T(T* dst, const double* src, int64_t n, cudaStream_t s);
 template <typename T>

@@ -566,6 +566,8 @@ int check_handle(lbm_handle* h, bool need_ws) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (h->ncases != 1) return fail(LBM_ERR_ARG, "reverse mode needs a single-case handle");
   if (h->precision != LBM_F64) return fail(LBM_ERR_ARG, "reverse mode needs an FP64 handle");
+  if (h->params[0].walls)
+    return fail(LBM_ERR_UNIMPLEMENTED, "reverse mode of the wall boundaries is not built");
   if (need_ws && !h->adj_ws) return fail(LBM_ERR_WORKSPACE, "call lbm_adjoint_attach first");
   return LBM_OK;
 }

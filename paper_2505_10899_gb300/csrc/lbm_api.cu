@@ -86,6 +86,10 @@ int check_params(const lbm_params* c, int n) {
       if (!(p.vortex_T != 0) || !std::isfinite(p.vortex_T) || !std::isfinite(p.vortex_U))
         return bad("vortex_T must be nonzero");
     }
+    if (p.walls != 0 && p.walls != 1) return bad("walls must be 0 or 1");
+    if (p.walls && p.flow != LBM_FLOW_COUPLED) return bad("walls need the coupled flow");
+    if (!std::isfinite(p.u_wall_top) || !std::isfinite(p.u_wall_bottom))
+      return bad("wall velocities must be finite");
     for (int i = 0; i < 9; ++i) {
       const bool tied_f = (i == 7 || i == 8), tied_g = (i == 3 || i == 5);
       if (!tied_f && !(p.s_f[i] > 0 && p.s_f[i] < 2)) return bad("s_f rates must lie in (0,2)");
@@ -263,6 +267,9 @@ CaseDev<T> make_case(const lbm_handle* h, int k) {
   c.sD7 = (T)(-0.25 * s7);
   c.hD7 = (T)(0.25 * (1.0 - 0.5 * s7));
   c.nregions = h->nregions[k];
+  c.walls = p.walls;
+  c.u_top = (T)(p.walls ? p.u_wall_top : 0.0);
+  c.u_bot = (T)(p.walls ? p.u_wall_bottom : 0.0);
   c.vol_base = h->vol_base[k];
   c.item_begin = h->item_begin[k];
   c.item_end = h->item_end[k];
@@ -448,7 +455,10 @@ int do_get_state(lbm_handle* h, int c, double* f, double* g, double* j) {
     const T* buf = which == 0 ? cd.g[h->parity] : cd.f[h->parity];
     if (!out || !buf) continue;
     for (int i = 0; i < 9; ++i) {
-      cudaError_t e = lbmk::launch_plane_export<T>(st, buf + i * cd.plane, i, p.nx, p.ny, h->stream);
+      cudaError_t e =
+          lbmk::launch_plane_export<T>(st, buf, cd.plane, i, p.nx, p.ny, cd.walls, h->stream);
+      if (e == cudaSuccess && which == 1 && cd.walls)  // f arriving from a wall
+        e = lbmk::launch_wall_f_fix<T>(st, cd, h->parity, i, 1.0, h->stream);
       if (e == cudaSuccess && which == 0 && i == 0 && cd.g0lo[h->parity])
         e = lbmk::launch_add_lo_f64<T>(st, cd.g0lo[h->parity], n, h->stream);  // g_0 = hi + lo
       if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
@@ -479,7 +489,11 @@ int do_set_state(lbm_handle* h, int c, const double* f, const double* g, const d
     if (!in || !buf) continue;
     for (int i = 0; i < 9; ++i) {
       LBM_CUDA(cudaMemcpyAsync(st, in + i * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-      cudaError_t e = lbmk::launch_plane_import<T>(buf + i * cd.plane, st, i, p.nx, p.ny, h->stream);
+      cudaError_t e = cudaSuccess;
+      if (which == 1 && cd.walls)  // g is already in place: rho(phi) is known
+        e = lbmk::launch_wall_f_fix<T>(st, cd, h->parity, i, -1.0, h->stream);
+      if (e == cudaSuccess)
+        e = lbmk::launch_plane_import<T>(buf, cd.plane, st, i, p.nx, p.ny, cd.walls, h->stream);
       if (e == cudaSuccess && which == 0 && i == 0 && cd.g0lo[h->parity])
         e = lbmk::launch_lo_from_f64<T>(cd.g0lo[h->parity], buf, st, n, h->stream);
       if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
@@ -597,6 +611,10 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
     h->tma_ok = true;
     for (int k = 0; k < ncases; ++k)
       if (cases[k].nx % vec != 0 || cases[k].nx < 4) h->tma_ok = false;
+    // the bulk-copy kernel stages periodic source rows only: walls run the
+    // register-pipelined kernel
+    for (int k = 0; k < ncases; ++k)
+      if (cases[k].walls) h->tma_ok = false;
   }
 
   auto cleanup = [&](int code) {

@@ -11,6 +11,8 @@ namespace lbmk {
 __device__ __constant__ static const int kCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ __constant__ static const int kCY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
+__device__ __constant__ static const int kOPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
 // Position in a pull buffer that holds the value population i must deliver
 // to node (x, y): (x - c_ix, y - c_iy), periodic.
 __device__ __forceinline__ int64_t pull_src(int i, int x, int y, int nx, int ny) {
@@ -18,6 +20,44 @@ __device__ __forceinline__ int64_t pull_src(int i, int x, int y, int nx, int ny)
   xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
   ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
   return (int64_t)ys * nx + xs;
+}
+
+// The same with walls: a population that would come from beyond a wall is
+// the node's own population in the opposite direction (halfway bounce-back).
+// Returns the position; *plane receives the plane it sits in.
+__device__ __forceinline__ int64_t pull_loc(int i, int x, int y, int nx, int ny, int walls,
+                                            int* plane) {
+  const int ys = y - kCY[i];
+  if (walls && (ys < 0 || ys >= ny)) {
+    *plane = kOPP[i];
+    return (int64_t)y * nx + x;
+  }
+  *plane = i;
+  return pull_src(i, x, y, nx, ny);
+}
+
+// Moving-wall term carried by population i at node (x, y) after streaming:
+// 2 w_i rho (c_i . u_w) / c_s^2 for a population entering from a wall.
+template <typename T>
+__device__ __forceinline__ double wall_term(const CaseDev<T>& cd, int i, int y, double rho) {
+  if (!cd.walls) return 0.0;
+  const double w = (i == 0) ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+  if (y == 0 && kCY[i] == 1) return 6.0 * w * rho * kCX[i] * (double)cd.u_bot;
+  if (y == cd.ny - 1 && kCY[i] == -1) return 6.0 * w * rho * kCX[i] * (double)cd.u_top;
+  return 0.0;
+}
+
+// phi at node (x, y) of buffer `par` (Eq. 35, the pulled g), in FP64.
+template <typename T>
+__device__ __forceinline__ double phi_at(const CaseDev<T>& cd, int par, int x, int y) {
+  double phi = 0.0;
+  for (int i = 0; i < 9; ++i) {
+    int pl;
+    const int64_t pos = pull_loc(i, x, y, cd.nx, cd.ny, cd.walls, &pl);
+    phi += (double)cd.g[par][pl * cd.plane + pos];
+  }
+  if (cd.g0lo[par]) phi += (double)cd.g0lo[par][(int64_t)y * cd.nx + x];
+  return phi;
 }
 
 // Initial state (Sec. 4 set-ups), computed in FP64 and rounded once:
@@ -36,7 +76,9 @@ __global__ void init_kernel(CaseDev<T> cd, double beta4, double kappa,
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    // rows above and below; with walls the ghost row mirrors the wall row
+    const int ym = y == 0 ? (cd.walls ? 0 : ny - 1) : y - 1;
+    const int yp = y == ny - 1 ? (cd.walls ? ny - 1 : 0) : y + 1;
     const double p = phi0[k];
     const double pE = phi0[(int64_t)y * nx + xp], pW = phi0[(int64_t)y * nx + xm];
     const double pN = phi0[(int64_t)yp * nx + x], pS = phi0[(int64_t)ym * nx + x];
@@ -68,11 +110,16 @@ __global__ void init_kernel(CaseDev<T> cd, double beta4, double kappa,
       const double cu = kCX[i] * ux + kCY[i] * uy;
       const double cJ = kCX[i] * Jx + kCY[i] * Jy;
       const double gi = (i == 0) ? p + (w - 1.0) * lam : w * lam + 3.0 * w * cJ;
-      const int64_t dst = (int64_t)i * cd.plane + pull_src(i, x, y, nx, ny);
+      int pl;
+      const int64_t dst = (int64_t)0 + pull_loc(i, x, y, nx, ny, cd.walls, &pl) +
+                          (int64_t)pl * cd.plane;
       gb[dst] = (T)gi;
       // FP32: the rest population is a float pair (high part + low part)
       if (i == 0 && cd.g0lo[par]) cd.g0lo[par][k] = (T)(gi - (double)(T)gi);
-      if (fb) fb[dst] = (T)(rho * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2));
+      // f arriving from a wall carries the moving-wall term on top of the
+      // stored value: store f_eq minus that term
+      if (fb)
+        fb[dst] = (T)(rho * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2) - wall_term(cd, i, y, rho));
     }
     cd.J[par][k] = (T)Jx;
     cd.J[par][cd.plane + k] = (T)Jy;
@@ -81,25 +128,46 @@ __global__ void init_kernel(CaseDev<T> cd, double beta4, double kappa,
 
 // Import one population plane (FP64 host layout, value at the node it
 // belongs to after streaming) into a pull buffer, or export it.
+// buf: the 9-plane buffer (plane stride P); with walls the value of plane i
+// at a wall row may sit in the opposite plane (bounce-back).
 template <typename T>
-__global__ void plane_import(T* __restrict__ dst_plane, const double* __restrict__ src,
-                             int i, int nx, int ny) {
+__global__ void plane_import(T* __restrict__ buf, int64_t P, const double* __restrict__ src,
+                             int i, int nx, int ny, int walls) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
-    dst_plane[pull_src(i, x, y, nx, ny)] = (T)src[k];
+    int pl;
+    const int64_t pos = pull_loc(i, x, y, nx, ny, walls, &pl);
+    buf[pl * P + pos] = (T)src[k];
   }
 }
 
 template <typename T>
-__global__ void plane_export(double* __restrict__ dst, const T* __restrict__ src_plane,
-                             int i, int nx, int ny) {
+__global__ void plane_export(double* __restrict__ dst, const T* __restrict__ buf, int64_t P,
+                             int i, int nx, int ny, int walls) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
-    dst[k] = (double)src_plane[pull_src(i, x, y, nx, ny)];
+    int pl;
+    const int64_t pos = pull_loc(i, x, y, nx, ny, walls, &pl);
+    dst[k] = (double)buf[pl * P + pos];
+  }
+}
+
+// f plane i of an exported / imported state at the wall rows: add (sign +1)
+// or remove (sign -1) the moving-wall term, with rho from the phi of the g
+// buffer of parity `par` (which must already hold the state).
+template <typename T>
+__global__ void wall_f_fix(double* __restrict__ v, CaseDev<T> cd, int par, int i,
+                           double rho_g, double drho, double sign) {
+  const int nx = cd.nx, ny = cd.ny;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 2 * nx; k += gridDim.x * blockDim.x) {
+    const int x = k % nx, y = k < nx ? 0 : ny - 1;
+    if (k >= nx && ny == 1) continue;  // one row: already handled as row 0
+    const double rho = rho_g + phi_at(cd, par, x, y) * drho;
+    v[(int64_t)y * nx + x] += sign * wall_term(cd, i, y, rho);
   }
 }
 
@@ -155,18 +223,24 @@ __global__ void __launch_bounds__(BX) volume_partial(const CaseDev<T>* __restric
     const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
     for (int k = 0; k < it.nrows; ++k) {
       const int y = it.y0 + k;
-      const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-      const int64_t o0 = (int64_t)y * nx, om = (int64_t)ym * nx, op = (int64_t)yp * nx;
-      double phi = (double)gs[o0 + x];
-      if (cd.g0lo[parity]) phi += (double)cd.g0lo[parity][o0 + x];
-      phi += (double)gs[P + o0 + xm];
-      phi += (double)gs[2 * P + om + x];
-      phi += (double)gs[3 * P + o0 + xp];
-      phi += (double)gs[4 * P + op + x];
-      phi += (double)gs[5 * P + om + xm];
-      phi += (double)gs[6 * P + om + xp];
-      phi += (double)gs[7 * P + op + xp];
-      phi += (double)gs[8 * P + op + xm];
+      const int64_t o0 = (int64_t)y * nx;
+      double phi;
+      if (cd.walls) {
+        phi = phi_at(cd, parity, x, y);
+      } else {
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const int64_t om = (int64_t)ym * nx, op = (int64_t)yp * nx;
+        phi = (double)gs[o0 + x];
+        if (cd.g0lo[parity]) phi += (double)cd.g0lo[parity][o0 + x];
+        phi += (double)gs[P + o0 + xm];
+        phi += (double)gs[2 * P + om + x];
+        phi += (double)gs[3 * P + o0 + xp];
+        phi += (double)gs[4 * P + op + x];
+        phi += (double)gs[5 * P + om + xm];
+        phi += (double)gs[6 * P + om + xp];
+        phi += (double)gs[7 * P + op + xp];
+        phi += (double)gs[8 * P + op + xm];
+      }
       const int lab = cd.labels ? (int)cd.labels[o0 + x] : 0;
 #pragma unroll
       for (int r = 0; r < kMaxRegions; ++r)

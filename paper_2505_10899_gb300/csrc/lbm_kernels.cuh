@@ -47,6 +47,43 @@ __device__ __forceinline__ void pull9(const T* __restrict__ b, uint32_t P,
   v[8] = ld<COHERENT>(b + (8u * P + op + xm));
 }
 
+// The same pull at a row next to a wall (bot: row 0, top: row ny-1):
+// halfway bounce-back -- a population that would come from beyond the wall is
+// the node's own post-collision population in the opposite direction (the
+// moving-wall term of f is added by the caller, once phi is known).
+template <bool COHERENT = false, typename T>
+__device__ __forceinline__ void pull9w(const T* __restrict__ b, uint32_t P, uint32_t o0,
+                                       uint32_t om, uint32_t op, uint32_t x, uint32_t xm,
+                                       uint32_t xp, bool bot, bool top, T v[9]) {
+  v[0] = ld<COHERENT>(b + (o0 + x));
+  v[1] = ld<COHERENT>(b + (P + o0 + xm));
+  v[3] = ld<COHERENT>(b + (3u * P + o0 + xp));
+  v[2] = ld<COHERENT>(b + (bot ? 4u * P + o0 + x : 2u * P + om + x));
+  v[5] = ld<COHERENT>(b + (bot ? 7u * P + o0 + x : 5u * P + om + xm));
+  v[6] = ld<COHERENT>(b + (bot ? 8u * P + o0 + x : 6u * P + om + xp));
+  v[4] = ld<COHERENT>(b + (top ? 2u * P + o0 + x : 4u * P + op + x));
+  v[7] = ld<COHERENT>(b + (top ? 5u * P + o0 + x : 7u * P + op + xp));
+  v[8] = ld<COHERENT>(b + (top ? 6u * P + o0 + x : 8u * P + op + xm));
+}
+
+// Moving-wall term of the bounced f (walls along x at u_bot below row 0 and
+// u_top above row ny-1): f_i += 2 w_i rho (c_i . u_w)/c_s^2 = rho c_ix u_w / 6
+// for the diagonal populations entering from the wall (w_i = 1/36).
+template <typename T>
+__device__ __forceinline__ void wall_momentum(T F[9], T rho, bool bot, bool top, T u_bot,
+                                              T u_top) {
+  if (bot) {
+    const T d = rho * u_bot * T(1.0 / 6.0);
+    F[5] += d;  // c = (1, 1)
+    F[6] -= d;  // c = (-1, 1)
+  }
+  if (top) {
+    const T d = rho * u_top * T(1.0 / 6.0);
+    F[7] -= d;  // c = (-1, -1)
+    F[8] += d;  // c = (1, -1)
+  }
+}
+
 // CTA reduction of the fused phase volume: warp shuffles, then warps in order.
 template <int BX>
 __device__ __forceinline__ void write_volume_partial(double vacc, double* vred, double* out) {
@@ -111,8 +148,15 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
   const CaseK<T> K = case_consts<T, COUPLED>(a, cdp, xc);
 
   auto rowoff = [&](int r) -> uint32_t { return (uint32_t)r * (uint32_t)nx; };
-  // periodic row index for r in [-1, ny + 1]
-  auto wrap = [&](int r) -> int { return r < 0 ? r + ny : (r >= ny ? r - ny : r); };
+  // row index for r in [-1, ny]: periodic, or with walls the mirrored ghost
+  // row (rows -1 and ny only feed phi and psi to the stencils)
+  const bool walls = cdp->walls != 0;
+  auto wrap = [&](int r) -> int {
+    if (walls) return r < 0 ? 0 : (r >= ny ? ny - 1 : r);
+    return r < 0 ? r + ny : (r >= ny ? r - ny : r);
+  };
+  auto at_bot = [&](int rr) -> bool { return walls && rr == 0; };
+  auto at_top = [&](int rr) -> bool { return walls && rr == ny - 1; };
 
   // register sets of the pipeline: rows k (current), k+1 (next), k+2 (fetch)
   struct Regs {
@@ -125,9 +169,10 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
     const int rr = wrap(r);
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
-    pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G);
+    const bool bt = at_bot(rr), tp = at_top(rr);
+    pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, bt, tp, R.G);
     R.lo = LO ? ld<COHERENT>(los + (o0 + xc)) : T(0);
-    if (COUPLED) pull9<COHERENT>(fs, P, o0, om, op, xc, xm, xp, R.F);
+    if (COUPLED) pull9w<COHERENT>(fs, P, o0, om, op, xc, xm, xp, bt, tp, R.F);
     if (MODE == kModeStep) {  // phi*u of the previous step at the own node
       R.J[0] = ld<COHERENT>(Js + (o0 + xc));
       R.J[1] = ld<COHERENT>(Js + (P + o0 + xc));
@@ -137,13 +182,13 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
     const int rr = wrap(r);
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
-    pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G);
+    pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, at_bot(rr), at_top(rr), R.G);
   };
   auto fetch_halo = [&](int r, T H[9]) {
     const int rr = wrap(r);
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
-    pull9<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, H);
+    pull9w<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, at_bot(rr), at_top(rr), H);
   };
   // write phi/psi of local row k (k >= -1) into the ring.  phi is the plain
   // sum of the nine pulled values (FP32: the low part of g_0 enters only the
@@ -195,6 +240,9 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
       const int y = wrap(y0 + k);
       const Stencil<T> S = read_stencil(ring, k, tid + 1);
       if (do_vol) vacc += (double)S.p;
+      if (COUPLED && walls && (y == 0 || y == ny - 1))
+        wall_momentum(C.F, K.rho_g + S.p * K.drho, y == 0, y == ny - 1, cdp->u_bot,
+                      cdp->u_top);
       const NodeOut<T> o =
           node_update<T, COUPLED, MODE>(a.ph, K, C.F, C.G, C.lo, C.J[0], C.J[1], S, y);
       const uint32_t node = rowoff(y) + (uint32_t)xc;

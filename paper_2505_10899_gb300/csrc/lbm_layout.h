@@ -30,6 +30,9 @@ struct CaseDev {
   int32_t nregions;      // volume regions of this case
   int32_t vol_base;      // first output slot of this case's volumes
   int32_t item_begin, item_end;  // work items of this case
+  int32_t walls;         // 1: moving walls below row 0 and above row ny-1
+  int32_t pad_;
+  T u_top, u_bot;        // wall velocities along x
 };
 
 // Launch-uniform physics, converted to the working precision T.

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "liblbm_gb300.so")
 
-LBM_ABI_VERSION = 1
+LBM_ABI_VERSION = 2
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_WORKSPACE = 0, -1, -2, -3
 LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_UNIMPLEMENTED = -4, -5, -6
 LBM_F64, LBM_F32 = 0, 1
@@ -32,13 +32,14 @@ class LbmError(RuntimeError):
 class lbm_params(ctypes.Structure):
     _fields_ = [
         ("abi_version", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
-        ("precision", ctypes.c_int32), ("flow", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("flow", ctypes.c_int32), ("walls", ctypes.c_int32),
         ("W", ctypes.c_double), ("sigma", ctypes.c_double), ("lam", ctypes.c_double),
         ("xi", ctypes.c_double), ("tau_g", ctypes.c_double),
         ("rho_l", ctypes.c_double), ("rho_g", ctypes.c_double),
         ("tau_f_l", ctypes.c_double), ("tau_f_g", ctypes.c_double),
         ("s_f", ctypes.c_double * 9), ("s_g", ctypes.c_double * 9),
         ("vortex_U", ctypes.c_double), ("vortex_T", ctypes.c_double),
+        ("u_wall_top", ctypes.c_double), ("u_wall_bottom", ctypes.c_double),
     ]
 
 
@@ -135,7 +136,7 @@ def make_params(case: dict, precision: str = "f32") -> lbm_params:
     p.nx, p.ny = int(case["nx"]), int(case["ny"])
     p.precision = {"f64": LBM_F64, "f32": LBM_F32}[precision]
     p.flow = {"coupled": LBM_FLOW_COUPLED, "vortex": LBM_FLOW_VORTEX}[case.get("flow", "coupled")]
-    p.reserved = 0
+    p.walls = int(case.get("walls", 0))
     p.W = case["W"]
     p.sigma = case["sigma"]
     p.lam = case.get("lambda", 0.5)
@@ -152,6 +153,8 @@ def make_params(case: dict, precision: str = "f32") -> lbm_params:
         p.s_g[k] = sg[k]
     p.vortex_U = case.get("vortex_U", 0.0)
     p.vortex_T = case.get("vortex_T", 1.0)
+    p.u_wall_top = case.get("u_top", 0.0)
+    p.u_wall_bottom = case.get("u_bot", 0.0)
     return p
 
 

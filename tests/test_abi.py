@@ -48,8 +48,8 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_params_struct_layout(L):
-    # 6 int32 + 9 doubles + 2x9 rates + 2 doubles, no padding
-    assert ctypes.sizeof(L.lbm_params) == 6 * 4 + 9 * 8 + 18 * 8 + 2 * 8
+    # 6 int32 + 9 doubles + 2x9 rates + 2 vortex + 2 wall doubles, no padding
+    assert ctypes.sizeof(L.lbm_params) == 6 * 4 + 9 * 8 + 18 * 8 + 2 * 8 + 2 * 8
     assert L.lib().lbm_abi_version() == L.LBM_ABI_VERSION
 
 
@@ -65,7 +65,9 @@ def test_workspace_bytes_and_validation(L):
     assert n32 > 64 * 32 * (38 * 4) and n64 > n32
     for bad in (dict(tau_g=0.5), dict(W=0.0), dict(rho_l=-1.0), dict(tau_f_l=0.4),
                 dict(s_f=[0.0] + [1.0] * 8),
-                dict(s_g=[1.0, 2.0] + [1.0] * 7)):
+                dict(s_g=[1.0, 2.0] + [1.0] * 7), dict(walls=2),
+                dict(walls=1, flow="vortex", vortex_U=0.02, vortex_T=100.0),
+                dict(walls=1, u_top=float("nan"))):
         assert L.lbm_workspace_bytes([L.make_params(_case(**bad), "f32")]) == 0
     # tied rates may hold anything (they are replaced by 1/tau)
     ok = L.make_params(_case(s_f=[1.0] * 7 + [9.0, 9.0], s_g=[1, 1, 1, 7.0, 1, 7.0, 1, 1, 1]))

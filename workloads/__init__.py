@@ -226,3 +226,24 @@ def random_state3(nx, ny, nz, seed, phi_lo=-0.05, phi_hi=1.05):
     f = uniform(seed + 2, (19, nz, ny, nx), -2e-3, 2e-3)
     j = uniform(seed + 3, (3, nz, ny, nx), -1e-3, 1e-3)
     return f, g, j
+
+
+def shear_droplet(nx=512, ny=256, R=40.0, U=0.01, Ca=0.1, Re=0.1, W=4.0, tau_g=0.8,
+                  lam=0.5, rho_ratio=1.0):
+    """A droplet in the sheared cavity of Sec. 4.4 (configs[3]): walls below
+    y = 0 and above y = ny - 1 moving at -U and +U, droplet of radius R at the
+    centre, equal kinematic viscosities.  Shear rate G = 2U/ny; the viscosity
+    and surface tension follow from Re = G R^2 / nu and Ca = rho nu G R / sigma.
+    The fluid starts on the linear Couette profile through the wall positions
+    (walls half a node outside the end rows).  Returns (case, phi0, u0)."""
+    G = 2.0 * U / ny
+    nu = G * R * R / Re
+    tau_f = 3.0 * nu + 0.5
+    sigma = nu * G * R / Ca
+    case = base_case(nx, ny, W=W, sigma=sigma, tau_g=tau_g, rho_l=rho_ratio, rho_g=1.0,
+                     tau_f_l=tau_f, tau_f_g=tau_f, walls=1, u_top=U, u_bot=-U,
+                     **{"lambda": lam})
+    phi0 = tanh_disc(nx, ny, 0.5 * nx, 0.5 * ny - 0.5, R, W)
+    u0 = np.zeros((2, ny, nx))
+    u0[0] = -U + 2.0 * U * (np.arange(ny, dtype=np.float64)[:, None] + 0.5) / ny
+    return case, phi0, u0
