@@ -254,19 +254,22 @@ int lbm_set_time(lbm_handle* h, int64_t t);
  *     given the adjoint of S_{t+1} (d_adj_in), writes the adjoint of S_t
  *     (d_adj_out, a different buffer) through the transposed Jacobian of one
  *     step (Eqs. 20-37 as computed by lbm_step), and accumulates on the device
- *     the derivatives with respect to (sigma, tau_g, lambda, tau_f); with
- *     h_param_grads[4] non-NULL the accumulated values are added to it and the
- *     accumulator is cleared (this synchronises), with NULL the call is
- *     asynchronous.  The tau_f entry is zero when tau_f varies with phi or in
- *     vortex mode.  The state is not modified.  At the clip of Eq. 37 and where
- *     |grad psi| = 0 the derivative of the branch taken is used.
+ *     the derivatives with respect to (sigma, tau_g, lambda, tau_f,
+ *     u_wall_top, u_wall_bottom); with h_param_grads[6] non-NULL the
+ *     accumulated values are added to it and the accumulator is cleared (this
+ *     synchronises), with NULL the call is asynchronous.  The tau_f entry is
+ *     zero when tau_f varies with phi or in vortex mode, the wall entries
+ *     without walls.  Walls are transposed with the rest (bounce-back, the
+ *     moving-wall term, the mirrored ghost rows).  The state is not modified.
+ *     At the clip of Eq. 37 and where |grad psi| = 0 the derivative of the
+ *     branch taken is used.
  *   lbm_adjoint_init: adjoint of the initial-state map of lbm_init: given the
  *     adjoint of S_0, writes d_adj_phi0 [ny][nx] and accumulates the sigma and
  *     lambda derivatives (h_param_grads as for lbm_adjoint_step); d_phi0
  *     [ny][nx] and d_u0 ([2][ny][nx] or NULL) are the device copies of the
  *     initial fields.
  *   lbm_adjoint_take_param_grads: adds the accumulated parameter derivatives
- *     to h_param_grads[4] and clears the accumulator (synchronises).
+ *     to h_param_grads[6] and clears the accumulator (synchronises).
  * Synchronise when h_param_grads is non-NULL.  Errors: LBM_ERR_ARG (batch,
  * FP32 handle, null buffers), LBM_ERR_WORKSPACE (no scratch), LBM_ERR_CUDA. */
 size_t lbm_adjoint_workspace_bytes(const lbm_handle* h);

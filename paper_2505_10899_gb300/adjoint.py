@@ -3,7 +3,8 @@ around the library's discrete adjoint (lbm_adjoint_step / lbm_adjoint_init).
 
 ``coupled_run(phi0, theta, case, nsteps, ckpt_every)`` advances one FP64 case
 and returns phi at the final step as a CUDA tensor; it is differentiable with
-respect to the initial field phi0 and theta = (sigma, tau_g, lambda, tau_f).
+respect to the initial field phi0 and theta = (sigma, tau_g, lambda, tau_f) or,
+for a case with walls, (sigma, tau_g, lambda, tau_f, u_wall_top, u_wall_bottom).
 The backward pass restores a snapshot every ``ckpt_every`` steps, recomputes
 the states of that segment on the GPU, and runs the adjoint steps backwards.
 All arithmetic runs in the CUDA library; torch holds the device buffers.
@@ -66,7 +67,7 @@ class AdjointSim:
 
     def vjp_step(self, adj_in, grads=None, adj_out=None):
         """Adjoint of S_t from the adjoint of S_{t+1}.  Parameter derivatives
-        accumulate on the device; with ``grads`` (numpy[4]) they are fetched."""
+        accumulate on the device; with ``grads`` (numpy[6]) they are fetched."""
         if adj_out is None:
             adj_out = torch.empty((20,) + self.shape, dtype=torch.float64, device=self.dev)
         rc = lbm.lbm_adjoint_step(self.h, adj_in.data_ptr(), adj_out.data_ptr(), grads)
@@ -92,6 +93,8 @@ def case_with(case, theta):
     c = dict(case)
     c["sigma"], c["tau_g"], c["lambda"] = float(theta[0]), float(theta[1]), float(theta[2])
     c["tau_f_l"] = c["tau_f_g"] = float(theta[3])
+    if len(theta) > 4:
+        c["u_top"], c["u_bot"] = float(theta[4]), float(theta[5])
     return c
 
 
@@ -108,13 +111,14 @@ class CoupledRun(torch.autograd.Function):
         phiT = asim.phi()
         ctx.asim, ctx.ckpts, ctx.nsteps, ctx.k = asim, ckpts, nsteps, ckpt_every
         ctx.theta_dtype, ctx.theta_device = theta.dtype, theta.device
+        ctx.ntheta = int(theta.numel())
         ctx.phi0_dtype, ctx.phi0_device = phi0.dtype, phi0.device
         return phiT
 
     @staticmethod
     def backward(ctx, grad_phiT):
         asim, nsteps, k = ctx.asim, ctx.nsteps, ctx.k
-        grads = np.zeros(4)
+        grads = np.zeros(6)
         adj = asim.seed_phi(grad_phiT)
         spare = torch.empty_like(adj)
         seg = [torch.empty_like(adj) for _ in range(k - 1)]  # recomputed states
@@ -133,7 +137,8 @@ class CoupledRun(torch.autograd.Function):
         dphi0 = asim.vjp_init(adj, None)
         asim.take_grads(grads)
         asim.close()
-        gtheta = torch.as_tensor(grads, dtype=ctx.theta_dtype, device=ctx.theta_device)
+        gtheta = torch.as_tensor(grads[:ctx.ntheta], dtype=ctx.theta_dtype,
+                                 device=ctx.theta_device)
         dphi0 = dphi0.to(device=ctx.phi0_device, dtype=ctx.phi0_dtype)
         return dphi0, gtheta, None, None, None, None
 
@@ -141,3 +146,23 @@ class CoupledRun(torch.autograd.Function):
 def coupled_run(phi0, theta, case, nsteps, ckpt_every=16, u0=None):
     """phi after nsteps coupled steps, differentiable in phi0 and theta."""
     return CoupledRun.apply(phi0, theta, case, int(nsteps), int(ckpt_every), u0)
+
+
+def taylor_deformation(phi):
+    """Taylor deformation D = (L - B)/(L + B) of a droplet from the second
+    moments of phi about its centroid (L, B: semi-axes of the ellipse with
+    those moments, proportional to the square roots of their eigenvalues).
+    phi: [ny][nx] tensor; differentiable (torch autograd), for the shear-flow
+    objective of the sheared-droplet set-up.  The droplet must not touch the
+    periodic x-boundary."""
+    ny, nx = phi.shape
+    y = torch.arange(ny, dtype=phi.dtype, device=phi.device)[:, None]
+    x = torch.arange(nx, dtype=phi.dtype, device=phi.device)[None, :]
+    m = phi.sum()
+    cx, cy = (phi * x).sum() / m, (phi * y).sum() / m
+    dx, dy = x - cx, y - cy
+    ixx, iyy, ixy = (phi * dx * dx).sum() / m, (phi * dy * dy).sum() / m, (phi * dx * dy).sum() / m
+    # eigenvalues of [[ixx, ixy], [ixy, iyy]]
+    half_tr, rad = 0.5 * (ixx + iyy), torch.sqrt(0.25 * (ixx - iyy) ** 2 + ixy * ixy)
+    L, B = torch.sqrt(half_tr + rad), torch.sqrt(half_tr - rad)
+    return (L - B) / (L + B)

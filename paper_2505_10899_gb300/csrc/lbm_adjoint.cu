@@ -17,6 +17,10 @@
 //              psi, and adds the total to the adjoints of its 9 pulled g.
 // The clip of Eq. 37 and the normalisation of grad(psi) use the derivative
 // of the branch taken (0 outside (0,1) and where |grad psi| = 0).
+// Walls (bounce-back rows, moving-wall term, mirrored ghost rows) are
+// transposed as well: the bounce-back keeps the pull a bijection between
+// buffer positions and (node, direction), and the mirrored ghost rows add
+// the uses of a wall row's phi and psi by the wall row itself.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -39,12 +43,15 @@ namespace {
 
 constexpr int kAdThreads = 256;
 constexpr int kAdBlocks = 152 * 8;
-constexpr int kNParam = 5;  // beta4, kappa, lambda, tau_g (via s3,s5), tau_f (via s7,s8)
+// raw partials: beta4, kappa, lambda, tau_g (via s3,s5), tau_f (via s7,s8),
+// u_wall_top, u_wall_bottom
+constexpr int kNParam = 7;
 
 __device__ __constant__ int kAX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __device__ __constant__ int kAY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 __device__ __constant__ double kAW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                                          1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+__device__ __constant__ int kAOPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 
 int fail(int code, const std::string& m) { return lbmk::set_last_error(code, m.c_str()); }
 
@@ -54,6 +61,58 @@ __device__ __forceinline__ int64_t shift(int x, int y, int dx, int dy, int nx, i
   x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
   y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
   return (int64_t)y * nx + x;
+}
+
+// Buffer position of the value population i delivers to node (x, y): the
+// pull source, or with walls the node's own opposite population for a
+// population that would come from beyond a wall (halfway bounce-back).
+__device__ __forceinline__ int64_t ad_src(int i, int x, int y, int nx, int ny, int walls,
+                                          int* pl) {
+  const int ys = y - kAY[i];
+  if (walls && (ys < 0 || ys >= ny)) {
+    *pl = kAOPP[i];
+    return (int64_t)y * nx + x;
+  }
+  *pl = i;
+  return shift(x, y, -kAX[i], -kAY[i], nx, ny);
+}
+
+// Stencil neighbour (x + dx, y + dy): periodic, or with walls the mirrored
+// ghost row beyond a wall row.
+__device__ __forceinline__ int64_t ad_nb(int x, int y, int dx, int dy, int nx, int ny,
+                                         int walls) {
+  if (!walls) return shift(x, y, dx, dy, nx, ny);
+  x += dx;
+  x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+  y += dy;
+  y = y < 0 ? 0 : (y >= ny ? ny - 1 : y);
+  return (int64_t)y * nx + x;
+}
+
+// Adjoint of phi (lP, [9][n]) and psi (lQ, [8][n]) stencil uses gathered at
+// node (x, y): the nodes s whose stencil entry j reads this node.  Without
+// walls s = (x, y) - c_j; with walls also the wall row's own uses of its
+// mirrored ghost row.
+__device__ __forceinline__ void gather_uses(const double* __restrict__ lP,
+                                            const double* __restrict__ lQ, int x, int y,
+                                            int nx, int ny, int walls, double& sp, double& sq) {
+  const int64_t n = (int64_t)nx * ny;
+  for (int j = 1; j < 9; ++j) {
+    const int ys = y - kAY[j];
+    if (!walls || (ys >= 0 && ys < ny)) {
+      const int64_t s = shift(x, y, -kAX[j], -kAY[j], nx, ny);
+      sp += lP[j * n + s];
+      if (lQ) sq += lQ[(j - 1) * n + s];
+    }
+    // a wall row reads its own row through the ghost row beyond the wall
+    if (walls && ((y == 0 && kAY[j] == -1) || (y == ny - 1 && kAY[j] == 1))) {
+      int xs = x - kAX[j];
+      xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+      const int64_t s = (int64_t)y * nx + xs;
+      sp += lP[j * n + s];
+      if (lQ) sq += lQ[(j - 1) * n + s];
+    }
+  }
 }
 
 struct AdArgs {
@@ -74,17 +133,23 @@ struct AdArgs {
   int var_tau, coupled;
   double ct;    // vortex: U cos(pi t / T)
   double invW;  // 1/W: d(lambda/W)/d(lambda)
+  int walls;
+  double u_top, u_bot;
 };
 
 // phi (Eq. 35, pulled sum in the forward order) and psi = ln(a/b) (Eq. 37).
-__global__ void ad_phase(const double* __restrict__ gA, int64_t P, int nx, int ny, double xi,
-                         double* __restrict__ phi, double* __restrict__ psi) {
+__global__ void ad_phase(const double* __restrict__ gA, int64_t P, int nx, int ny, int walls,
+                         double xi, double* __restrict__ phi, double* __restrict__ psi) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     double G[9];
-    for (int i = 0; i < 9; ++i) G[i] = gA[i * P + shift(x, y, -kAX[i], -kAY[i], nx, ny)];
+    for (int i = 0; i < 9; ++i) {
+      int pl;
+      const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
+      G[i] = gA[pl * P + pos];
+    }
     const double p = lbmk::sum9(G);
     phi[k] = p;
     psi[k] = lbmk::psi_of(p, xi);
@@ -96,23 +161,37 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
   const int nx = a.nx, ny = a.ny;
   const int64_t n = (int64_t)nx * ny, P = a.P;
   const Phys<double>& ph = a.ph;
-  double gacc[kNParam] = {0, 0, 0, 0, 0};
+  double gacc[kNParam] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     int64_t src[9];
+    int spl[9];
     double F[9], G[9];
     for (int i = 0; i < 9; ++i) {
-      src[i] = shift(x, y, -kAX[i], -kAY[i], nx, ny);
-      G[i] = a.gA[i * P + src[i]];
-      F[i] = a.coupled ? a.fA[i * P + src[i]] : 0.0;
+      src[i] = ad_src(i, x, y, nx, ny, a.walls, &spl[i]);
+      G[i] = a.gA[spl[i] * P + src[i]];
+      F[i] = a.coupled ? a.fA[spl[i] * P + src[i]] : 0.0;
     }
     const double jpx = a.JA[k], jpy = a.JA[P + k];
     double Pv[9], Qv[9];
     for (int j = 0; j < 9; ++j) {
-      const int64_t s = shift(x, y, kAX[j], kAY[j], nx, ny);
+      const int64_t s = ad_nb(x, y, kAX[j], kAY[j], nx, ny, a.walls);
       Pv[j] = a.phi[s];
       Qv[j] = a.psi[s];
+    }
+    // moving-wall term of the bounced f (rho of this node)
+    const bool wbot = a.walls && y == 0, wtop = a.walls && y == ny - 1;
+    if (a.coupled && (wbot || wtop)) {
+      const double rw = a.rho_g + Pv[0] * a.drho;
+      if (wbot) {
+        F[5] += rw * a.u_bot / 6.0;
+        F[6] -= rw * a.u_bot / 6.0;
+      }
+      if (wtop) {
+        F[7] -= rw * a.u_top / 6.0;
+        F[8] += rw * a.u_top / 6.0;
+      }
     }
     // ---------------- forward recompute (as node_update) ----------------
     const double phi = Pv[0];
@@ -333,6 +412,17 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
       lirho += (mf.m5 + 0.5 * Fy) * luy;
       // m = M F
       lbmk::add_back(lF, lm[0], lm[1], lm[2], lm[3], lm[4], lm[5], lm[6], lm[7], lm[8]);
+      // moving-wall term: F_i += rho c_ix u_w / 6, rho = rho_g + phi drho
+      if (wbot) {
+        const double l = (lF[5] - lF[6]) / 6.0;
+        lrho += a.u_bot * l;
+        gacc[6] += rho * l;
+      }
+      if (wtop) {
+        const double l = (lF[8] - lF[7]) / 6.0;
+        lrho += a.u_top * l;
+        gacc[5] += rho * l;
+      }
       // irho = 1/rho, rho = rho_g + phi drho
       lrho += -irho * irho * lirho;
       lphi += a.drho * lrho;
@@ -368,10 +458,11 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
     a.lQ[6 * n + k] = -lqx - lqy;  // Q7
     a.lQ[7 * n + k] = lqx - lqy;   // Q8
 
-    // transpose of the pull: adjoint of the source positions
+    // transpose of the pull: adjoint of the source positions (a bijection,
+    // walls included)
     for (int i = 0; i < 9; ++i) {
-      a.aout[i * n + src[i]] = lF[i];
-      a.aout[(9 + i) * n + src[i]] = lG[i];
+      a.aout[spl[i] * n + src[i]] = lF[i];
+      a.aout[(9 + spl[i]) * n + src[i]] = lG[i];
     }
     a.aout[18 * n + k] = ljpx;
     a.aout[19 * n + k] = ljpy;
@@ -394,23 +485,23 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
 // Sum the stencil adjoints referring to each node's phi and psi and add them
 // to the adjoints of the node's 9 pulled g (phi = sum g).
 __global__ void ad_gather(const double* __restrict__ phi, const double* __restrict__ lP,
-                          const double* __restrict__ lQ, int nx, int ny, double xi,
+                          const double* __restrict__ lQ, int nx, int ny, int walls, double xi,
                           double* __restrict__ aout) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     double sp = lP[k], sq = 0.0;
-    for (int j = 1; j < 9; ++j) {
-      const int64_t s = shift(x, y, -kAX[j], -kAY[j], nx, ny);  // node using phi(k) as P_j
-      sp += lP[j * n + s];
-      sq += lQ[(j - 1) * n + s];
-    }
+    gather_uses(lP, lQ, x, y, nx, ny, walls, sp, sq);
     const double p = phi[k];
     double dpsi = 0.0;  // d ln(a/b) / d phi inside the clip
     if (p > 0.0 && p < 1.0) dpsi = 1.0 / (p + xi) + 1.0 / ((1.0 - p) + xi);
     const double tot = sp + dpsi * sq;
-    for (int i = 0; i < 9; ++i) aout[(9 + i) * n + shift(x, y, -kAX[i], -kAY[i], nx, ny)] += tot;
+    for (int i = 0; i < 9; ++i) {
+      int pl;
+      const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
+      aout[(9 + pl) * n + pos] += tot;
+    }
   }
 }
 
@@ -428,6 +519,8 @@ struct AdInitArgs {
   double rho_g, drho;
   int coupled, vortex;
   double vU;
+  int walls;
+  double u_top, u_bot;
 };
 
 __global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs a) {
@@ -435,14 +528,14 @@ __global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs a) 
   const int nx = a.nx, ny = a.ny;
   const int64_t n = (int64_t)nx * ny;
   const Phys<double>& ph = a.ph;
-  double gacc[kNParam] = {0, 0, 0, 0, 0};
+  double gacc[kNParam] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     const double p = a.phi0[k];
     double s_ax = 0.0, s_dg = 0.0;
     for (int j = 1; j < 9; ++j) {
-      const double v = a.phi0[shift(x, y, kAX[j], kAY[j], nx, ny)];
+      const double v = a.phi0[ad_nb(x, y, kAX[j], kAY[j], nx, ny, a.walls)];
       if (j < 5) s_ax += v; else s_dg += v;
     }
     const double lap = (2.0 / 3.0) * (s_ax - 4.0 * p) + (1.0 / 6.0) * (s_dg - 4.0 * p);
@@ -460,9 +553,11 @@ __global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs a) 
     }
     double lLam = 0.0, lphi = 0.0, lJx = a.ain[18 * n + k], lJy = a.ain[19 * n + k], lrho = 0.0;
     const double u2 = ux * ux + uy * uy;
+    const double rho = a.rho_g + p * a.drho;
     for (int i = 0; i < 9; ++i) {
-      const int64_t s = shift(x, y, -kAX[i], -kAY[i], nx, ny);
-      const double lg = a.ain[(9 + i) * n + s];
+      int pl;
+      const int64_t s = ad_src(i, x, y, nx, ny, a.walls, &pl);
+      const double lg = a.ain[(9 + pl) * n + s];
       if (i == 0) {
         lphi += lg;
         lLam += (kAW[0] - 1.0) * lg;
@@ -473,7 +568,16 @@ __global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs a) 
       }
       if (a.coupled) {
         const double cu = kAX[i] * ux + kAY[i] * uy;
-        lrho += kAW[i] * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2) * a.ain[i * n + s];
+        const double lf = a.ain[pl * n + s];
+        lrho += kAW[i] * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2) * lf;
+        // the stored f of a population entering from a wall is f_eq minus the
+        // moving-wall term rho c_ix u_w / 6 (added back when it is pulled)
+        if (a.walls && ((y == 0 && kAY[i] == 1) || (y == ny - 1 && kAY[i] == -1))) {
+          const bool bot = y == 0 && kAY[i] == 1;
+          const double uw = bot ? a.u_bot : a.u_top;
+          lrho += -kAX[i] * uw / 6.0 * lf;
+          gacc[bot ? 6 : 5] += -rho * kAX[i] / 6.0 * lf;
+        }
       }
     }
     lphi += ux * lJx + uy * lJy + a.drho * lrho;
@@ -500,35 +604,43 @@ __global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs a) 
   }
 }
 
-// lambda_phi0(y) = local + sum_j w_lap_j * llap(y - c_j) - (10/3) llap(y)
+// lambda_phi0(y) = local - (10/3) llap(y) + sum over the nodes s whose
+// Laplacian entry j reads y of w_lap_j * llap(s) (walls: mirrored ghost rows)
 __global__ void ad_init_gather(const double* __restrict__ lphi, const double* __restrict__ llap,
-                               int nx, int ny, double* __restrict__ out) {
+                               int nx, int ny, int walls, double* __restrict__ out) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     double v = lphi[k] - (10.0 / 3.0) * llap[k];
-    for (int j = 1; j < 9; ++j)
-      v += (j < 5 ? 2.0 / 3.0 : 1.0 / 6.0) * llap[shift(x, y, -kAX[j], -kAY[j], nx, ny)];
+    for (int j = 1; j < 9; ++j) {
+      const double w = j < 5 ? 2.0 / 3.0 : 1.0 / 6.0;
+      const int ys = y - kAY[j];
+      if (!walls || (ys >= 0 && ys < ny)) v += w * llap[shift(x, y, -kAX[j], -kAY[j], nx, ny)];
+      if (walls && ((y == 0 && kAY[j] == -1) || (y == ny - 1 && kAY[j] == 1))) {
+        int xs = x - kAX[j];
+        xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+        v += w * llap[(int64_t)y * nx + xs];
+      }
+    }
     out[k] = v;
   }
 }
 
-// The adjoint of phi = sum of pulled g, seeded from a field adjoint.
-__global__ void ad_seed_phi(const double* __restrict__ dphi, int nx, int ny,
+// The adjoint of phi = sum of pulled g, seeded from a field adjoint: every
+// node scatters dphi to the positions of its 9 pulled g (the f and phi*u
+// planes are cleared beforehand).
+__global__ void ad_seed_phi(const double* __restrict__ dphi, int nx, int ny, int walls,
                             double* __restrict__ aout) {
   const int64_t n = (int64_t)nx * ny;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < 20 * n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t plane = k / n, node = k % n;
-    double v = 0.0;
-    if (plane >= 9 && plane < 18) {
-      // position node of plane i holds the value delivered to node + c_i
-      const int i = (int)plane - 9;
-      const int x = (int)(node % nx), y = (int)(node / nx);
-      v = dphi[shift(x, y, kAX[i], kAY[i], nx, ny)];
+    const int x = (int)(k % nx), y = (int)(k / nx);
+    for (int i = 0; i < 9; ++i) {
+      int pl;
+      const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
+      aout[(9 + pl) * n + pos] = dphi[k];
     }
-    aout[k] = v;
   }
 }
 
@@ -566,18 +678,19 @@ int check_handle(lbm_handle* h, bool need_ws) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (h->ncases != 1) return fail(LBM_ERR_ARG, "reverse mode needs a single-case handle");
   if (h->precision != LBM_F64) return fail(LBM_ERR_ARG, "reverse mode needs an FP64 handle");
-  if (h->params[0].walls)
-    return fail(LBM_ERR_UNIMPLEMENTED, "reverse mode of the wall boundaries is not built");
   if (need_ws && !h->adj_ws) return fail(LBM_ERR_WORKSPACE, "call lbm_adjoint_attach first");
   return LBM_OK;
 }
 
-// Combine the raw partial sums into d/d(sigma, tau_g, lambda, tau_f).
+// Combine the raw partial sums into
+// d/d(sigma, tau_g, lambda, tau_f, u_wall_top, u_wall_bottom).
 void to_param_grads(const lbm_params& p, const double raw[kNParam], double* out) {
   out[0] += raw[0] * (48.0 / p.W) + raw[1] * (1.5 * p.W);  // beta4 = 48 sigma/W, kappa = 1.5 sigma W
   out[1] += raw[3];
   out[2] += raw[2];
   out[3] += raw[4];
+  out[4] += raw[5];
+  out[5] += raw[6];
 }
 
 // Reads and clears the device accumulator, adding d/d(sigma, tau_g, lambda,
@@ -627,8 +740,11 @@ int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, double* d_adj_stat
   if (rc) return rc;
   if (!d_dphi || !d_adj_state) return fail(LBM_ERR_ARG, "null pointer");
   const lbm_params& p = h->params[0];
-  ad_seed_phi<<<kAdBlocks, kAdThreads, 0, h->stream>>>(d_dphi, p.nx, p.ny, d_adj_state);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaMemsetAsync(d_adj_state, 0, 20 * sizeof(double) * p.nx * (size_t)p.ny,
+                                  h->stream);
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  ad_seed_phi<<<kAdBlocks, kAdThreads, 0, h->stream>>>(d_dphi, p.nx, p.ny, p.walls, d_adj_state);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   return LBM_OK;
 }
@@ -642,8 +758,8 @@ int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, doubl
   const CaseDev<double>& cd = h->cd[0];
   const bool coupled = h->flow == LBM_FLOW_COUPLED;
   AdScratch s = carve(h);
-  ad_phase<<<kAdBlocks, kAdThreads, 0, h->stream>>>(cd.g[h->parity], cd.plane, p.nx, p.ny, p.xi,
-                                                    s.phi, s.psi);
+  ad_phase<<<kAdBlocks, kAdThreads, 0, h->stream>>>(cd.g[h->parity], cd.plane, p.nx, p.ny,
+                                                    p.walls, p.xi, s.phi, s.psi);
   AdArgs a{};
   a.fA = coupled ? cd.f[h->parity] : nullptr;
   a.gA = cd.g[h->parity];
@@ -670,13 +786,16 @@ int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, doubl
   a.coupled = coupled ? 1 : 0;
   a.ct = coupled ? 0.0 : cospi((double)h->t / p.vortex_T) * p.vortex_U;
   a.invW = 1.0 / p.W;
+  a.walls = p.walls;
+  a.u_top = p.walls ? p.u_wall_top : 0.0;
+  a.u_bot = p.walls ? p.u_wall_bottom : 0.0;
   if (!coupled) {  // the f planes and the tau_f entry stay zero
     cudaError_t e = cudaMemsetAsync(d_adj_out, 0, 9 * sizeof(double) * p.nx * (size_t)p.ny, h->stream);
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   }
   ad_node<<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
-  ad_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.lP, s.lQ, p.nx, p.ny, p.xi,
-                                                     (double*)d_adj_out);
+  ad_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.lP, s.lQ, p.nx, p.ny, p.walls,
+                                                     p.xi, (double*)d_adj_out);
   ad_sum_partials<<<1, 32, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
@@ -707,8 +826,12 @@ int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
   a.coupled = h->flow == LBM_FLOW_COUPLED;
   a.vortex = h->flow == LBM_FLOW_VORTEX;
   a.vU = p.vortex_U;
+  a.walls = p.walls;
+  a.u_top = p.walls ? p.u_wall_top : 0.0;
+  a.u_bot = p.walls ? p.u_wall_bottom : 0.0;
   ad_init_local<<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
-  ad_init_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.psi, p.nx, p.ny, d_adj_phi0);
+  ad_init_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.psi, p.nx, p.ny, p.walls,
+                                                          d_adj_phi0);
   ad_sum_partials<<<1, 32, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));

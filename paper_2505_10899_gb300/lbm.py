@@ -319,7 +319,8 @@ def lbm_adjoint_seed_phi(h, d_dphi: int, d_adj: int):
 
 
 def lbm_adjoint_step(h, d_in: int, d_out: int, grads=None):
-    """Returns the status; adds d/d(sigma, tau_g, lambda, tau_f) into grads (numpy[4])."""
+    """Returns the status; adds d/d(sigma, tau_g, lambda, tau_f, u_wall_top,
+    u_wall_bottom) into grads (numpy[6])."""
     gp = _dp(grads) if grads is not None else None
     return int(_lib.lbm_adjoint_step(h, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), gp))
 

@@ -64,8 +64,9 @@ def test_adjoint_step_matches_fd(L, flow):
     delta = _rand((20, ny, nx), 12)
     if flow != "coupled":
         delta[:9] = 0
-    grads = np.zeros(4)
+    grads = np.zeros(6)
     lam_in = base.vjp_step(lam_out, grads)
+    assert grads[4] == 0.0 and grads[5] == 0.0  # no walls
     eps = 1e-6
     Sp = _one_step_out(A, case, S + eps * delta, 5)
     Sm = _one_step_out(A, case, S - eps * delta, 5)

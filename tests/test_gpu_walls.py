@@ -133,3 +133,104 @@ def test_fp32_walls_volume_drift_1e4_steps(L):
     s.step(10000)
     assert s.status() == L.LBM_OK
     assert abs(s.volume()[0] / v0 - 1) <= 1e-6
+
+
+# ---------------------------------------------------------------- reverse mode
+
+def _ad_modules():
+    from paper_2505_10899_gb300 import adjoint
+    return adjoint
+
+
+def _one_step_out(A, case, state, t):
+    s = A.AdjointSim(case, np.full((case["ny"], case["nx"]), 0.5))
+    s.restore(state, t)
+    s.step(1)
+    out = s.snapshot()
+    s.close()
+    return out
+
+
+def test_adjoint_step_with_walls_matches_fd(L):
+    # one step: <lambda_t, delta> against central differences of the GPU
+    # forward step, for the state and all six parameters (incl. wall speeds)
+    import torch
+    A = _ad_modules()
+    nx, ny = 36, 20
+    case = W.base_case(nx, ny, walls=1, u_top=0.02, u_bot=-0.01, sigma=5e-3, rho_l=4.0,
+                       tau_f_l=0.9, tau_f_g=0.9)
+    f, g, j = W.random_state(nx, ny, seed=17, coupled=True, phi_lo=0.1, phi_hi=0.9)
+    base = A.AdjointSim(case, np.full((ny, nx), 0.5))
+    base.sim.set_state(0, f, g, j, 5)
+    S = base.snapshot()
+    lam_out = torch.as_tensor(W.uniform(11, (20, ny, nx), -1, 1), device="cuda")
+    delta = torch.as_tensor(W.uniform(12, (20, ny, nx), -1, 1), device="cuda")
+    grads = np.zeros(6)
+    lam_in = base.vjp_step(lam_out, grads)
+    eps = 1e-6
+    fd = float(((_one_step_out(A, case, S + eps * delta, 5)
+                 - _one_step_out(A, case, S - eps * delta, 5)) * lam_out).sum()) / (2 * eps)
+    ad = float((lam_in * delta).sum())
+    assert abs(ad - fd) <= 1e-6 * abs(fd) + 1e-9, (ad, fd)
+    th0 = np.array([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"],
+                    case["u_top"], case["u_bot"]])
+    for q, h in enumerate([1e-7, 1e-6, 1e-6, 1e-6, 1e-6, 1e-6]):
+        outs = []
+        for sgn in (+1, -1):
+            th = th0.copy()
+            th[q] += sgn * h
+            outs.append(_one_step_out(A, A.case_with(case, th), S, 5))
+        fdq = float(((outs[0] - outs[1]) * lam_out).sum()) / (2 * h)
+        assert abs(grads[q] - fdq) <= 1e-5 * abs(fdq) + 1e-7, (q, grads[q], fdq)
+    assert abs(grads[4]) > 0 and abs(grads[5]) > 0
+    base.close()
+
+
+def _np_taylor_D(phi):
+    ny, nx = phi.shape
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    m = phi.sum()
+    cx, cy = (phi * x).sum() / m, (phi * y).sum() / m
+    dx, dy = x - cx, y - cy
+    I = np.array([[(phi * dx * dx).sum(), (phi * dx * dy).sum()],
+                  [(phi * dx * dy).sum(), (phi * dy * dy).sum()]]) / m
+    ev = np.linalg.eigvalsh(I)
+    return (np.sqrt(ev[1]) - np.sqrt(ev[0])) / (np.sqrt(ev[1]) + np.sqrt(ev[0]))
+
+
+def test_taylor_deformation_gradient_vs_oracle_fd(L):
+    # J = D(phi_T) of a sheared droplet: gradients through the checkpointed
+    # reverse mode against central differences of J from the FP64 oracle
+    import torch
+    A = _ad_modules()
+    case, phi0, u0 = W.shear_droplet(nx=48, ny=32, R=6.0, U=0.01, Ca=0.2, Re=0.5)
+    T = 160
+    th0 = np.array([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"],
+                    case["u_top"], case["u_bot"]])
+    phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
+    th_t = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    phiT = A.coupled_run(phi0_t, th_t, case, T, ckpt_every=32, u0=u0)
+    J = A.taylor_deformation(phiT)
+    J.backward()
+    g = th_t.grad.numpy()
+
+    def oJ(th, p0=phi0):
+        o = oracle.Oracle(A.case_with(case, th), p0, u0).step(T)
+        phi = o.fields()[0]
+        # the clip of Eq. 37 is touched only by round-off-size excursions
+        assert phi.min() > -1e-9 and phi.max() < 1
+        return _np_taylor_D(phi)
+
+    assert abs(float(J.detach()) - oJ(th0)) < 1e-10 * abs(float(J.detach()))
+    assert float(J.detach()) > 0.01  # the droplet has deformed
+    for q, h in [(0, 1e-6), (1, 1e-5), (4, 1e-6), (5, 1e-6)]:
+        tp, tm = th0.copy(), th0.copy()
+        tp[q] += h
+        tm[q] -= h
+        fd = (oJ(tp) - oJ(tm)) / (2 * h)
+        assert abs(g[q] - fd) <= 2e-5 * abs(fd) + 1e-9, (q, g[q], fd)
+    d = W.uniform(9, phi0.shape, -1.0, 1.0) * phi0 * (1 - phi0)
+    h = 1e-6
+    fd = (oJ(th0, phi0 + h * d) - oJ(th0, phi0 - h * d)) / (2 * h)
+    ad = float((phi0_t.grad.numpy() * d).sum())
+    assert abs(ad - fd) <= 2e-5 * abs(fd) + 1e-9, (ad, fd)
