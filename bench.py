@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--steps3", type=int, default=50, help="timed 3-D steps (FP64: a fifth)")
     ap.add_argument("--tiling3", type=str, default=None,
                     help="VARIANT,BX,BY,ZC for the 3-D step (default: autotuned)")
+    ap.add_argument("--only-shear", action="store_true",
+                    help="only the sheared-droplet numbers (walls, FP32/FP64, D gradient)")
     ap.add_argument("--only-adjoint", action="store_true",
                     help="print the reverse-mode timing only (profiling aid)")
     return ap.parse_args()
@@ -419,6 +421,7 @@ def run_extras(args, cases, dev):
     out["single_vortex"] = vort
     out["adjoint"] = adjoint_timing(dev)
     out["rayleigh_plateau_3d"] = rp3d_timing(dev, steps=args.steps3)
+    out["shear_droplet"] = shear_timing(dev)
     return out
 
 
@@ -550,6 +553,62 @@ def adjoint_timing(dev, nx=512, ny=256, nsteps=32, ckpt=8):
             "checkpoint_every": ckpt}
 
 
+def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
+    """The sheared droplet of configs[3] (512 x 256 channel, walls at -U and
+    +U = 0.01, R = 40, W = 4, Ca = 0.1, Re = 0.1): FP32 forward MLUPS over
+    nsteps (register-pipelined kernel with walls), the Taylor deformation D
+    after nsteps in FP32 and FP64, and the checkpointed FP64 reverse mode of
+    D(phi_T) with respect to (sigma, tau_g, U_w) with its cost relative to
+    the forward run (U_w moves both walls: dD/dU_w = dD/du_top - dD/du_bot)."""
+    import torch
+    from paper_2505_10899_gb300 import adjoint as A
+    from paper_2505_10899_gb300 import lbm
+
+    case, phi0, u0 = W.shear_droplet(512, 256, R=40.0, U=0.01, Ca=0.1, Re=0.1)
+    out = {"grid": "512x256", "walls_u": 0.01, "R": 40.0, "Ca": 0.1, "Re": 0.1, "W": 4.0,
+           "steps": nsteps}
+    for prec in ("f32", "f64"):
+        s = lbm.Sim(case, phi0, u0, precision=prec)
+        s.step(3)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s.stream)
+        s.step(nsteps - 3)
+        b.record(s.stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b) / (nsteps - 3)
+        phi = torch.as_tensor(s.fields(0)[0])
+        out[prec] = {"mlups": round(512 * 256 / (ms * 1e-3) / 1e6, 1),
+                     "kernel": {1: "step_kernel", 3: "step_kernel_persistent"}.get(s.kernel(),
+                                                                                    "?"),
+                     "taylor_D": float(A.taylor_deformation(phi)),
+                     "status": s.status()}
+        s.close()
+    # checkpointed reverse mode of D(phi_T)
+    th = torch.tensor([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"],
+                       case["u_top"], case["u_bot"]], dtype=torch.float64, requires_grad=True)
+    phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    phiT = A.coupled_run(phi0_t, th, case, grad_steps, ckpt, u0=u0)
+    D = A.taylor_deformation(phiT)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    D.backward()
+    torch.cuda.synchronize(dev)
+    t2 = time.perf_counter()
+    g = th.grad.numpy()
+    out["gradient_f64"] = {"steps": grad_steps, "checkpoint_every": ckpt,
+                           "D": float(D.detach()),
+                           "dD_dsigma": float(g[0]), "dD_dtau_g": float(g[1]),
+                           "dD_dU_w": float(g[4] - g[5]),
+                           "forward_s": round(t1 - t0, 3), "backward_s": round(t2 - t1, 3),
+                           "backward_over_forward": round((t2 - t1) / (t1 - t0), 3),
+                           "plain_f64_forward_s": round(grad_steps * 512 * 256
+                                                        / (out["f64"]["mlups"] * 1e6), 3)}
+    return out
+
+
 def cpu_baseline(cases, seconds):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of
     the same workload: the first cases of the batch, 2 steps each."""
@@ -626,6 +685,10 @@ def main():
     if args.only_adjoint:
         import torch
         print(json.dumps({"adjoint": adjoint_timing(torch.device("cuda", 0))}), flush=True)
+        return
+    if args.only_shear:
+        import torch
+        print(json.dumps({"shear_droplet": shear_timing(torch.device("cuda", 0))}), flush=True)
         return
     if args.only_3d:
         import torch

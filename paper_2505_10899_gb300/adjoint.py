@@ -104,9 +104,12 @@ class CoupledRun(torch.autograd.Function):
         th = theta.detach().cpu().numpy().astype(np.float64)
         asim = AdjointSim(case_with(case, th), phi0.detach().cpu().numpy(), u0)
         ckpts = {0: asim.snapshot()}
-        for t in range(1, nsteps + 1):
-            asim.step(1)
-            if t % ckpt_every == 0 and t < nsteps:
+        t = 0
+        while t < nsteps:  # whole segments: the library replays CUDA graphs
+            n = min(ckpt_every, nsteps - t)
+            asim.step(n)
+            t += n
+            if t < nsteps:
                 ckpts[t] = asim.snapshot()
         phiT = asim.phi()
         ctx.asim, ctx.ckpts, ctx.nsteps, ctx.k = asim, ckpts, nsteps, ckpt_every
