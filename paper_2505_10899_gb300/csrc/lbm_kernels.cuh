@@ -170,9 +170,14 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
     const bool bt = at_bot(rr), tp = at_top(rr);
-    pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, bt, tp, R.G);
+    if (bt || tp) {  // a wall row (uniform over the CTA)
+      pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, bt, tp, R.G);
+      if (COUPLED) pull9w<COHERENT>(fs, P, o0, om, op, xc, xm, xp, bt, tp, R.F);
+    } else {
+      pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G);
+      if (COUPLED) pull9<COHERENT>(fs, P, o0, om, op, xc, xm, xp, R.F);
+    }
     R.lo = LO ? ld<COHERENT>(los + (o0 + xc)) : T(0);
-    if (COUPLED) pull9w<COHERENT>(fs, P, o0, om, op, xc, xm, xp, bt, tp, R.F);
     if (MODE == kModeStep) {  // phi*u of the previous step at the own node
       R.J[0] = ld<COHERENT>(Js + (o0 + xc));
       R.J[1] = ld<COHERENT>(Js + (P + o0 + xc));
@@ -182,13 +187,19 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
     const int rr = wrap(r);
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
-    pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, at_bot(rr), at_top(rr), R.G);
+    if (at_bot(rr) || at_top(rr))
+      pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, at_bot(rr), at_top(rr), R.G);
+    else
+      pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G);
   };
   auto fetch_halo = [&](int r, T H[9]) {
     const int rr = wrap(r);
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
-    pull9w<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, at_bot(rr), at_top(rr), H);
+    if (at_bot(rr) || at_top(rr))
+      pull9w<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, at_bot(rr), at_top(rr), H);
+    else
+      pull9<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, H);
   };
   // write phi/psi of local row k (k >= -1) into the ring.  phi is the plain
   // sum of the nine pulled values (FP32: the low part of g_0 enters only the
