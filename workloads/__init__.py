@@ -247,3 +247,44 @@ def shear_droplet(nx=512, ny=256, R=40.0, U=0.01, Ca=0.1, Re=0.1, W=4.0, tau_g=0
     u0 = np.zeros((2, ny, nx))
     u0[0] = -U + 2.0 * U * (np.arange(ny, dtype=np.float64)[:, None] + 0.5) / ny
     return case, phi0, u0
+
+
+def coarse_sheared_droplet(lam=0.5, U=0.01, Ca=0.1, Re=0.1, W=4.0, tau_g=0.8):
+    """The sheared droplet of Sec. 4.4 on the grid given there: a 128 x 64
+    cavity between walls moving at -U (below) and +U (above), one droplet of
+    radius 8 (Eq. 46) at the cavity centre, fluid on the Couette profile.  The
+    wall speed, Ca, Re, W and tau_g are not given with the experiment; these
+    defaults are the values chosen for it.  Returns (case, phi0, u0)."""
+    return shear_droplet(nx=128, ny=64, R=8.0, U=U, Ca=Ca, Re=Re, W=W, tau_g=tau_g, lam=lam)
+
+
+def film_eq45(nx=256, ny=128, a=0.15, amp=0.05, W=4.0, sigma=1e-3, tau_f=0.6, lam=0.5):
+    """Eq. 45 on the two-dimensional grid as printed: the domain
+    (0, 2 pi) x (0, pi) on nx x ny nodes (spacing pi / ny), a liquid layer of
+    height a + amp cos(x) (in the domain's units) on a resting wall below
+    y = 0, a resting wall above y = pi, fluid at rest.  Node (i, j) sits at
+    x = i h, y = (j + 1/2) h, the walls half a node outside the end rows; W is
+    in lattice units.  Returns (case, phi0)."""
+    h = np.pi / ny
+    x = np.arange(nx, dtype=np.float64)[None, :] * (2.0 * np.pi / nx)
+    y = (np.arange(ny, dtype=np.float64)[:, None] + 0.5) * h
+    phi0 = 0.5 * (1.0 + np.tanh(2.0 * (a - y + amp * np.cos(x)) / (W * h)))
+    case = base_case(nx, ny, W=W, sigma=sigma, tau_f_l=tau_f, tau_f_g=tau_f, walls=1,
+                     u_top=0.0, u_bot=0.0, **{"lambda": lam})
+    return case, phi0
+
+
+def column_eq45(n=256, a=0.15, amp=0.05, W=4.0, sigma=1e-3, tau_f=0.6, lam=0.5,
+                tau_g=0.8, rho_ratio=1.0, n_side=None):
+    """Eq. 45 read as a section through an axisymmetric liquid thread (y the
+    distance from the axis, x along it) and run as a three-dimensional column
+    on a periodic box: the axis along z over one period 2 pi (n nodes,
+    spacing h = 2 pi / n), radius a + amp cos(z) in those units, i.e. a / h
+    lattice units with a relative perturbation amp / a, fluid at rest.  The
+    transverse box has side 2 pi (n_side = n nodes: the radial extent pi on
+    each side of the axis) unless n_side says otherwise.  Returns (case, phi0)."""
+    h = 2.0 * np.pi / n
+    m = n if n_side is None else int(n_side)
+    case = base_case3(m, m, n, W=W, sigma=sigma, tau_g=tau_g, rho_l=rho_ratio, rho_g=1.0,
+                      tau_f_l=tau_f, tau_f_g=tau_f, **{"lambda": lam})
+    return case, liquid_column(m, m, n, a / h, W, eps=amp / a, wavelength=n)
