@@ -150,3 +150,39 @@ def column(case, phi0, times, precision="f32", autotune=True):
     finally:
         s.close()
     return rows
+
+
+def main(argv=None):
+    """Both set-ups for lambda = 0.5 (modified) and 0 (classical); one JSON
+    line on stdout.  --quick shortens the runs (a 96-node-wide column box,
+    fewer steps) for a smoke check."""
+    import argparse
+    import json
+    import sys
+
+    sys.path.insert(0, __import__("os").path.dirname(__import__("os").path.dirname(__file__)))
+    import workloads as W
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--quick", action="store_true")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    a = ap.parse_args(argv)
+    t_drop = [0, 5000, 10000, 20000, 40000, 80000, 160000, 240000, 320000, 400000]
+    t_film = [0, 50000, 100000, 200000]
+    t_col = list(range(0, 200001, 10000))
+    side = None
+    if a.quick:
+        t_drop, t_film, t_col, side = t_drop[:5], t_film[:2], t_col[:4], 96
+    res = {}
+    for lam in (0.5, 0.0):
+        c, p, u = W.coarse_sheared_droplet(lam=lam)
+        res[f"sheared_droplet_128x64_lambda{lam}"] = sheared_droplet(c, p, u, t_drop, a.precision)
+        c, p = W.film_eq45(lam=lam)
+        res[f"film_eq45_256x128_lambda{lam}"] = film(c, p, t_film, a.precision)
+        c, p = W.column_eq45(lam=lam, n_side=side)
+        res[f"column_eq45_{c['nx']}x{c['ny']}x{c['nz']}_lambda{lam}"] = column(c, p, t_col, a.precision)
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()
