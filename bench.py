@@ -529,28 +529,37 @@ def adjoint_timing(dev, nx=512, ny=256, nsteps=32, ckpt=8):
     vjp_ms = timed(one_vjp, 20)
     s.close()
 
-    # full backward through torch.autograd with checkpoint every `ckpt` steps
-    # (second run timed: the first one loads the kernels)
-    def fwd_bwd():
+    # full backward through torch.autograd: forward states recorded in device
+    # memory (the default), and checkpoints every `ckpt` steps with
+    # recomputation (store_bytes=0).  The second run of each is timed: the
+    # first one loads the kernels.
+    def fwd_bwd(store):
         phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
         theta = torch.tensor([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"]],
                              dtype=torch.float64, requires_grad=True)
-        phiT = A.coupled_run(phi0_t, theta, case, nsteps, ckpt)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
+        phiT = A.coupled_run(phi0_t, theta, case, nsteps, ckpt, store_bytes=store)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
         phiT.sum().backward()
         torch.cuda.synchronize(dev)
-        return (time.perf_counter() - t0) * 1e3 / nsteps
+        t2 = time.perf_counter()
+        return (t1 - t0) * 1e3 / nsteps, (t2 - t1) * 1e3 / nsteps
 
-    fwd_bwd()
-    bwd_ms = fwd_bwd()
-    return {"grid": f"{nx}x{ny}", "precision": "f64",
+    res = {}
+    for name, store in (("recorded", None), ("recomputed", 0)):
+        fwd_bwd(store)
+        f_ms, b_ms = fwd_bwd(store)
+        res[name] = {"forward_ms_per_step": round(f_ms, 4), "backward_ms_per_step": round(b_ms, 4),
+                     "backward_over_forward_step": round(b_ms / fwd_ms, 3)}
+    res["recomputed"]["checkpoint_every"] = ckpt
+    return {"grid": f"{nx}x{ny}", "precision": "f64", "steps": nsteps,
             "forward_ms_per_step": round(fwd_ms, 4),
             "vjp_ms_per_step": round(vjp_ms, 4),
             "vjp_over_forward": round(vjp_ms / fwd_ms, 3),
-            "checkpointed_backward_ms_per_step": round(bwd_ms, 4),
-            "checkpointed_backward_over_forward": round(bwd_ms / fwd_ms, 3),
-            "checkpoint_every": ckpt}
+            "backward_states_recorded": res["recorded"],
+            "backward_states_recomputed": res["recomputed"]}
 
 
 def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
@@ -590,7 +599,8 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
     phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    phiT = A.coupled_run(phi0_t, th, case, grad_steps, ckpt, u0=u0)
+    store = 64 << 30  # device memory for recorded states; the rest is recomputed
+    phiT = A.coupled_run(phi0_t, th, case, grad_steps, ckpt, u0=u0, store_bytes=store)
     D = A.taylor_deformation(phiT)
     torch.cuda.synchronize(dev)
     t1 = time.perf_counter()
@@ -599,11 +609,14 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
     t2 = time.perf_counter()
     g = th.grad.numpy()
     out["gradient_f64"] = {"steps": grad_steps, "checkpoint_every": ckpt,
+                           "recorded_steps": min(grad_steps, store // (20 * 8 * 512 * 256)),
                            "D": float(D.detach()),
                            "dD_dsigma": float(g[0]), "dD_dtau_g": float(g[1]),
                            "dD_dU_w": float(g[4] - g[5]),
                            "forward_s": round(t1 - t0, 3), "backward_s": round(t2 - t1, 3),
                            "backward_over_forward": round((t2 - t1) / (t1 - t0), 3),
+                           "backward_over_plain_forward": round(
+                               (t2 - t1) * out["f64"]["mlups"] * 1e6 / (grad_steps * 512 * 256), 3),
                            "plain_f64_forward_s": round(grad_steps * 512 * 256
                                                         / (out["f64"]["mlups"] * 1e6), 3)}
     return out

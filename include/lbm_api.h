@@ -263,6 +263,12 @@ int lbm_set_time(lbm_handle* h, int64_t t);
  *     moving-wall term, the mirrored ghost rows).  The state is not modified.
  *     At the clip of Eq. 37 and where |grad psi| = 0 the derivative of the
  *     branch taken is used.
+ *   lbm_adjoint_step_from: as lbm_adjoint_step, for the state S_t held in
+ *     d_state (an FP64 snapshot of the case, layout of lbm_snapshot) at step
+ *     index t instead of the handle's own state, which is neither read nor
+ *     modified.  A reverse sweep over recorded states then needs no
+ *     lbm_restore before each step.  d_adj_out must differ from d_adj_in and
+ *     d_state; d_state is caller-owned and read on the handle's stream.
  *   lbm_adjoint_init: adjoint of the initial-state map of lbm_init: given the
  *     adjoint of S_0, writes d_adj_phi0 [ny][nx] and accumulates the sigma and
  *     lambda derivatives (h_param_grads as for lbm_adjoint_step); d_phi0
@@ -277,6 +283,8 @@ int lbm_adjoint_attach(lbm_handle* h, void* d_scratch, size_t bytes);
 int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, double* d_adj_state);
 int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out,
                      double* h_param_grads);
+int lbm_adjoint_step_from(lbm_handle* h, const void* d_state, int64_t t,
+                          const void* d_adj_in, void* d_adj_out, double* h_param_grads);
 int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
                      const void* d_adj_state, double* d_adj_phi0,
                      double* h_param_grads);

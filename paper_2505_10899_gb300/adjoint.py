@@ -5,9 +5,14 @@ around the library's discrete adjoint (lbm_adjoint_step / lbm_adjoint_init).
 and returns phi at the final step as a CUDA tensor; it is differentiable with
 respect to the initial field phi0 and theta = (sigma, tau_g, lambda, tau_f) or,
 for a case with walls, (sigma, tau_g, lambda, tau_f, u_wall_top, u_wall_bottom).
-The backward pass restores a snapshot every ``ckpt_every`` steps, recomputes
-the states of that segment on the GPU, and runs the adjoint steps backwards.
-All arithmetic runs in the CUDA library; torch holds the device buffers.
+The forward pass records the states of the last steps in device memory, as
+many as ``store_bytes`` holds (by default a quarter of the free device
+memory), and a checkpoint every ``ckpt_every`` steps before them.  The
+backward pass runs the adjoint steps straight from the recorded states; below
+them it restores each checkpoint, recomputes the states of its segment and
+runs the segment backwards.  So a run that fits in memory is differentiated
+without recomputation.  All arithmetic runs in the CUDA library; torch holds
+the device buffers.
 """
 from __future__ import annotations
 
@@ -75,6 +80,18 @@ class AdjointSim:
             raise lbm.LbmError(rc, "lbm_adjoint_step", lbm.lib().lbm_last_error().decode())
         return adj_out
 
+    def vjp_step_from(self, state, t, adj_in, adj_out=None):
+        """Adjoint of S_t from the adjoint of S_{t+1}, for the snapshot
+        ``state`` of S_t (the handle's own state is not used).  Parameter
+        derivatives accumulate on the device."""
+        if adj_out is None:
+            adj_out = torch.empty((20,) + self.shape, dtype=torch.float64, device=self.dev)
+        rc = lbm.lbm_adjoint_step_from(self.h, state.data_ptr(), int(t), adj_in.data_ptr(),
+                                       adj_out.data_ptr(), None)
+        if rc != lbm.LBM_OK:
+            raise lbm.LbmError(rc, "lbm_adjoint_step_from", lbm.lib().lbm_last_error().decode())
+        return adj_out
+
     def take_grads(self, grads):
         lbm.lbm_adjoint_take_param_grads(self.h, grads)
 
@@ -98,21 +115,37 @@ def case_with(case, theta):
     return c
 
 
+def _stored_steps(nsteps, state_bytes, store_bytes, dev):
+    """How many of the last steps keep their state in device memory."""
+    if store_bytes is None:
+        free, _ = torch.cuda.mem_get_info(dev)
+        store_bytes = free // 4
+    return int(max(0, min(nsteps, int(store_bytes) // state_bytes)))
+
+
 class CoupledRun(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, phi0, theta, case, nsteps, ckpt_every, u0):
+    def forward(ctx, phi0, theta, case, nsteps, ckpt_every, u0, store_bytes):
         th = theta.detach().cpu().numpy().astype(np.float64)
         asim = AdjointSim(case_with(case, th), phi0.detach().cpu().numpy(), u0)
-        ckpts = {0: asim.snapshot()}
+        state_bytes = 20 * 8 * asim.shape[0] * asim.shape[1]
+        m = _stored_steps(nsteps, state_bytes, store_bytes, asim.dev)
+        t_rec = nsteps - m  # states S_t, t in [t_rec, nsteps), stay on the device
+        rec = torch.empty((m, 20) + asim.shape, dtype=torch.float64, device=asim.dev)
+        ckpts = {0: asim.snapshot()} if t_rec > 0 else {}
         t = 0
-        while t < nsteps:  # whole segments: the library replays CUDA graphs
-            n = min(ckpt_every, nsteps - t)
+        while t < t_rec:  # whole segments: the library replays CUDA graphs
+            n = min(ckpt_every, t_rec - t)
             asim.step(n)
             t += n
-            if t < nsteps:
+            if t < t_rec:
                 ckpts[t] = asim.snapshot()
+        for k in range(m):
+            asim.snapshot(rec[k])
+            asim.step(1)
         phiT = asim.phi()
-        ctx.asim, ctx.ckpts, ctx.nsteps, ctx.k = asim, ckpts, nsteps, ckpt_every
+        ctx.asim, ctx.ckpts, ctx.rec, ctx.t_rec = asim, ckpts, rec, t_rec
+        ctx.nsteps, ctx.k = nsteps, ckpt_every
         ctx.theta_dtype, ctx.theta_device = theta.dtype, theta.device
         ctx.ntheta = int(theta.numel())
         ctx.phi0_dtype, ctx.phi0_device = phi0.dtype, phi0.device
@@ -120,35 +153,41 @@ class CoupledRun(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_phiT):
-        asim, nsteps, k = ctx.asim, ctx.nsteps, ctx.k
+        asim, nsteps, k, t_rec, rec = ctx.asim, ctx.nsteps, ctx.k, ctx.t_rec, ctx.rec
         grads = np.zeros(6)
         adj = asim.seed_phi(grad_phiT)
         spare = torch.empty_like(adj)
-        seg = [torch.empty_like(adj) for _ in range(k - 1)]  # recomputed states
+        # recorded states: no recomputation
+        for t in reversed(range(t_rec, nsteps)):
+            adj, spare = asim.vjp_step_from(rec[t - t_rec], t, adj, spare), adj
+        ctx.rec = rec = None
+        # checkpointed segments below: recompute the states, then run backwards
+        seg = [torch.empty_like(adj) for _ in range(min(k, t_rec) - 1)]
         for t0 in reversed(sorted(ctx.ckpts)):
-            t1 = min(t0 + k, nsteps)
-            # recompute the states of the segment [t0, t1) from its checkpoint
+            t1 = min(t0 + k, t_rec)
             asim.restore(ctx.ckpts[t0], t0)
             states = {t0: ctx.ckpts[t0]}
             for t in range(t0 + 1, t1):
                 asim.step(1)
                 states[t] = asim.snapshot(seg[t - t0 - 1])
             for t in reversed(range(t0, t1)):
-                asim.restore(states[t], t)
-                adj, spare = asim.vjp_step(adj, None, spare), adj
-        asim.restore(ctx.ckpts[0], 0)
+                adj, spare = asim.vjp_step_from(states[t], t, adj, spare), adj
+        if 0 in ctx.ckpts:
+            asim.restore(ctx.ckpts[0], 0)
         dphi0 = asim.vjp_init(adj, None)
         asim.take_grads(grads)
         asim.close()
         gtheta = torch.as_tensor(grads[:ctx.ntheta], dtype=ctx.theta_dtype,
                                  device=ctx.theta_device)
         dphi0 = dphi0.to(device=ctx.phi0_device, dtype=ctx.phi0_dtype)
-        return dphi0, gtheta, None, None, None, None
+        return dphi0, gtheta, None, None, None, None, None
 
 
-def coupled_run(phi0, theta, case, nsteps, ckpt_every=16, u0=None):
-    """phi after nsteps coupled steps, differentiable in phi0 and theta."""
-    return CoupledRun.apply(phi0, theta, case, int(nsteps), int(ckpt_every), u0)
+def coupled_run(phi0, theta, case, nsteps, ckpt_every=16, u0=None, store_bytes=None):
+    """phi after nsteps coupled steps, differentiable in phi0 and theta.
+    store_bytes bounds the device memory for recorded states (None: a
+    quarter of the free memory; 0: checkpoints and recomputation only)."""
+    return CoupledRun.apply(phi0, theta, case, int(nsteps), int(ckpt_every), u0, store_bytes)
 
 
 def taylor_deformation(phi):

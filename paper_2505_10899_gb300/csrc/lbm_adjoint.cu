@@ -749,22 +749,26 @@ int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, double* d_adj_stat
   return LBM_OK;
 }
 
-int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, double* h_param_grads) {
-  int rc = check_handle(h, true);
-  if (rc) return rc;
-  if (!d_adj_in || !d_adj_out) return fail(LBM_ERR_ARG, "null adjoint buffer");
-  if (d_adj_in == d_adj_out) return fail(LBM_ERR_ARG, "d_adj_in and d_adj_out must differ");
+}  // extern "C"
+
+namespace {
+
+// One adjoint step from the state S_t held in (fA, gA, JA) with plane stride
+// P at step index t (the handle's own buffers, or a snapshot).
+int adjoint_step_impl(lbm_handle* h, const double* fA, const double* gA, const double* JA,
+                      int64_t P, int64_t t, const void* d_adj_in, void* d_adj_out,
+                      double* h_param_grads) {
   const lbm_params& p = h->params[0];
   const CaseDev<double>& cd = h->cd[0];
   const bool coupled = h->flow == LBM_FLOW_COUPLED;
   AdScratch s = carve(h);
-  ad_phase<<<kAdBlocks, kAdThreads, 0, h->stream>>>(cd.g[h->parity], cd.plane, p.nx, p.ny,
-                                                    p.walls, p.xi, s.phi, s.psi);
+  ad_phase<<<kAdBlocks, kAdThreads, 0, h->stream>>>(gA, P, p.nx, p.ny, p.walls, p.xi, s.phi,
+                                                    s.psi);
   AdArgs a{};
-  a.fA = coupled ? cd.f[h->parity] : nullptr;
-  a.gA = cd.g[h->parity];
-  a.JA = cd.J[h->parity];
-  a.P = cd.plane;
+  a.fA = coupled ? fA : nullptr;
+  a.gA = gA;
+  a.JA = JA;
+  a.P = P;
   a.nx = p.nx;
   a.ny = p.ny;
   a.phi = s.phi;
@@ -784,7 +788,7 @@ int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, doubl
   a.s7 = 1.0 / p.tau_f_l;
   a.var_tau = cd.var_tau;
   a.coupled = coupled ? 1 : 0;
-  a.ct = coupled ? 0.0 : cospi((double)h->t / p.vortex_T) * p.vortex_U;
+  a.ct = coupled ? 0.0 : cospi((double)t / p.vortex_T) * p.vortex_U;
   a.invW = 1.0 / p.W;
   a.walls = p.walls;
   a.u_top = p.walls ? p.u_wall_top : 0.0;
@@ -801,6 +805,34 @@ int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, doubl
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   if (h_param_grads) return take_grads(h, h_param_grads);
   return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, double* h_param_grads) {
+  int rc = check_handle(h, true);
+  if (rc) return rc;
+  if (!d_adj_in || !d_adj_out) return fail(LBM_ERR_ARG, "null adjoint buffer");
+  if (d_adj_in == d_adj_out) return fail(LBM_ERR_ARG, "d_adj_in and d_adj_out must differ");
+  const CaseDev<double>& cd = h->cd[0];
+  return adjoint_step_impl(h, cd.f[h->parity], cd.g[h->parity], cd.J[h->parity], cd.plane, h->t,
+                           d_adj_in, d_adj_out, h_param_grads);
+}
+
+int lbm_adjoint_step_from(lbm_handle* h, const void* d_state, int64_t t, const void* d_adj_in,
+                          void* d_adj_out, double* h_param_grads) {
+  int rc = check_handle(h, true);
+  if (rc) return rc;
+  if (!d_state || !d_adj_in || !d_adj_out) return fail(LBM_ERR_ARG, "null buffer");
+  if (t < 0) return fail(LBM_ERR_ARG, "t < 0");
+  if (d_adj_in == d_adj_out || d_state == d_adj_out)
+    return fail(LBM_ERR_ARG, "d_adj_out must differ from d_adj_in and d_state");
+  const int64_t n = (int64_t)h->params[0].nx * h->params[0].ny;
+  const double* st = (const double*)d_state;
+  return adjoint_step_impl(h, st, st + 9 * n, st + 18 * n, n, t, d_adj_in, d_adj_out,
+                           h_param_grads);
 }
 
 int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,

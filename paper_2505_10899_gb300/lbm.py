@@ -87,6 +87,7 @@ def _load():
         "lbm_load": ([_H, _VP, ctypes.c_size_t], ctypes.c_int),
         "lbm_status": ([_H], ctypes.c_int),
         "lbm_adjoint_step": ([_H, _VP, _VP, _D], ctypes.c_int),
+        "lbm_adjoint_step_from": ([_H, _VP, ctypes.c_int64, _VP, _VP, _D], ctypes.c_int),
         "lbm_adjoint_workspace_bytes": ([_H], ctypes.c_size_t),
         "lbm_adjoint_attach": ([_H, _VP, ctypes.c_size_t], ctypes.c_int),
         "lbm_adjoint_seed_phi": ([_H, _VP, _VP], ctypes.c_int),
@@ -323,6 +324,14 @@ def lbm_adjoint_step(h, d_in: int, d_out: int, grads=None):
     u_wall_bottom) into grads (numpy[6])."""
     gp = _dp(grads) if grads is not None else None
     return int(_lib.lbm_adjoint_step(h, ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), gp))
+
+
+def lbm_adjoint_step_from(h, d_state: int, t: int, d_in: int, d_out: int, grads=None):
+    """As lbm_adjoint_step, for the FP64 snapshot d_state of S_t; returns the
+    status."""
+    gp = _dp(grads) if grads is not None else None
+    return int(_lib.lbm_adjoint_step_from(h, ctypes.c_void_p(d_state), int(t),
+                                          ctypes.c_void_p(d_in), ctypes.c_void_p(d_out), gp))
 
 
 def lbm_adjoint_take_param_grads(h, grads):

@@ -4,9 +4,10 @@
     of the GPU forward step by central differences, for the state and for
     (sigma, tau_g, lambda, tau_f), coupled and vortex flow.
 (2) Many steps: gradients of J = sum(w * phi_T) with respect to sigma, tau_g,
-    lambda, tau_f and phi0 (directional) through the checkpointed
-    torch.autograd.Function equal central differences of J computed with the
-    FP64 CPU oracle.
+    lambda, tau_f and phi0 (directional) through the torch.autograd.Function
+    equal central differences of J computed with the FP64 CPU oracle, with
+    the forward states recorded in device memory and with checkpoints and
+    recomputation; every split between the two gives the same bits.
 States stay inside (0, 1) so that the clip of Eq. 37 is not hit."""
 import numpy as np
 import pytest
@@ -95,7 +96,8 @@ def _oracle_J(case, theta, phi0, w, nsteps, A):
     return float((o.fields()[0] * w).sum())
 
 
-def test_multistep_gradient_vs_oracle_fd(L):
+@pytest.mark.parametrize("store_bytes", [None, 0], ids=["recorded", "recomputed"])
+def test_multistep_gradient_vs_oracle_fd(L, store_bytes):
     import torch
     lbm, A = L
     nx, ny, T = 48, 40, 15
@@ -108,7 +110,7 @@ def test_multistep_gradient_vs_oracle_fd(L):
     theta0 = np.array([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"]])
     phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
     theta_t = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
-    phiT = A.coupled_run(phi0_t, theta_t, case, T, ckpt_every=4)
+    phiT = A.coupled_run(phi0_t, theta_t, case, T, ckpt_every=4, store_bytes=store_bytes)
     J = (phiT * torch.as_tensor(w, device=phiT.device)).sum()
     J.backward()
     g_theta = theta_t.grad.numpy()
@@ -129,3 +131,52 @@ def test_multistep_gradient_vs_oracle_fd(L):
           - _oracle_J(case, theta0, phi0 - h * d, w, T, A)) / (2 * h)
     ad = float((g_phi0 * d).sum())
     assert abs(ad - fd) <= 2e-5 * abs(fd) + 1e-9, (ad, fd)
+
+
+def test_adjoint_step_from_snapshot_equals_step_on_handle(L):
+    # lbm_adjoint_step_from on a snapshot of S_t gives the bits of
+    # lbm_adjoint_step with S_t in the handle, parameter derivatives included
+    import torch
+    lbm, A = L
+    nx, ny = 40, 24
+    case = W.base_case(nx, ny, walls=1, u_top=0.01, u_bot=-0.02, sigma=5e-3, rho_l=3.0,
+                       tau_f_l=0.8, tau_f_g=0.8)
+    f, g, j = W.random_state(nx, ny, seed=23, coupled=True, phi_lo=0.1, phi_hi=0.9)
+    s = A.AdjointSim(case, np.full((ny, nx), 0.5))
+    s.sim.set_state(0, f, g, j, 7)
+    S = s.snapshot()
+    lam = _rand((20, ny, nx), 31)
+    g1, g2 = np.zeros(6), np.zeros(6)
+    a1 = s.vjp_step(lam, g1)
+    s.step(3)  # the handle's own state no longer matters
+    a2 = s.vjp_step_from(S, 7, lam)
+    s.take_grads(g2)
+    assert torch.equal(a1, a2)
+    assert np.array_equal(g1, g2) and np.abs(g1).max() > 0
+    with pytest.raises(lbm.LbmError):
+        s.vjp_step_from(S, 7, lam, lam)
+    with pytest.raises(lbm.LbmError):
+        s.vjp_step_from(S, 7, lam, S)
+    s.close()
+
+
+def test_recorded_and_recomputed_states_give_the_same_gradient(L):
+    import torch
+    lbm, A = L
+    nx, ny, T = 36, 28, 23
+    case = W.base_case(nx, ny, sigma=4e-3, rho_l=2.0, tau_f_l=0.9, tau_f_g=0.9)
+    phi0 = W.tanh_disc(nx, ny, 17.3, 13.6, 6.0, 4.0, periodic=True)
+    w = torch.as_tensor(W.uniform(4, (ny, nx), 0.0, 1.0), device="cuda")
+    state_bytes = 20 * 8 * nx * ny
+    out = {}
+    for store in (0, 5 * state_bytes, T * state_bytes, None):
+        phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
+        th = torch.tensor([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"]],
+                          dtype=torch.float64, requires_grad=True)
+        phiT = A.coupled_run(phi0_t, th, case, T, ckpt_every=4, store_bytes=store)
+        (phiT * w).sum().backward()
+        out[store] = (phiT.detach().cpu().numpy(), th.grad.numpy(), phi0_t.grad.numpy())
+    ref = out[0]
+    for store, (p, gt, gp) in out.items():
+        assert np.array_equal(p, ref[0]), store
+        assert np.array_equal(gt, ref[1]) and np.array_equal(gp, ref[2]), store
