@@ -70,6 +70,8 @@ def parse():
                     help="VARIANT,BX,BY,ZC for the 3-D step (default: autotuned)")
     ap.add_argument("--only-shear", action="store_true",
                     help="only the sheared-droplet numbers (walls, FP32/FP64, D gradient)")
+    ap.add_argument("--only-batching", action="store_true",
+                    help="only the batched-vs-separate-handles comparison")
     ap.add_argument("--only-adjoint", action="store_true",
                     help="print the reverse-mode timing only (profiling aid)")
     return ap.parse_args()
@@ -419,10 +421,67 @@ def run_extras(args, cases, dev):
         s.close()
     vort["phi_maxdiff_f32_vs_f64"] = float(np.abs(fin["f32"] - fin["f64"]).max())
     out["single_vortex"] = vort
+    out["batching"] = batching_timing(cases, dev)
     out["adjoint"] = adjoint_timing(dev)
     out["rayleigh_plateau_3d"] = rp3d_timing(dev, steps=args.steps3)
     out["shear_droplet"] = shear_timing(dev)
     return out
+
+
+def batching_timing(cases, dev, steps_launch=10, steps_graph=64):
+    """The headline batch advanced by one launch per step for all cases,
+    against the same cases as separate single-case handles on one stream:
+    (a) one lbm_step(h, 1) per case per step, i.e. one launch per case per
+    step; (b) each case advanced steps_graph steps in turn, which the library
+    replays as a CUDA graph per case.  FP32; the batch is autotuned as in the
+    headline, the separate handles keep the library's default tiling."""
+    import torch
+    from paper_2505_10899_gb300 import lbm
+
+    nodes = sum(c["nx"] * c["ny"] for c in cases)
+    phis, us = host_inputs(cases)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b)
+
+    sim = lbm.Sim(cases, phis, us, precision="f32")
+    sim.autotune(1)
+    sim.step(3)
+    ms_b = timed(lambda: [sim.step(1) for _ in range(steps_launch)]) / steps_launch
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    sims = [lbm.Sim(c, p, u, precision="f32") for c, p, u in zip(cases, phis, us)]
+    for s in sims:
+        s.step(2)
+
+    def per_launch():
+        for _ in range(steps_launch):
+            for s in sims:
+                s.step(1)
+
+    ms_l = timed(per_launch) / steps_launch
+    ms_g = timed(lambda: [s.step(steps_graph) for s in sims]) / steps_graph
+    ok = all(s.status() == lbm.LBM_OK for s in sims)
+    for s in sims:
+        s.close()
+    del sims
+    torch.cuda.empty_cache()
+    mlups = lambda ms: round(nodes / (ms * 1e-3) / 1e6, 1)
+    return {"ncases": len(cases), "nodes": nodes,
+            "batched_mlups": mlups(ms_b),
+            "per_case_launch_each_step_mlups": mlups(ms_l),
+            "per_case_graph_replay_mlups": mlups(ms_g),
+            "speedup_vs_launch_per_case_per_step": round(ms_l / ms_b, 2),
+            "speedup_vs_graph_per_case": round(ms_g / ms_b, 2),
+            "status_ok": ok}
 
 
 def rp3d_timing(dev, grid=(256, 256, 1024), precisions=("f32", "f16", "f64"), steps=50,
@@ -698,6 +757,12 @@ def main():
     if args.only_adjoint:
         import torch
         print(json.dumps({"adjoint": adjoint_timing(torch.device("cuda", 0))}), flush=True)
+        return
+    if args.only_batching:
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"batching": batching_timing(rank_cases(args, 0), dev)}), flush=True)
         return
     if args.only_shear:
         import torch
