@@ -33,7 +33,11 @@
  *   - rho(phi) and mu(phi) are linear in the unclipped phi, and
  *     tau_f(x) = mu/(rho c_s^2) + 1/2 from Eq. 27;
  *   - F in Eqs. 21 and 28 is the surface force hbar*grad(phi) (Eq. 18);
- *   - n = grad(psi)/|grad(psi)| is taken as 0 where |grad(psi)| == 0;
+ *   - n = grad(psi)/|grad(psi)| where |grad(psi)| >= 0.1, else 0 (psi of
+ *     Eq. 14, a signed distance with |grad(psi)| = 1 on the equilibrium
+ *     profile): |grad(psi)| < 0.1 only on ridges of psi (droplet centres,
+ *     thread axes, mid-planes of necks) and in the clipped bulk, where a
+ *     unit vector would take its direction from rounding;
  *   - the backward difference starts from phi0*u0 (d_t(phi u) = 0 at t=0);
  *   - prescribed single-vortex velocity: u = -U sin^2(pi X) sin(2 pi Y)
  *     cos(pi t/T), v = U sin^2(pi Y) sin(2 pi X) cos(pi t/T) with node-centred
@@ -50,6 +54,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* |grad(psi)| below which n of Eq. 17 is 0 (see the header). */
+#define NORMAL_MIN 0.1
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -520,7 +527,7 @@ static void collide_node(const orc_params *p, const double *f, const double *g,
   double gsx = w->gsx[k], gsy = w->gsy[k];
   double nrm2 = gsx * gsx + gsy * gsy;
   double nx_ = 0.0, ny_ = 0.0;
-  if (nrm2 != 0.0) {
+  if (nrm2 >= NORMAL_MIN * NORMAL_MIN) {
     double nrm = sqrt(nrm2);
     nx_ = gsx / nrm;
     ny_ = gsy / nrm;

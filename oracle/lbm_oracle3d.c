@@ -15,7 +15,9 @@
  *     with g_eq of Eq. 31 and G_i of Eq. 32 on that lattice, so that the
  *     mobility is M = (tau_g - 1/2)/4 (Eq. 34 with c_s^2 = 1/4);
  *   - the isotropic gradient and Laplacian of Sec. 3.2 with the D3Q19 set;
- *   - psi, its clip and xi as Eq. 37; phi = sum g (Eq. 35).
+ *   - psi, its clip and xi as Eq. 37; phi = sum g (Eq. 35);
+ *   - n = grad(psi)/|grad(psi)| where |grad(psi)| >= 0.1, else 0, as in the
+ *     2-D oracle.
  * Only the test-suite, the smoke check and the CPU-baseline leg of the
  * benchmark may load this file.  It shares no code with the CUDA library.
  *
@@ -26,6 +28,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* |grad(psi)| below which n of Eq. 17 is 0. */
+#define NORMAL_MIN 0.1
 
 /* ORC_PLANT (11-20) selects a deliberately wrong variant of one formula, for
  * the mutation test of the pins only; 0 (the default) is the method. */
@@ -310,7 +315,7 @@ int orc3_step(const orc3_params *p, double *f, double *g, double *j, int64_t nst
 #endif
           }
           double g2 = m.gs[0] * m.gs[0] + m.gs[1] * m.gs[1] + m.gs[2] * m.gs[2];
-          if (g2 != 0.0)
+          if (g2 >= NORMAL_MIN * NORMAL_MIN)
             for (int a = 0; a < 3; ++a) nn[a] = m.gs[a] / sqrt(g2);
           double ge[7], Gi[7];
           orc3_geq(phi, m.mu, p->lambda, m.u, ge);

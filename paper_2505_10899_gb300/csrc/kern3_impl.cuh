@@ -24,6 +24,11 @@ static Args3<T, S> make_args(const Bufs& b, const Host3& h, int parity) {
   a.var_tau = h.var_tau;
   a.beta4 = (T)h.beta4, a.kappa = (T)h.kappa, a.lambda = (T)h.lambda;
   a.lamW = (T)h.lamW, a.xi = (T)h.xi, a.tfac = (T)h.tfac;
+  {
+    // psi_k is ln(a/b) in FP64 and log2(a/b) in FP32, q = 12 grad(psi_k)
+    const double qs = 48.0 * lbmk3::kNormalMin / (h.W * (sizeof(T) == 4 ? 0.69314718055994531 : 1.0));
+    a.qmin2 = (T)(qs * qs);
+  }
   a.wg = (T)h.wg, a.hg = (T)h.hg, a.wf = (T)h.wf, a.hf = (T)h.hf;
   a.rho_g = (T)h.rho_g, a.drho = (T)h.drho, a.mu_g = (T)h.mu_g, a.dmu = (T)h.dmu;
   return a;

@@ -21,6 +21,7 @@ struct Host3 {
   int32_t nx, ny, nz, var_tau;
   int64_t plane;
   double beta4, kappa, lambda, lamW, xi, tfac, wg, hg, wf, hf, rho_g, drho, mu_g, dmu;
+  double W;  // interface width (the threshold of the normal scales with it)
 };
 
 inline bool tile_ok(int bx, int by) {

@@ -138,6 +138,7 @@ Host3 host_params(const lbm3_params& p, int64_t plane) {
   h.lamW = p.lambda / p.W;
   h.xi = p.xi;
   h.tfac = 4.0 / ((1.0 + 2.0 * p.xi) * (1.0 + 2.0 * p.xi));
+  h.W = p.W;
   h.wg = 1.0 / p.tau_g;
   h.hg = 1.0 - 0.5 / p.tau_g;
   const double cs2 = 1.0 / 3.0;

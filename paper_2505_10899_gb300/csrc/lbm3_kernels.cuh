@@ -294,7 +294,7 @@ __device__ __forceinline__ Out3<T> node3(const Args3<T, S>& a, T (&F)[19], T (&G
   const T pc = N3<T>::clamp01(phi);
   const T ta = pc + a.xi, tb = (T(1) - pc) + a.xi;
   const T q2 = (qx * qx + qy * qy) + qz * qz;
-  const T iq = (q2 > T(0)) ? N3<T>::rsq(q2) : T(0);
+  const T iq = (q2 >= a.qmin2) ? N3<T>::rsq(q2) : T(0);  // n := 0 on ridges of psi
   // (lambda/W)[1 - tanh^2(2 psi/W)] / |grad psi|, with 1 - tanh^2 = 4ab/(a+b)^2
   const T sh = a.lamW * a.tfac * ta * tb * iq;
   // c_s^2 x the braced vector of Eq. 32: d_t(phi u) + (sharpening) / 4

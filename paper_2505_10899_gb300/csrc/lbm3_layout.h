@@ -9,7 +9,11 @@
 #pragma once
 #include <cstdint>
 
+#include "lbm_layout.h"
+
 namespace lbmk3 {
+
+using lbmk::kNormalMin;  // threshold of the interface normal, as in 2-D
 
 constexpr int kQF = 19;  // D3Q19 (hydrodynamics)
 constexpr int kQG = 7;   // D3Q7 (phase field)
@@ -40,6 +44,7 @@ struct Args3 {
   int32_t var_tau;         // 1: tau_f varies with phi (Eq. 27 per node)
   T beta4, kappa, lambda;  // 4 beta (beta = 12 sigma/W), kappa = 3 sigma W/2
   T lamW, xi, tfac;        // lambda/W, xi, 4/(1+2 xi)^2
+  T qmin2;                 // |12 grad(psi_k)|^2 at |grad(psi)| = kNormalMin
   T wg, hg;                // 1/tau_g, 1 - 1/(2 tau_g)
   T wf, hf;                // uniform tau_f: 1/tau_f, 1 - 1/(2 tau_f)
   T rho_g, drho, mu_g, dmu;  // rho(phi) = rho_g + phi drho, mu(phi) likewise

@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
     const double pc = fmin(fmax(phi, 0.0), 1.0);
     const double ta = pc + ph.xi, tb = (1.0 - pc) + ph.xi;
     const double q2 = qx * qx + qy * qy;
-    const double iq = (q2 > 0.0) ? 1.0 / sqrt(q2) : 0.0;
+    const double iq = (q2 >= ph.qmin2) ? 1.0 / sqrt(q2) : 0.0;
     const double sh = ph.lamW * ph.tfac * ta * tb * iq;
     const double Vx = 3.0 * dJx + sh * qx, Vy = 3.0 * dJy + sh * qy;
     const Mom<double> mg = lbmk::moments(G);
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
     const double c0 = ph.lamW * ph.tfac;
     const double lta = c0 * tb * iq * lsh, ltb = c0 * ta * iq * lsh, liq = c0 * ta * tb * lsh;
     gacc[2] += ph.tfac * ta * tb * iq * lsh * a.invW;  // lamW = lambda / W
-    if (q2 > 0.0) {
+    if (q2 >= ph.qmin2) {  // below the threshold n = 0: no derivative
       const double lq2 = -0.5 * iq * iq * iq * liq;
       lqx += 2.0 * qx * lq2;
       lqy += 2.0 * qy * lq2;

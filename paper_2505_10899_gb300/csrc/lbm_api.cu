@@ -220,6 +220,10 @@ Phys<T> make_phys(const lbm_params& p) {
   ph.lamW = (T)(p.lambda / p.W);
   ph.xi = (T)p.xi;
   ph.tfac = (T)(4.0 / ((1.0 + 2.0 * p.xi) * (1.0 + 2.0 * p.xi)));
+  // the kernels' psi_k is ln(a/b) in FP64 and log2(a/b) in FP32, psi = (W/4) ln(a/b),
+  // and they form q = 12 grad(psi_k): |grad(psi)| = (W s / 48) |q|, s = 1 or ln 2
+  const double qs = 48.0 * lbmk::kNormalMin / (p.W * (sizeof(T) == 4 ? 0.69314718055994531 : 1.0));
+  ph.qmin2 = (T)(qs * qs);
   double sg[9];
   for (int i = 0; i < 9; ++i) sg[i] = p.s_g[i];
   sg[3] = sg[5] = 1.0 / p.tau_g;  // Eq. 34

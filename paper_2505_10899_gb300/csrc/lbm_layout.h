@@ -39,6 +39,16 @@ struct CaseDev {
 // Moment-space rates are folded with the inverse row norms
 // D = diag(1/9, 1/36, 1/36, 1/6, 1/12, 1/6, 1/12, 1/4, 1/4) of Eq. 24:
 //   sD[k] = -s_k D_k,  hD[k] = (1 - s_k/2) D_k.
+// Interface normal of Eq. 17: n = grad(psi)/|grad(psi)| where |grad(psi)| >=
+// kNormalMin, else 0 (psi of Eq. 14 in lattice units).  psi is a signed
+// distance, |grad(psi)| = 1 on the equilibrium profile; it falls below
+// kNormalMin only on ridges of psi (the centre of a droplet, the axis of a
+// thread, the mid-plane of a neck: points no nearer to one part of the
+// interface than to another) and in the clipped bulk.  There a unit vector
+// would take its direction from rounding, and a small |grad(psi)| would
+// amplify any perturbation by 1/|grad(psi)|.
+constexpr double kNormalMin = 0.1;
+
 template <typename T>
 struct Phys {
   T beta4;   // 4 beta, beta = 12 sigma / W
@@ -47,6 +57,7 @@ struct Phys {
   T lamW;    // lambda / W
   T xi;
   T tfac;    // 4 / (1 + 2 xi)^2 : 1 - tanh^2(2 psi / W) = tfac * a * b
+  T qmin2;   // |12 grad(psi_k)|^2 at |grad(psi)| = kNormalMin (psi_k: the kernel's psi)
   T fsD[kQ], fhD[kQ];
   T gsD[kQ], ghD3[kQ];  // ghD3 = ghD / 3 (the source moments carry a 1/3)
   double vU, vT;        // prescribed vortex amplitude and period

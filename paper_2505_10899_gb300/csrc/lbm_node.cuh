@@ -314,7 +314,7 @@ __device__ __forceinline__ NodeOut<T> node_update(const Phys<T>& ph, const CaseK
     const T pc = Num<T>::clamp01(phi);
     const T ta = pc + ph.xi, tb = (T(1) - pc) + ph.xi;
     const T q2 = qx * qx + qy * qy;
-    const T iq = (q2 > T(0)) ? Num<T>::rsq(q2) : T(0);
+    const T iq = (q2 >= ph.qmin2) ? Num<T>::rsq(q2) : T(0);  // n := 0 on ridges of psi
     // (lambda/W) [1 - tanh^2(2psi/W)] / |grad psi|, tanh via Eqs. 13-15
     const T sh = ph.lamW * ph.tfac * ta * tb * iq;
     const T Vx = T(3) * dJx + sh * qx;  // d_t(phi u)/c_s^2 + sharpening flux

@@ -66,3 +66,54 @@ def test_batched_512_fp32_volume_drift_1e4_steps(L):
     v = s.volume()
     assert np.all(np.isfinite(v))
     assert np.abs(v / v0 - 1.0).max() <= 1e-6
+
+
+def _vs_oracle(L, case, phi0, u0, nsteps, prec):
+    o = oracle.Oracle(case, phi0, u0).step(nsteps)
+    s = L.Sim(case, phi0, u0, precision=prec)
+    s.autotune(1)  # the launch bench.py times
+    s.step(nsteps)
+    assert s.status() == L.LBM_OK
+    phi, ux, uy, p = s.fields(0)
+    ophi, oux, ouy, op = o.fields()
+    s.close()
+    return (float(np.abs(phi - ophi).max()),
+            float(max(np.abs(ux - oux).max(), np.abs(uy - ouy).max())))
+
+
+@pytest.mark.parametrize("config", ["two_droplets_as_printed", "single_vortex_256",
+                                    "sheared_droplet_512x256"])
+def test_configs_at_full_size_against_oracle(L, config):
+    # the 2-D set-ups at their stated sizes, without added noise: droplets
+    # centred on nodes (ridges of psi) and a saturated liquid bulk, the two
+    # places where the direction of the normal of Eq. 17 is not defined
+    if config == "two_droplets_as_printed":
+        case, phi0, u0, _, _ = W.two_droplets()
+    elif config == "single_vortex_256":
+        case, phi0, u0 = W.single_vortex(n=256, W=3.0, U=0.02, T=16384)
+    else:
+        case, phi0, u0 = W.shear_droplet(512, 256, R=40.0, U=0.01, Ca=0.1, Re=0.1)
+    dphi, du = _vs_oracle(L, case, phi0, u0, 100, "f64")
+    assert dphi <= 1e-12 and du <= 1e-12, (dphi, du)
+    dphi, du = _vs_oracle(L, case, phi0, u0, 100, "f32")
+    assert dphi <= 1e-5 and du <= 1e-6, (dphi, du)
+
+
+def test_batched_512_fp64_sampled_against_oracle(L):
+    # FP64 on the whole benchmark batch (saturated droplets up to R = 150):
+    # sampled cases within 1e-12 of the oracle after 10 steps
+    cases = W.batched_droplets(512, seed=2026)
+    phis, us = zip(*(W.case_fields(c) for c in cases))
+    s = L.Sim(cases, list(phis), list(us), precision="f64")
+    s.step(10)
+    assert s.status() == L.LBM_OK
+    edges = np.array([c["nx"] for c in cases])
+    radii = np.array([c["R"] for c in cases])
+    sample = sorted({0, 511, int(edges.argmin()), int(edges.argmax()), int(radii.argmax())})
+    for k in sample:
+        o = oracle.Oracle(cases[k], phis[k], us[k]).step(10)
+        phi, ux, uy, p = s.fields(k)
+        ophi, oux, ouy, op = o.fields()
+        assert np.abs(phi - ophi).max() <= 1e-12, k
+        assert max(np.abs(ux - oux).max(), np.abs(uy - ouy).max()) <= 1e-12, k
+    s.close()
