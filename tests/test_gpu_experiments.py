@@ -105,11 +105,7 @@ def test_column_eq45_satellites_kept_by_modified_model(E):
     # models pinch off and leave satellites by step 50000; between then and
     # step 80000 the classical model shrinks the satellites and has lost
     # over 10% of the volume inside phi = 1/2, the modified model keeps
-    # both.  Satellite sizes are compared as totals: the unit normal of
-    # Eq. 17 at the axis nodes of the symmetry planes makes the modified
-    # model's pinch-off break the mirror symmetry (test_oracle3d.py), so
-    # individual satellites are not mirror pairs and their split depends on
-    # rounding.
+    # both.  Satellite sizes are compared as totals.
     res = {}
     for lam in (0.5, 0.0):
         case, phi0 = W.column_eq45(lam=lam, n_side=128)
