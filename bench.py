@@ -578,6 +578,7 @@ def adjoint_timing(dev, nx=512, ny=256, nsteps=32, ckpt=8):
     import torch
     from paper_2505_10899_gb300 import adjoint as A
 
+    torch.cuda.empty_cache()
     case = W.base_case(nx, ny)
     phi0 = W.tanh_disc(nx, ny, nx / 2, ny / 2, 40.0, 4.0, periodic=True)
     s = A.AdjointSim(case, phi0)
@@ -669,7 +670,9 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
                      "taylor_D": float(A.taylor_deformation(phi)),
                      "status": s.status()}
         s.close()
-    # checkpointed reverse mode of D(phi_T)
+    # reverse mode of D(phi_T); cached blocks of the earlier legs are returned
+    # first so that the 64 GiB of recorded states is one fresh allocation
+    torch.cuda.empty_cache()
     th = torch.tensor([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"],
                        case["u_top"], case["u_bot"]], dtype=torch.float64, requires_grad=True)
     phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
