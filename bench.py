@@ -673,6 +673,10 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
     # reverse mode of D(phi_T); cached blocks of the earlier legs are returned
     # first so that the 64 GiB of recorded states is one fresh allocation
     torch.cuda.empty_cache()
+    # untimed: the first CUDA call of the objective and of its derivative loads
+    # torch's own kernels
+    A.taylor_deformation(torch.tensor(phi0, device=dev, requires_grad=True)).backward()
+    torch.cuda.synchronize(dev)
     th = torch.tensor([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"],
                        case["u_top"], case["u_bot"]], dtype=torch.float64, requires_grad=True)
     phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
