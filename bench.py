@@ -682,7 +682,9 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
     phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    store = 64 << 30  # device memory for recorded states; the rest is recomputed
+    # device memory for recorded states (the rest is recomputed): 128 GiB, at
+    # most half of what is free
+    store = min(128 << 30, torch.cuda.mem_get_info(dev)[0] // 2)
     phiT = A.coupled_run(phi0_t, th, case, grad_steps, ckpt, u0=u0, store_bytes=store)
     D = A.taylor_deformation(phiT)
     torch.cuda.synchronize(dev)
