@@ -670,6 +670,21 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
                      "taylor_D": float(A.taylor_deformation(phi)),
                      "status": s.status()}
         s.close()
+    # the parameter range of the set-up: D after nsteps for Ca in {0.1, 0.2,
+    # 0.4} and Re in {0.1, 1} (FP32), beside Taylor's small-deformation
+    # value D = Ca (19 m + 16) / (16 m + 16) = 35/32 Ca at viscosity ratio m = 1
+    sweep = []
+    for Ca in (0.1, 0.2, 0.4):
+        for Re in (0.1, 1.0):
+            c, p0, v0 = W.shear_droplet(512, 256, R=40.0, U=0.01, Ca=Ca, Re=Re)
+            s = lbm.Sim(c, p0, v0, precision="f32")
+            s.step(nsteps)
+            phi = torch.as_tensor(s.fields(0)[0])
+            sweep.append({"Ca": Ca, "Re": Re, "taylor_D": round(float(A.taylor_deformation(phi)), 5),
+                          "small_deformation_theory": round(35.0 / 32.0 * Ca, 5),
+                          "status": s.status()})
+            s.close()
+    out["ca_re_sweep_f32"] = sweep
     # reverse mode of D(phi_T); cached blocks of the earlier legs are returned
     # first so that the 64 GiB of recorded states is one fresh allocation
     torch.cuda.empty_cache()
