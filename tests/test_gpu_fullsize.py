@@ -117,3 +117,81 @@ def test_batched_512_fp64_sampled_against_oracle(L):
         assert np.abs(phi - ophi).max() <= 1e-12, k
         assert max(np.abs(ux - oux).max(), np.abs(uy - ouy).max()) <= 1e-12, k
     s.close()
+
+
+def test_sheared_droplet_gradient_at_full_size_vs_central_differences(L):
+    # The sheared droplet at its stated size (512 x 256, walls at -U and +U =
+    # 0.01, R = 40, Ca = 0.1, Re = 0.1), 2 x 10^4 steps: dD/d(sigma, tau_g,
+    # U_w) of the Taylor deformation from the reverse mode (states stored in
+    # HBM, checkpoints below them) against central differences of D from FP64
+    # forward runs of the same library.  U_w moves both walls (u_top = U_w,
+    # u_bot = -U_w); the initial Couette field stays fixed.  The droplet
+    # saturates (phi crosses 1 inside it and 0 in the gas), so the clip of
+    # Eq. 37 puts kinks into D(theta): central differences average over the
+    # kinks that a step of h crosses, the reverse mode takes the derivative of
+    # the branch taken.  Measured gaps: 5e-5 to 9e-5 relative for sigma and
+    # U_w at h = 1e-4 and 1e-5, independent of h; 1.4e-3 (1.5e-6 absolute)
+    # for the small tau_g derivative.  Without saturation the two agree to
+    # 1e-9 (test below).
+    import torch
+    from paper_2505_10899_gb300 import adjoint as A
+    case, phi0, u0 = W.shear_droplet(512, 256, R=40.0, U=0.01, Ca=0.1, Re=0.1)
+    T = 20000
+    th0 = np.array([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"],
+                    case["u_top"], case["u_bot"]])
+    th_t = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    phiT = A.coupled_run(torch.tensor(phi0), th_t, case, T, ckpt_every=256, u0=u0,
+                         store_bytes=8 << 30)
+    D = A.taylor_deformation(phiT)
+    D.backward()
+    g = th_t.grad.numpy()
+
+    def D_of(th):
+        s = L.Sim(A.case_with(case, th), phi0, u0, precision="f64")
+        s.step(T)
+        assert s.status() == L.LBM_OK
+        phi = torch.as_tensor(s.fields(0)[0])
+        s.close()
+        return float(A.taylor_deformation(phi))
+
+    assert abs(D_of(th0) - float(D.detach())) < 1e-12
+    for name, dirn, grad in (("sigma", [1, 0, 0, 0, 0, 0], g[0]),
+                             ("tau_g", [0, 1, 0, 0, 0, 0], g[1]),
+                             ("U_w", [0, 0, 0, 0, 1, -1], g[4] - g[5])):
+        dirn = np.array(dirn, dtype=float)
+        h = 1e-4 * float(np.abs(th0) @ np.abs(dirn)) / np.abs(dirn).sum()
+        fd = (D_of(th0 + h * dirn) - D_of(th0 - h * dirn)) / (2 * h)
+        assert abs(grad - fd) <= 3e-4 * abs(fd) + 5e-6, (name, grad, fd)
+
+
+def test_sheared_droplet_gradient_over_long_runs_vs_central_differences(L):
+    # A droplet that never saturates (R = 6, W = 4, 48 x 32 channel): D(theta)
+    # is smooth, and the reverse mode (checkpoints and recomputation only)
+    # matches central differences of FP64 forward runs to 1e-8 relative after
+    # 4000 steps, for sigma, tau_g, lambda and U_w.
+    import torch
+    from paper_2505_10899_gb300 import adjoint as A
+    case, phi0, u0 = W.shear_droplet(nx=48, ny=32, R=6.0, U=0.01, Ca=0.2, Re=0.5)
+    T = 4000
+    th0 = np.array([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"],
+                    case["u_top"], case["u_bot"]])
+    th_t = torch.tensor(th0, dtype=torch.float64, requires_grad=True)
+    phiT = A.coupled_run(torch.tensor(phi0), th_t, case, T, ckpt_every=64, u0=u0, store_bytes=0)
+    A.taylor_deformation(phiT).backward()
+    g = th_t.grad.numpy()
+
+    def D_of(th):
+        s = L.Sim(A.case_with(case, th), phi0, u0, precision="f64")
+        s.step(T)
+        phi = torch.as_tensor(s.fields(0)[0])
+        s.close()
+        return float(A.taylor_deformation(phi))
+
+    for name, dirn, grad in (("sigma", [1, 0, 0, 0, 0, 0], g[0]),
+                             ("tau_g", [0, 1, 0, 0, 0, 0], g[1]),
+                             ("lambda", [0, 0, 1, 0, 0, 0], g[2]),
+                             ("U_w", [0, 0, 0, 0, 1, -1], g[4] - g[5])):
+        dirn = np.array(dirn, dtype=float)
+        h = 1e-5 * float(np.abs(th0) @ np.abs(dirn)) / np.abs(dirn).sum()
+        fd = (D_of(th0 + h * dirn) - D_of(th0 - h * dirn)) / (2 * h)
+        assert abs(grad - fd) <= 1e-8 * abs(fd), (name, grad, fd)
