@@ -740,10 +740,23 @@ def cpu_baseline(cases, seconds):
         used += 1
         if t_used > seconds:
             break
-    return {"value": round(done_nodes * steps / t_used / 1e6, 3), "unit": "MLUPS",
-            "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"first {used} of {len(cases)} cases x {steps} steps "
-                      f"({done_nodes} nodes, {t_used:.1f} s of oracle time)"}
+    out = {"value": round(done_nodes * steps / t_used / 1e6, 3), "unit": "MLUPS",
+           "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"first {used} of {len(cases)} cases x {steps} steps "
+                     f"({done_nodes} nodes, {t_used:.1f} s of oracle time)"}
+    # the same loops on one core (the results are the same bits), first case
+    n = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        phi, u = W.case_fields(cases[0])
+        o = oracle.Oracle(cases[0], phi, u)
+        t0 = time.perf_counter()
+        o.step(1)
+        t1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(n)
+    out["single_core_value"] = round(cases[0]["nx"] * cases[0]["ny"] / t1 / 1e6, 3)
+    return out
 
 
 def run_reference(args):

@@ -88,6 +88,7 @@ def lib():
             L.orc_collide.argtypes = [P, _D, _D, _D, ctypes.c_int64, _D, _D, _D]
             L.orc_volume.argtypes = [P, _D, _I8, ctypes.c_int32, _D]
             L.orc_num_threads.restype = ctypes.c_int
+            L.orc_set_num_threads.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
@@ -195,6 +196,11 @@ def stencil(chi):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracles' OpenMP loops (process-wide)."""
+    lib().orc_set_num_threads(int(n))
 
 
 class Oracle:

@@ -695,3 +695,15 @@ int orc_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Threads of the OpenMP loops over rows (the runtime is shared by every
+ * oracle library in the process).  Each node is computed by one thread with
+ * no reduction across nodes, so the results do not depend on the count. */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
