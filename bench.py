@@ -70,6 +70,10 @@ def parse():
                     help="VARIANT,BX,BY,ZC for the 3-D step (default: autotuned)")
     ap.add_argument("--only-shear", action="store_true",
                     help="only the sheared-droplet numbers (walls, FP32/FP64, D gradient)")
+    ap.add_argument("--only-lattice", action="store_true",
+                    help="only the droplet-lattice grid (one large case)")
+    ap.add_argument("--lattice", type=str, default="16384,8192",
+                    help="NX,NY of the droplet-lattice grid (multiples of 256)")
     ap.add_argument("--only-batching", action="store_true",
                     help="only the batched-vs-separate-handles comparison")
     ap.add_argument("--only-adjoint", action="store_true",
@@ -439,6 +443,7 @@ def run_extras(args, cases, dev):
     vort["phi_maxdiff_f32_vs_f64"] = float(np.abs(fin["f32"] - fin["f64"]).max())
     out["single_vortex"] = vort
     out["batching"] = batching_timing(cases, dev)
+    out["droplet_lattice_16384x8192"] = lattice_timing(dev)
     out["adjoint"] = adjoint_timing(dev)
     out["rayleigh_plateau_3d"] = rp3d_timing(dev, steps=args.steps3)
     out["shear_droplet"] = shear_timing(dev)
@@ -499,6 +504,49 @@ def batching_timing(cases, dev, steps_launch=10, steps_graph=64):
             "speedup_vs_launch_per_case_per_step": round(ms_l / ms_b, 2),
             "speedup_vs_graph_per_case": round(ms_g / ms_b, 2),
             "status_ok": ok}
+
+
+def lattice_timing(dev, steps=50, grid=(16384, 8192), tiling=None):
+    """The coupled FP32 step on one large periodic grid: 16384 x 8192 nodes
+    (134 M) holding a 64 x 32 lattice of R = 24 droplets with the physics of
+    the two-droplet set-up; about 22 GB of state.  Autotuned, 3 warm-up steps,
+    `steps` timed steps with CUDA events; MLUPS and the fraction of the
+    measured HBM peak at 160 algorithmic bytes per node."""
+    import torch
+    from paper_2505_10899_gb300 import lbm
+
+    torch.cuda.empty_cache()
+    nx, ny = grid
+    case, phi0, _ = W.droplet_lattice(nx, ny, nx // 256, ny // 256)
+    nodes = case["nx"] * case["ny"]
+    s = lbm.Sim(case, phi0, None, precision="f32")
+    if tiling:
+        s.set_tiling(*tiling)
+    else:
+        s.autotune(1)
+    s.step(3)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(s.stream)
+    s.step(steps)
+    b.record(s.stream)
+    torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / steps
+    peak, kind = measured_peaks()
+    gbs = 160 * nodes / (ms * 1e-3) / 1e9
+    out = {"grid": f"{case['nx']}x{case['ny']}", "nodes": nodes,
+           "droplets": f"{nx // 256}x{ny // 256}, R = 24",
+           "mlups": round(nodes / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 4),
+           "kernel": "step_kernel_tma" if s.kernel() == 2 else "step_kernel",
+           "tiling": {"bx": s.tiling()[0], "rows": s.tiling()[1],
+                      "chosen_by": "fixed" if tiling else "autotune"},
+           "roofline": {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(gbs / peak, 4), "peak_kind": kind},
+           "status": s.status()}
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return out
 
 
 def rp3d_timing(dev, grid=(256, 256, 1024), precisions=("f32", "f16", "f64"), steps=50,
@@ -811,6 +859,15 @@ def main():
     if args.only_adjoint:
         import torch
         print(json.dumps({"adjoint": adjoint_timing(torch.device("cuda", 0))}), flush=True)
+        return
+    if args.only_lattice:
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        grid = tuple(int(v) for v in args.lattice.split(","))
+        til = tuple(int(v) for v in args.tiling.split(",")) if args.tiling else None
+        print(json.dumps({"droplet_lattice": lattice_timing(dev, grid=grid, tiling=til)}),
+              flush=True)
         return
     if args.only_batching:
         import torch

@@ -178,8 +178,8 @@ Layout make_layout(const lbm_params* c, int n, int n_items, int total_regions) {
   off = align_up(off + (size_t)std::max(total_regions, n * lbmk::kMaxRegions) * sizeof(double));
   int64_t maxp = 0;
   for (int k = 0; k < n; ++k) maxp = std::max<int64_t>(maxp, (int64_t)c[k].nx * c[k].ny);
-  L.staging = off;  // two slots of 4 planes: lbm_init alternates them
-  off = align_up(off + (size_t)maxp * 8 * sizeof(double));
+  L.staging = off;  // slots of 4 planes, two for a batch: lbm_init alternates them
+  off = align_up(off + (size_t)maxp * (n > 1 ? 8 : 4) * sizeof(double));
   L.f.resize(n);
   L.g.resize(n);
   L.glo.resize(n);

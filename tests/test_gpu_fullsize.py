@@ -195,3 +195,25 @@ def test_sheared_droplet_gradient_over_long_runs_vs_central_differences(L):
         h = 1e-5 * float(np.abs(th0) @ np.abs(dirn)) / np.abs(dirn).sum()
         fd = (D_of(th0 + h * dirn) - D_of(th0 - h * dirn)) / (2 * h)
         assert abs(grad - fd) <= 1e-8 * abs(fd), (name, grad, fd)
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", 1e-5), ("f64", 1e-12)])
+def test_droplet_lattice_16384x8192_against_oracle_cell(L, prec, tol):
+    # One 134 M-node grid of 64 x 32 identical droplet cells.  The run of the
+    # whole grid equals, cell by cell, the oracle's run of one periodic cell:
+    # every cell of the GPU result is compared with it after 100 steps, and
+    # all cells must agree with each other to the bit (the per-node arithmetic
+    # does not depend on where a cell falls in the kernel's strips and runs).
+    case, phi0, cell = W.droplet_lattice()
+    ny, nx = phi0.shape
+    cy, cx = cell.shape
+    o = oracle.Oracle(dict(case, nx=cx, ny=cy), cell).step(100)
+    ocell = o.fields()[0]
+    s = L.Sim(case, phi0, None, precision=prec)
+    s.autotune(1)
+    s.step(100)
+    assert s.status() == L.LBM_OK
+    phi = s.fields(0)[0].reshape(ny // cy, cy, nx // cx, cx).transpose(0, 2, 1, 3)
+    s.close()
+    assert np.abs(phi - ocell).max() <= tol
+    assert (phi == phi[0, 0]).all()

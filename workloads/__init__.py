@@ -288,3 +288,17 @@ def column_eq45(n=256, a=0.15, amp=0.05, W=4.0, sigma=1e-3, tau_f=0.6, lam=0.5,
     case = base_case3(m, m, n, W=W, sigma=sigma, tau_g=tau_g, rho_l=rho_ratio, rho_g=1.0,
                       tau_f_l=tau_f, tau_f_g=tau_f, **{"lambda": lam})
     return case, liquid_column(m, m, n, a / h, W, eps=amp / a, wavelength=n)
+
+
+def droplet_lattice(nx=16384, ny=8192, mx=64, my=32, R=24.0, W=4.0, lam=0.5):
+    """One large periodic grid holding an mx x my lattice of equal droplets of
+    radius R (tanh profile), each centred in its (nx/mx) x (ny/my) cell, with
+    the physics of the two-droplet set-up of Sec. 4.1 (sigma = 1e-3,
+    tau_g = 0.8, tau_f = 1, density ratio 1), fluid at rest.  The field is
+    one cell repeated, so a run of the whole grid equals, cell by cell, a run
+    of one periodic cell.  Returns (case, phi0, cell)."""
+    cx, cy = nx // mx, ny // my
+    assert cx * mx == nx and cy * my == ny
+    cell = tanh_disc(cx, cy, 0.5 * cx, 0.5 * cy, R, W, periodic=True)
+    case = base_case(nx, ny, W=W, sigma=1e-3, tau_g=0.8, **{"lambda": lam})
+    return case, np.tile(cell, (my, mx)), cell
