@@ -190,6 +190,14 @@ def coupled_run(phi0, theta, case, nsteps, ckpt_every=16, u0=None, store_bytes=N
     return CoupledRun.apply(phi0, theta, case, int(nsteps), int(ckpt_every), u0, store_bytes)
 
 
+def region_volume(phi, labels, region):
+    """Phase volume sum(phi) over the nodes whose label is `region` (the
+    droplet volumes of Fig. 3b): a linear objective of phi for the reverse
+    mode.  phi: [ny][nx] tensor; labels: [ny][nx] integer array or tensor."""
+    lab = torch.as_tensor(labels, device=phi.device)
+    return (phi * (lab == region).to(phi.dtype)).sum()
+
+
 def taylor_deformation(phi):
     """Taylor deformation D = (L - B)/(L + B) of a droplet from the second
     moments of phi about its centroid (L, B: semi-axes of the ellipse with
