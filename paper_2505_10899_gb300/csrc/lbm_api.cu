@@ -178,8 +178,8 @@ Layout make_layout(const lbm_params* c, int n, int n_items, int total_regions) {
   off = align_up(off + (size_t)std::max(total_regions, n * lbmk::kMaxRegions) * sizeof(double));
   int64_t maxp = 0;
   for (int k = 0; k < n; ++k) maxp = std::max<int64_t>(maxp, (int64_t)c[k].nx * c[k].ny);
-  L.staging = off;  // slots of 4 planes, two for a batch: lbm_init alternates them
-  off = align_up(off + (size_t)maxp * (n > 1 ? 8 : 4) * sizeof(double));
+  L.staging = off;
+  off = align_up(off + (size_t)maxp * 4 * sizeof(double));
   L.f.resize(n);
   L.g.resize(n);
   L.glo.resize(n);
@@ -641,64 +641,64 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   if (rc) return cleanup(rc);
 
   const bool vortex = h->flow == LBM_FLOW_VORTEX;
-  // The initial fields pass through two staging slots in turn: a slot is
-  // reused only after the init kernel that read it has finished (an event),
-  // so uploads and init kernels of consecutive cases queue without a host
-  // round trip per case.  One synchronisation at the end: on return the
-  // host buffers are no longer read.
-  int64_t maxp = 0;
-  for (int k = 0; k < ncases; ++k) maxp = std::max<int64_t>(maxp, (int64_t)cases[k].nx * cases[k].ny);
-  cudaEvent_t slot_free[2] = {nullptr, nullptr};
-  auto drop_events = [&]() {
-    for (auto& ev : slot_free)
-      if (ev) cudaEventDestroy(ev);
+  // The initial fields of each case go straight into that case's buffer of
+  // parity 1 (f planes, or g planes without hydrodynamics), which the init
+  // kernel does not write and the first step overwrites.  The uploads run on
+  // a second stream, so that the upload of one case overlaps the (FP64)
+  // init kernel of the one before; each init waits for its own upload on an
+  // event.  One synchronisation at the end: on return the host buffers are
+  // no longer read.
+  const size_t es = elem_size(h->precision);
+  cudaStream_t up = nullptr;
+  cudaEvent_t ev[8] = {};
+  auto release = [&]() {
+    if (up) cudaStreamSynchronize(up);
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+    if (up) cudaStreamDestroy(up);
   };
-  for (auto& ev : slot_free)
-    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
-      ev = nullptr;
-      drop_events();
-      return cleanup(fail(LBM_ERR_CUDA, "event create failed"));
-    }
+  bool ok = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) == cudaSuccess;
+  for (auto& e : ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  // the uploads start after what the caller's stream already holds
+  ok = ok && cudaEventRecord(ev[0], h->stream) == cudaSuccess &&
+       cudaStreamWaitEvent(up, ev[0], 0) == cudaSuccess;
+  if (!ok) {
+    release();
+    return cleanup(fail(LBM_ERR_CUDA, "upload stream set-up failed"));
+  }
   for (int k = 0; k < ncases; ++k) {
     const lbm_params& p = cases[k];
     const int64_t n = (int64_t)p.nx * p.ny;
-    double* st = h->staging + (k & 1) * 4 * maxp;
-    if (k >= 2 && cudaEventSynchronize(slot_free[k & 1]) != cudaSuccess) {
-      drop_events();
-      return cleanup(fail(LBM_ERR_CUDA, "init sync failed"));
-    }
-    if (cudaMemcpyAsync(st, h_phi0[k], n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-    {
-      drop_events();
-      return cleanup(fail(LBM_ERR_CUDA, "phi0 upload failed"));
-    }
+    const size_t pb = (size_t)h->L.plane[k] * es;
+    double* st = (double*)(h->ws + (vortex ? h->L.g[k] : h->L.f[k]) + 9 * pb);
     const double* u0d = nullptr;
-    if (!vortex && h_u0 && h_u0[k]) {
-      if (cudaMemcpyAsync(st + n, h_u0[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
-      {
-        drop_events();
-        return cleanup(fail(LBM_ERR_CUDA, "u0 upload failed"));
-      }
+    cudaError_t e = cudaMemcpyAsync(st, h_phi0[k], n * sizeof(double), cudaMemcpyHostToDevice, up);
+    if (e == cudaSuccess && !vortex && h_u0 && h_u0[k]) {
+      e = cudaMemcpyAsync(st + n, h_u0[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice, up);
       u0d = st + n;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[k & 7], up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, ev[k & 7], 0);
+    if (e != cudaSuccess) {
+      release();
+      return cleanup(fail(LBM_ERR_CUDA, "initial-field upload failed"));
     }
     const double beta4 = 4.0 * (12.0 * p.sigma / p.W), kappa = 1.5 * p.sigma * p.W;
     const double rho_g = vortex ? 1.0 : p.rho_g, drho = vortex ? 0.0 : p.rho_l - p.rho_g;
-    cudaError_t e;
     if (h->precision == LBM_F32)
       e = lbmk::launch_init<float>(h->cf[k], beta4, kappa, p.lambda, rho_g, drho, st, u0d,
                                    vortex, p.vortex_U, 0, h->stream);
     else
       e = lbmk::launch_init<double>(h->cd[k], beta4, kappa, p.lambda, rho_g, drho, st, u0d,
                                     vortex, p.vortex_U, 0, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(slot_free[k & 1], h->stream);
     if (e != cudaSuccess) {
-      drop_events();
+      release();
       return cleanup(fail(LBM_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e)));
     }
   }
-  const cudaError_t es = cudaStreamSynchronize(h->stream);
-  drop_events();
-  if (es != cudaSuccess) return cleanup(fail(LBM_ERR_CUDA, "init sync failed"));
+  const cudaError_t es2 = cudaStreamSynchronize(h->stream);
+  release();
+  if (es2 != cudaSuccess) return cleanup(fail(LBM_ERR_CUDA, "init sync failed"));
   *out = h;
   return LBM_OK;
 }
