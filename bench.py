@@ -688,7 +688,7 @@ def adjoint_timing(dev, nx=512, ny=256, nsteps=32, ckpt=8):
 
 
 def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
-    """The sheared droplet of configs[3] (512 x 256 channel, walls at -U and
+    """The sheared droplet in a 512 x 256 channel (walls at -U and
     +U = 0.01, R = 40, W = 4, Ca = 0.1, Re = 0.1): FP32 forward MLUPS over
     nsteps (register-pipelined kernel with walls), the Taylor deformation D
     after nsteps in FP32 and FP64, and the checkpointed FP64 reverse mode of

@@ -230,7 +230,8 @@ def random_state3(nx, ny, nz, seed, phi_lo=-0.05, phi_hi=1.05):
 
 def shear_droplet(nx=512, ny=256, R=40.0, U=0.01, Ca=0.1, Re=0.1, W=4.0, tau_g=0.8,
                   lam=0.5, rho_ratio=1.0):
-    """A droplet in the sheared cavity of Sec. 4.4 (configs[3]): walls below
+    """A droplet in the sheared cavity of Sec. 4.4 (the 512 x 256 channel by
+    default): walls below
     y = 0 and above y = ny - 1 moving at -U and +U, droplet of radius R at the
     centre, equal kinematic viscosities.  Shear rate G = 2U/ny; the viscosity
     and surface tension follow from Re = G R^2 / nu and Ca = rho nu G R / sigma.
