@@ -177,10 +177,12 @@ int lbm_get_tiling(const lbm_handle* h, int32_t* bx, int32_t* rows,
 int lbm_set_tiling(lbm_handle* h, int32_t bx, int32_t rows);
 
 /* Self-tuning: time every (kernel variant, bx, rows) candidate on this
- * batch with `trials` trial launches each (CUDA events on the handle's
- * stream) and keep the fastest.  Trial launches read the current state and
- * write only the buffers the next step overwrites, so the state and the step
- * index do not change.  Outputs may be NULL.  Synchronises. */
+ * batch with max(trials, 8) trial steps each (CUDA events on the handle's
+ * stream) and keep the fastest.  The step kernels of variants 1 and 2 are
+ * timed as a captured CUDA graph of those steps, as lbm_step replays them;
+ * variant 3 as one persistent launch.  Trial launches read the current
+ * state and write only the buffers the next step overwrites, so the state
+ * and the step index do not change.  Outputs may be NULL.  Synchronises. */
 int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel,
                  int32_t* best_bx, int32_t* best_rows, double* best_ms);
 

@@ -235,7 +235,7 @@ def test_tiling_does_not_change_results(L, variant):
     u0 = np.zeros((2, 90, 200))
     u0[0] = 0.01
     ref = None
-    for bx, rows in [(32, 2), (64, 17), (128, 64), (128, 3)]:
+    for bx, rows in [(32, 2), (64, 17), (128, 64), (128, 3), (128, 2), (64, 2)]:
         for prec in ("f32",):
             s = L.Sim(case, phi0, u0, precision=prec)
             s.set_kernel(variant)
