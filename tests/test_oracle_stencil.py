@@ -44,3 +44,21 @@ def test_second_order_convergence():
     order = np.log2(e1 / e2)
     assert np.all(order > 1.9) and np.all(order < 2.1), order
     assert np.all(e2 < 1e-2)
+
+
+def test_interface_gradient_of_psi_is_far_above_the_ridge_cut():
+    # psi of Eq. 14 is a signed distance: across the interface band of a
+    # resolved droplet its isotropic gradient is close to 1, so the cut of the
+    # normal at |grad psi| < 0.1 touches only the saturated bulk and the
+    # ridge at the centre (nodes-centred and off-node droplets, R = 6 and 12).
+    import numpy as np
+    import oracle
+    import workloads as W
+    for R, cx in ((12.0, 32.0), (6.0, 32.0), (12.0, 32.4)):
+        phi = W.tanh_disc(64, 64, cx, 32.0, R, 4.0, periodic=True)
+        psi = np.vectorize(lambda p: oracle.psi(p, 4.0, 1e-10))(phi)
+        gx, gy, _ = oracle.stencil(psi)
+        g = np.hypot(gx, gy)
+        band = (phi > 0.01) & (phi < 0.99)
+        assert g[band].min() > 0.9
+        assert (phi[g < 0.1] * (1 - phi[g < 0.1])).max() < 1e-2
