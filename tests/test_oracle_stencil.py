@@ -50,7 +50,7 @@ def test_interface_gradient_of_psi_is_far_above_the_ridge_cut():
     # psi of Eq. 14 is a signed distance: across the interface band of a
     # resolved droplet its isotropic gradient is close to 1, so the cut of the
     # normal at |grad psi| < 0.1 touches only the saturated bulk and the
-    # ridge at the centre (nodes-centred and off-node droplets, R = 6 and 12).
+    # ridge at the centre (node-centred and off-node droplets, R = 6 and 12).
     import numpy as np
     import oracle
     import workloads as W
