@@ -32,7 +32,7 @@
 /* |grad(psi)| below which n of Eq. 17 is 0. */
 #define NORMAL_MIN 0.1
 
-/* ORC_PLANT (11-20) selects a deliberately wrong variant of one formula, for
+/* ORC_PLANT (11-20, 23) selects a deliberately wrong variant of one formula, for
  * the mutation test of the pins only; 0 (the default) is the method. */
 #ifndef ORC_PLANT
 #define ORC_PLANT 0
@@ -315,7 +315,11 @@ int orc3_step(const orc3_params *p, double *f, double *g, double *j, int64_t nst
 #endif
           }
           double g2 = m.gs[0] * m.gs[0] + m.gs[1] * m.gs[1] + m.gs[2] * m.gs[2];
+#if ORC_PLANT == 23
+          if (g2 != 0.0)
+#else
           if (g2 >= NORMAL_MIN * NORMAL_MIN)
+#endif
             for (int a = 0; a < 3; ++a) nn[a] = m.gs[a] / sqrt(g2);
           double ge[7], Gi[7];
           orc3_geq(phi, m.mu, p->lambda, m.u, ge);

@@ -51,6 +51,7 @@ PLANTS3 = {
     18: "wrong face-diagonal weight in the stencils (Sec. 3.2)",
     19: "g streamed against c_z",
     20: "tau_f from mu(phi)/rho_l instead of mu(phi)/rho(phi) (Eq. 27)",
+    23: "unit normal of Eq. 17 down to |grad psi| = 0 (no ridge cut)",
 }
 
 
