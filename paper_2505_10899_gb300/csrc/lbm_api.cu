@@ -596,8 +596,9 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   h->total_regions = ncases;
   h->L = make_layout(cases, ncases, max_items(cases, ncases), ncases * lbmk::kMaxRegions);
   if (ws_bytes < h->L.total) {
+    const size_t need = h->L.total;
     delete h;
-    return fail(LBM_ERR_WORKSPACE, "workspace too small: need " + std::to_string(h->L.total));
+    return fail(LBM_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need));
   }
   h->ws = (char*)d_workspace;
   h->ws_bytes = ws_bytes;

@@ -96,6 +96,8 @@ def test_init_rejects_bad_workspace_without_touching_the_device(L):
     with pytest.raises(L.LbmError) as e:
         L.lbm_init([p], 0x1000, 16, [phi])            # too small
     assert e.value.status == L.LBM_ERR_WORKSPACE
+    # the message states the size that is needed
+    assert f"need {L.lbm_workspace_bytes([p])}" in str(e.value)
 
 
 def test_status_strings(L):
