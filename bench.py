@@ -630,6 +630,7 @@ def adjoint_timing(dev, nx=512, ny=256, nsteps=32, ckpt=8):
     case = W.base_case(nx, ny)
     phi0 = W.tanh_disc(nx, ny, nx / 2, ny / 2, 40.0, 4.0, periodic=True)
     s = A.AdjointSim(case, phi0)
+    s.sim.autotune(1)  # the forward step of the comparison: the fastest kernel
     stream = s.sim.stream
 
     def timed(fn, n):
@@ -703,6 +704,7 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
            "steps": nsteps}
     for prec in ("f32", "f64"):
         s = lbm.Sim(case, phi0, u0, precision=prec)
+        s.autotune(1)
         s.step(3)
         torch.cuda.synchronize(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -713,6 +715,7 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
         ms = a.elapsed_time(b) / (nsteps - 3)
         phi = torch.as_tensor(s.fields(0)[0])
         out[prec] = {"mlups": round(512 * 256 / (ms * 1e-3) / 1e6, 1),
+                     "tiling": {"bx": s.tiling()[0], "rows": s.tiling()[1]},
                      "kernel": {1: "step_kernel", 3: "step_kernel_persistent"}.get(s.kernel(),
                                                                                     "?"),
                      "taylor_D": float(A.taylor_deformation(phi)),

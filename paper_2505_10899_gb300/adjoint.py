@@ -125,9 +125,11 @@ def _stored_steps(nsteps, state_bytes, store_bytes, dev):
 
 class CoupledRun(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, phi0, theta, case, nsteps, ckpt_every, u0, store_bytes):
+    def forward(ctx, phi0, theta, case, nsteps, ckpt_every, u0, store_bytes, tune):
         th = theta.detach().cpu().numpy().astype(np.float64)
         asim = AdjointSim(case_with(case, th), phi0.detach().cpu().numpy(), u0)
+        if (nsteps >= 1000) if tune is None else bool(tune):
+            asim.sim.autotune(1)  # the forward and the recomputation step with the fastest kernel
         state_bytes = 20 * 8 * asim.shape[0] * asim.shape[1]
         m = _stored_steps(nsteps, state_bytes, store_bytes, asim.dev)
         t_rec = nsteps - m  # states S_t, t in [t_rec, nsteps), stay on the device
@@ -180,14 +182,18 @@ class CoupledRun(torch.autograd.Function):
         gtheta = torch.as_tensor(grads[:ctx.ntheta], dtype=ctx.theta_dtype,
                                  device=ctx.theta_device)
         dphi0 = dphi0.to(device=ctx.phi0_device, dtype=ctx.phi0_dtype)
-        return dphi0, gtheta, None, None, None, None, None
+        return dphi0, gtheta, None, None, None, None, None, None
 
 
-def coupled_run(phi0, theta, case, nsteps, ckpt_every=16, u0=None, store_bytes=None):
+def coupled_run(phi0, theta, case, nsteps, ckpt_every=16, u0=None, store_bytes=None,
+                tune=None):
     """phi after nsteps coupled steps, differentiable in phi0 and theta.
     store_bytes bounds the device memory for recorded states (None: a
-    quarter of the free memory; 0: checkpoints and recomputation only)."""
-    return CoupledRun.apply(phi0, theta, case, int(nsteps), int(ckpt_every), u0, store_bytes)
+    quarter of the free memory; 0: checkpoints and recomputation only).
+    tune: autotune the stepping kernel first (None: for runs of 1000 steps
+    or more, where it pays for its trial steps)."""
+    return CoupledRun.apply(phi0, theta, case, int(nsteps), int(ckpt_every), u0, store_bytes,
+                            tune)
 
 
 def region_volume(phi, labels, region):
