@@ -646,12 +646,16 @@ __global__ void ad_seed_phi(const double* __restrict__ dphi, int nx, int ny, int
 
 // Adds this sweep's parameter partials (in block order) to the device
 // accumulator `acc`, which lbm_adjoint_take_param_grads reads and clears.
+// Deterministic sum of the per-block partials (launch: one block of
+// 32 * kNParam threads): warp q sums parameter q, lane l the blocks
+// l, l + 32, ... in order, then a fixed shuffle tree.
 __global__ void ad_sum_partials(const double* __restrict__ part, int nb, double* __restrict__ acc) {
-  const int q = threadIdx.x;
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= kNParam) return;
   double v = 0.0;
-  for (int b = 0; b < nb; ++b) v += part[(int64_t)b * kNParam + q];
-  acc[q] += v;
+  for (int b = lane; b < nb; b += 32) v += part[(int64_t)b * kNParam + q];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) acc[q] += v;
 }
 
 // Scratch layout inside the caller's adjoint workspace (doubles).
@@ -800,7 +804,7 @@ int adjoint_step_impl(lbm_handle* h, const double* fA, const double* gA, const d
   ad_node<<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
   ad_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.lP, s.lQ, p.nx, p.ny, p.walls,
                                                      p.xi, (double*)d_adj_out);
-  ad_sum_partials<<<1, 32, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
+  ad_sum_partials<<<1, 32 * kNParam, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   if (h_param_grads) return take_grads(h, h_param_grads);
@@ -864,7 +868,7 @@ int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
   ad_init_local<<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
   ad_init_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.psi, p.nx, p.ny, p.walls,
                                                           d_adj_phi0);
-  ad_sum_partials<<<1, 32, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
+  ad_sum_partials<<<1, 32 * kNParam, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   if (h_param_grads) return take_grads(h, h_param_grads);
