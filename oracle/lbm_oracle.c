@@ -62,7 +62,7 @@
 #define M_PI 3.14159265358979323846
 #endif
 
-/* ORC_PLANT (1-10, 21-22) selects a deliberately wrong variant of one formula, for the
+/* ORC_PLANT (1-10, 21-22, 24-27) selects a deliberately wrong variant of one formula, for the
  * mutation test that shows the pins catch it (0 = the oracle as written). */
 #ifndef ORC_PLANT
 #define ORC_PLANT 0
@@ -312,10 +312,24 @@ void orc_stencil(const double *chi, int32_t nx, int32_t ny, double *gx,
 /* Prescribed single-vortex velocity (Eqs. 43-44, reading in the header). */
 static void vortex_u(const orc_params *p, int x, int y, int64_t t, double *ux,
                      double *uy) {
+#if ORC_PLANT == 26
+  double X = (double)x / p->nx, Y = (double)y / p->ny;
+#elif ORC_PLANT == 25
+  double Y = (x + 0.5) / p->nx, X = (y + 0.5) / p->ny;
+#else
   double X = (x + 0.5) / p->nx, Y = (y + 0.5) / p->ny;
+#endif
+#if ORC_PLANT == 24
+  double ct = cos(2.0 * M_PI * (double)t / p->vortex_T);
+#else
   double ct = cos(M_PI * (double)t / p->vortex_T);
+#endif
   double sx = sin(M_PI * X), sy = sin(M_PI * Y);
+#if ORC_PLANT == 27
+  *ux = -p->vortex_U * sx * sin(2.0 * M_PI * Y) * ct;
+#else
   *ux = -p->vortex_U * sx * sx * sin(2.0 * M_PI * Y) * ct;
+#endif
   *uy = p->vortex_U * sy * sy * sin(2.0 * M_PI * X) * ct;
 }
 

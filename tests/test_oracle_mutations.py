@@ -23,10 +23,14 @@ PLANTS = {
     10: "sign of the sharpening flux flipped (Eq. 32)",
     21: "sign of the moving-wall momentum term flipped (halfway bounce-back)",
     22: "periodic ghost row at the walls instead of the mirrored one",
+    24: "cos(2 pi t/T) for the time factor of the single vortex (Eqs. 43-44)",
+    25: "X and Y swapped in the single vortex (Eqs. 43-44)",
+    26: "single-vortex coordinates x/L without the half-node offset (Eqs. 43-44)",
+    27: "sin instead of sin^2 in the single vortex's u (Eq. 43)",
 }
 PIN_FILES = ["tests/test_oracle_lattice.py", "tests/test_oracle_node.py",
              "tests/test_oracle_stencil.py", "tests/test_oracle_physics.py",
-             "tests/test_oracle_walls.py"]
+             "tests/test_oracle_walls.py", "tests/test_oracle_vortex.py"]
 
 
 @pytest.mark.parametrize("plant", sorted(PLANTS), ids=lambda k: f"plant{k}")
