@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
     ap.add_argument("--ncases", type=int, default=512)
+    ap.add_argument("--partition", action="store_true",
+                    help="N > 1: split one batch over the ranks instead of one batch per rank")
     ap.add_argument("--seed", type=int, default=2026)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -61,6 +63,8 @@ def parse():
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 register, 2 bulk-copy")
     ap.add_argument("--tiling", type=str, default=None, help="BX,ROWS (default: autotuned)")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--chains", type=int, default=0,
+                    help="independent case groups as parallel graph branches (0: library default)")
     ap.add_argument("--only-3d", action="store_true",
                     help="only the 3-D Rayleigh-Plateau numbers (D3Q19 + D3Q7)")
     ap.add_argument("--grid3", type=str, default="256,256,1024", help="NX,NY,NZ of the 3-D box")
@@ -114,6 +118,45 @@ def whole_job_mlups(world_size, nodes_per_rank, steps, t_max_ms):
 def rank_cases(args, rank):
     """Each rank owns an independent batch (seeded by rank)."""
     return W.batched_droplets(args.ncases, seed=args.seed + 7919 * rank)
+
+
+def partition_cases(cases, world, rank):
+    """Indices of the cases that rank `rank` advances when one batch is split
+    over `world` ranks (--partition): cases taken largest first, each dealt
+    to the rank with the fewest nodes so far (ties to the lowest rank), so
+    the ranks' node counts differ by at most one case."""
+    order = sorted(range(len(cases)), key=lambda i: (-cases[i]["nx"] * cases[i]["ny"], i))
+    load = [0] * world
+    mine = []
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        load[r] += cases[i]["nx"] * cases[i]["ny"]
+        if r == rank:
+            mine.append(i)
+    return sorted(mine)
+
+
+def gather_case_volumes(pg, idx, vols, ncases, device):
+    """The per-case FP64 volumes of all ranks, in case order (all-gather of
+    (index, volume) pairs, padded to the longest list)."""
+    import torch
+    n = torch.tensor([len(idx)], dtype=torch.int64, device=device)
+    sizes = [torch.zeros_like(n) for _ in range(pg.get_world_size())]
+    pg.all_gather(sizes, n)
+    m = int(max(int(x.item()) for x in sizes))
+    buf = torch.full((m, 2), -1.0, dtype=torch.float64, device=device)
+    if len(idx):
+        buf[:len(idx), 0] = torch.tensor(idx, dtype=torch.float64)
+        buf[:len(idx), 1] = torch.as_tensor(np.asarray(vols, dtype=np.float64))
+    out = [torch.empty_like(buf) for _ in range(pg.get_world_size())]
+    pg.all_gather(out, buf)
+    full = np.full(ncases, np.nan)
+    for t in out:
+        t = t.cpu().numpy()
+        for k, v in t:
+            if k >= 0:
+                full[int(k)] = v
+    return full
 
 
 def host_inputs(cases):
@@ -221,13 +264,22 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream(device=dev)
-    cases = rank_cases(args, rank)
+    if args.partition:
+        # one batch split over the ranks (strong scaling)
+        all_cases = rank_cases(args, 0)
+        mine = partition_cases(all_cases, ws, rank)
+        cases = [all_cases[i] for i in mine]
+        total_nodes = sum(c["nx"] * c["ny"] for c in all_cases)
+    else:
+        cases = rank_cases(args, rank)
     nodes = sum(c["nx"] * c["ny"] for c in cases)
     phis, us = host_inputs(cases)
 
     with torch.cuda.stream(stream):
         sim = lbm.Sim(cases, phis, us, precision=args.precision, stream=stream)
         sim.set_kernel(args.kernel)
+        if args.chains:
+            sim.set_chains(args.chains)
         tuned = None
         if args.tiling:
             bx, rows = (int(v) for v in args.tiling.split(","))
@@ -237,12 +289,15 @@ def run_ours(args):
         vol = sim.track_volume(True)
         v0 = None
         sim.step(max(args.warmup, 3))
+        K = args.steps
+        # capture the step graphs of the timed call now (no step runs)
+        sim.prepare(K)
         stream.synchronize()
         v0 = vol.clone()
 
         # ---------------- timed region ----------------
-        K = args.steps
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        # one lbm_step(K) call: graphs of up to 64 steps, one branch per chain
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         sampler = ClockSampler(local) if rank == 0 else None
         if pg:
             pg.barrier()
@@ -251,26 +306,30 @@ def run_ours(args):
             sampler.start()
             time.sleep(0.4)
         ev[0].record(stream)
-        for k in range(K):
-            sim.step(1)
-            ev[k + 1].record(stream)
+        sim.step(K)
+        ev[1].record(stream)
         stream.synchronize()
         torch.cuda.synchronize(dev)
         if pg:
             pg.barrier()
         clocks = sampler.stop() if sampler else None
-        step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(K)]
-        total_ms = ev[0].elapsed_time(ev[K])
+        total_ms = ev[0].elapsed_time(ev[1])
         status = sim.status()
+        nchains = sim.chains()
         vend = vol.clone().cpu().numpy()
         drift = float(np.max(np.abs(vend / v0.cpu().numpy() - 1.0)))
 
     t_max = max_over_ranks(pg, total_ms, dev) if pg else total_ms
-    value = whole_job_mlups(ws, nodes, K, t_max)
+    if args.partition:
+        value = total_nodes * K / (t_max * 1e-3) / 1e6
+        vols_all = gather_case_volumes(pg, mine, vend, len(all_cases), dev) if pg else vend
+    else:
+        value = whole_job_mlups(ws, nodes, K, t_max)
 
-    # kernel duration: each per-step event pair brackets the step kernel plus
-    # the volume finalisation and clock kernels (a few microseconds)
-    kms = float(np.mean(step_ms))
+    # time per step: the K steps run as graphs whose branches (one per chain)
+    # each hold the step kernel and the volume finalisation of their cases,
+    # plus one clock kernel per graph
+    kms = total_ms / K
     bpn = BYTES_PER_NODE[args.precision]
     achieved = bpn * nodes / (kms * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
@@ -286,7 +345,7 @@ def run_ours(args):
         "warmup": args.warmup,
         "ms_per_step": round(t_max / K, 4),
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if args.partition else "weak",
         "vs_baseline": None,
         "dtype": "f32" if args.precision == "f32" else "f64",
         "data": "synthetic (seeded tanh droplets; no dataset in the paper)",
@@ -294,8 +353,14 @@ def run_ours(args):
                    "precision": args.precision, "volume_sums": "f64, fused, every step",
                    "l2": "inputs larger than L2 (%.1f GB of state)" % (
                        sim.ws_bytes / 1e9),
-                   "parallelism": f"independent batches, {ws} rank(s)",
-                   "tiling": "strip/run work items, one launch per step for all cases"},
+                   "parallelism": (f"one batch of {args.ncases} cases split over {ws} "
+                                   "rank(s), balanced by nodes; per-case volumes all-gathered"
+                                   if args.partition else
+                                   f"independent batches, {ws} rank(s)"),
+                   "chains": nchains,
+                   "tiling": "strip/run work items; the cases in %d chains, each chain one "
+                             "step-kernel launch per step, chains as parallel CUDA-graph "
+                             "branches" % nchains},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                      "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "traffic_source": traffic_kind,
@@ -308,10 +373,14 @@ def run_ours(args):
                      "algorithmic_bytes_per_node": bpn, "peak_kind": peak_kind,
                      "kernel_ms": round(kms, 4)},
         "clocks": clocks,
-        "gpu_launches": 3 * K,
+        "gpu_launches": 2 * nchains * K + (K + 63) // 64,
         "status": status,
         "volume_drift_rel": drift,
     }
+    if args.partition:
+        result["partition"] = {"cases_this_rank": len(cases), "nodes_this_rank": nodes,
+                               "volumes_gathered": int(np.isfinite(vols_all).sum()),
+                               "ncases": len(all_cases)}
     e2e_tiling = tuple(sim.tiling()[:2])
     sim.close()
     del sim
@@ -320,7 +389,10 @@ def run_ours(args):
     if rank == 0 and not args.no_e2e:
         result["e2e"] = run_e2e(args, cases, phis, us, dev, K, tiling=e2e_tiling)
     if rank == 0 and not args.no_extras:
-        result["extras"] = run_extras(args, cases, dev)
+        ex = run_extras(args, cases, dev)
+        result["extras"] = ex
+        # the secondary headline ratios, also at the top level of the line
+        result.update(headline_ratios(ex))
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(cases, args.cpu_seconds)
     if pg:
@@ -329,6 +401,85 @@ def run_ours(args):
         print(json.dumps(result), flush=True)
     if pg:
         pg.destroy_process_group()
+
+
+def fp64_peak(dev):
+    """Measured FP64 FMA rate of this GPU (lbm_fp64_fma_rate: 8 independent
+    FMA chains per thread, 4 CTAs of 256 threads per SM), timed for about
+    0.4 s with the SM clock sampled meanwhile."""
+    from paper_2505_10899_gb300 import lbm
+    import torch
+    _, ms = lbm.lbm_fp64_fma_rate(2000, 4)
+    trips = max(2000, int(2000 * 400.0 / max(ms, 1e-3)))
+    smp = ClockSampler(dev.index if dev.index is not None else 0)
+    smp.start()
+    time.sleep(0.3)
+    rate, ms = lbm.lbm_fp64_fma_rate(trips, 4)
+    clocks = smp.stop()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    per_clk = None
+    if clocks.get("sm_mhz"):
+        per_clk = rate / (clocks["sm_mhz"] * 1e6 * sms)
+    return {"fma_per_s": rate, "tflops": round(2 * rate / 1e12, 4), "timed_ms": round(ms, 2),
+            "sms": sms, "fma_per_clock_per_sm": per_clk, "clocks": clocks,
+            "how": "lbm_fp64_fma_rate: 8 independent FMA chains per thread, "
+                   "4 x 256 threads per SM, CUDA events"}
+
+
+def fp64_roofline(tag, nodes, ms_per_launch, peak):
+    """FP64 launches are bound by the FP64 pipe, not by HBM: achieved = FP64
+    pipe instructions per node (warp instructions x 32 from the committed
+    ncu summary, which also gives the pipe's busy fraction) x nodes / the
+    launch time, against the measured FMA rate (one FP64 pipe instruction
+    per FMA)."""
+    path = os.path.join(ROOT, "profiles", f"{tag}.md")
+    per_node = None
+    pipe = None
+    if os.path.exists(path):
+        txt = open(path).read()
+        m = re.search(r"fp64_pipe_inst_per_node:\s*([0-9.]+)", txt)
+        per_node = float(m.group(1)) if m else None
+        m = re.search(r"fp64_pipe_busy_pct:\s*([0-9.]+)", txt)
+        pipe = float(m.group(1)) if m else None
+    if per_node is None:
+        return {"bound": "fp64_alu", "achieved": None, "peak": peak["fma_per_s"] / 1e9,
+                "unit": "G FP64 inst/s", "frac": None, "note": "no committed instruction count"}
+    ach = per_node * nodes / (ms_per_launch * 1e-3) / 1e9
+    pk = peak["fma_per_s"] / 1e9
+    return {"bound": "fp64_alu", "achieved": round(ach, 2), "peak": round(pk, 2),
+            "unit": "G FP64 inst/s", "frac": round(ach / pk, 4),
+            "fp64_inst_per_node": per_node, "ncu_fp64_pipe_busy_pct": pipe,
+            "peak_kind": "measured (lbm_fp64_fma_rate)"}
+
+
+def headline_ratios(ex):
+    """Compact copies of the secondary ratios the metric names: batching
+    against separate per-case launches, the adjoint step against the forward
+    step, the whole reverse-mode gradient against the forward run (FP64 and
+    FP32), and the FP64 step against the FP64 pipe's measured peak."""
+    out = {}
+
+    def get(*path):
+        o = ex
+        for k in path:
+            if not isinstance(o, dict) or k not in o:
+                return None
+            o = o[k]
+        return o
+
+    out["batching_speedup_vs_launch_per_case"] = get(
+        "batching", "speedup_vs_launch_per_case_per_step")
+    out["batching_speedup_vs_graph_per_case"] = get("batching", "speedup_vs_graph_per_case")
+    out["adjoint_step_over_forward"] = get("adjoint", "vjp_over_forward")
+    out["adjoint_backward_over_forward_recorded"] = get(
+        "adjoint", "backward_states_recorded", "backward_over_forward_step")
+    out["gradient_over_forward_f64"] = get("shear_droplet", "gradient_f64",
+                                           "backward_over_plain_forward")
+    out["gradient_over_forward_f32"] = get("shear_droplet", "gradient_f32",
+                                           "backward_over_plain_forward")
+    out["fp64_step_fp64_pipe_frac"] = get("f64_first64cases", "roofline", "frac")
+    out["fp64_peak_tflops"] = get("fp64_peak", "tflops")
+    return out
 
 
 def sim_bx(sim):
@@ -403,6 +554,7 @@ def run_extras(args, cases, dev):
         return a.elapsed_time(b)
 
     out = {}
+    out["fp64_peak"] = fp64_peak(dev)
     sub = cases[:64]
     nodes = sum(c["nx"] * c["ny"] for c in sub)
     phis, us = host_inputs(sub)
@@ -410,9 +562,16 @@ def run_extras(args, cases, dev):
         s = lbm.Sim(sub, phis, us, precision=prec)
         s.autotune(1)
         s.step(3)
+        s.prepare(20)
         torch.cuda.synchronize(dev)
         ms = timed(s, 20)
         out[f"{prec}_mlups_first64cases"] = round(nodes * 20 / (ms * 1e-3) / 1e6, 1)
+        if prec == "f64":
+            out["f64_first64cases"] = {
+                "mlups": out["f64_mlups_first64cases"], "ms_per_step": round(ms / 20, 4),
+                "tiling": list(s.tiling()[:2]), "kernel": s.kernel(),
+                "roofline": fp64_roofline("coupled_step_f64_batched16", nodes, ms / 20,
+                                          out["fp64_peak"])}
         s.close()
     # FP32 vs FP64 on the two-droplet case (128x64, 100 steps)
     case, phi0, u0, _, _ = W.two_droplets(noise=1e-3)
@@ -445,7 +604,7 @@ def run_extras(args, cases, dev):
     out["batching"] = batching_timing(cases, dev)
     out["droplet_lattice_16384x8192"] = lattice_timing(dev)
     out["adjoint"] = adjoint_timing(dev)
-    out["rayleigh_plateau_3d"] = rp3d_timing(dev, steps=args.steps3)
+    out["rayleigh_plateau_3d"] = rp3d_timing(dev, steps=args.steps3, peak64=out["fp64_peak"])
     out["shear_droplet"] = shear_timing(dev)
     return out
 
@@ -550,7 +709,7 @@ def lattice_timing(dev, steps=50, grid=(16384, 8192), tiling=None):
 
 
 def rp3d_timing(dev, grid=(256, 256, 1024), precisions=("f32", "f16", "f64"), steps=50,
-                tiling=None):
+                tiling=None, peak64=None):
     """3-D Rayleigh-Plateau column (D3Q19 flow + D3Q7 phase field, SRT limit of
     the model): MLUPS per storage precision in the autotuned launch with its
     HBM roofline, the phase-volume drift over the timed steps, and the largest
@@ -613,6 +772,14 @@ def rp3d_timing(dev, grid=(256, 256, 1024), precisions=("f32", "f16", "f64"), st
             "phi_maxdiff_vs_f64_20steps": err,
             "status": s.status(),
         }
+        if prec == "f64":
+            # FP64 is bound by the FP64 pipe: that is the roofline; the HBM
+            # fraction stays beside it for reference
+            if peak64 is None:
+                peak64 = fp64_peak(dev)
+            hbm = out[prec]["roofline"]
+            out[prec]["roofline"] = fp64_roofline("rp3d_step_f64_128x128x256", n, ms, peak64)
+            out[prec]["roofline"]["hbm_frac"] = hbm["frac"]
         s.close()
         del s
         torch.cuda.empty_cache()
@@ -692,9 +859,10 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
     """The sheared droplet in a 512 x 256 channel (walls at -U and
     +U = 0.01, R = 40, W = 4, Ca = 0.1, Re = 0.1): FP32 forward MLUPS over
     nsteps (register-pipelined kernel with walls), the Taylor deformation D
-    after nsteps in FP32 and FP64, and the checkpointed FP64 reverse mode of
-    D(phi_T) with respect to (sigma, tau_g, U_w) with its cost relative to
-    the forward run (U_w moves both walls: dD/dU_w = dD/du_top - dD/du_bot)."""
+    after nsteps in FP32 and FP64, and the checkpointed reverse mode of
+    D(phi_T) with respect to (sigma, tau_g, U_w) in FP64 and in FP32, each
+    with its cost relative to the plain forward run of its own precision
+    (U_w moves both walls: dD/dU_w = dD/du_top - dD/du_bot)."""
     import torch
     from paper_2505_10899_gb300 import adjoint as A
     from paper_2505_10899_gb300 import lbm
@@ -743,33 +911,45 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
     # torch's own kernels
     A.taylor_deformation(torch.tensor(phi0, device=dev, requires_grad=True)).backward()
     torch.cuda.synchronize(dev)
-    th = torch.tensor([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"],
-                       case["u_top"], case["u_bot"]], dtype=torch.float64, requires_grad=True)
-    phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    # device memory for recorded states (the rest is recomputed): 128 GiB, at
-    # most half of what is free
-    store = min(128 << 30, torch.cuda.mem_get_info(dev)[0] // 2)
-    phiT = A.coupled_run(phi0_t, th, case, grad_steps, ckpt, u0=u0, store_bytes=store)
-    D = A.taylor_deformation(phiT)
-    torch.cuda.synchronize(dev)
-    t1 = time.perf_counter()
-    D.backward()
-    torch.cuda.synchronize(dev)
-    t2 = time.perf_counter()
-    g = th.grad.numpy()
-    out["gradient_f64"] = {"steps": grad_steps, "checkpoint_every": ckpt,
-                           "recorded_steps": min(grad_steps, store // (20 * 8 * 512 * 256)),
-                           "D": float(D.detach()),
-                           "dD_dsigma": float(g[0]), "dD_dtau_g": float(g[1]),
-                           "dD_dU_w": float(g[4] - g[5]),
-                           "forward_s": round(t1 - t0, 3), "backward_s": round(t2 - t1, 3),
-                           "backward_over_forward": round((t2 - t1) / (t1 - t0), 3),
-                           "backward_over_plain_forward": round(
-                               (t2 - t1) * out["f64"]["mlups"] * 1e6 / (grad_steps * 512 * 256), 3),
-                           "plain_f64_forward_s": round(grad_steps * 512 * 256
-                                                        / (out["f64"]["mlups"] * 1e6), 3)}
+    for prec in ("f64", "f32"):
+        torch.cuda.empty_cache()
+        th = torch.tensor([case["sigma"], case["tau_g"], case["lambda"], case["tau_f_l"],
+                           case["u_top"], case["u_bot"]], dtype=torch.float64, requires_grad=True)
+        phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        # device memory for recorded states (the rest is recomputed): 128 GiB,
+        # at most half of what is free
+        store = min(128 << 30, torch.cuda.mem_get_info(dev)[0] // 2)
+        phiT = A.coupled_run(phi0_t, th, case, grad_steps, ckpt, u0=u0, store_bytes=store,
+                             precision=prec)
+        D = A.taylor_deformation(phiT)
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        D.backward()
+        torch.cuda.synchronize(dev)
+        t2 = time.perf_counter()
+        g = th.grad.numpy()
+        state_bytes = (20 if prec == "f64" else 21) * (8 if prec == "f64" else 4) * 512 * 256
+        plain_s = grad_steps * 512 * 256 / (out[prec]["mlups"] * 1e6)
+        res = {"steps": grad_steps, "checkpoint_every": ckpt,
+               "recorded_steps": min(grad_steps, store // state_bytes),
+               "D": float(D.detach()),
+               "dD_dsigma": float(g[0]), "dD_dtau_g": float(g[1]),
+               "dD_dU_w": float(g[4] - g[5]),
+               "forward_s": round(t1 - t0, 3), "backward_s": round(t2 - t1, 3),
+               "backward_over_forward": round((t2 - t1) / (t1 - t0), 3),
+               "backward_over_plain_forward": round((t2 - t1) / plain_s, 3),
+               f"plain_{prec}_forward_s": round(plain_s, 3),
+               "adjoint_arithmetic": "fp64" if prec == "f64" else
+                                     "fp32 (parameter derivatives accumulated in fp64)"}
+        if prec == "f32":
+            ref = out["gradient_f64"]
+            res["rel_diff_vs_f64_gradient"] = {
+                k: round(abs(res[k] - ref[k]) / abs(ref[k]), 6)
+                for k in ("dD_dsigma", "dD_dtau_g", "dD_dU_w")}
+        out[f"gradient_{prec}"] = res
+        del phiT, D
     return out
 
 

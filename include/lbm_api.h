@@ -13,7 +13,8 @@
  *     (Sec. 3.1, Eqs. 20-29; target PDE Eq. 18) driven by F_s = hbar grad(phi),
  * with the isotropic gradient/Laplacian stencils of Sec. 3.2 for grad(phi),
  * lap(phi) and grad(psi), on the D2Q9 lattice of Eq. 19.  Lattice units:
- * dt = dx = 1, c_s^2 = 1/3.  The grid is periodic in x and y.
+ * dt = dx = 1, c_s^2 = 1/3.  The grid is periodic in x; in y it is
+ * periodic, or bounded by moving walls (lbm_params.walls).
  *
  * Conventions shared by every entry point
  *   - Return value: LBM_OK (0) or a negative LBM_ERR_* code.  No C++
@@ -59,7 +60,7 @@ enum {
   LBM_ERR_CUDA = -2,          /* a CUDA runtime call failed */
   LBM_ERR_WORKSPACE = -3,     /* workspace missing, too small or misaligned */
   LBM_ERR_NONFINITE = -4,     /* a NaN/Inf appeared in the macroscopic fields */
-  LBM_ERR_TIMEOUT = -5,       /* reserved: a bounded device wait gave up */
+  LBM_ERR_TIMEOUT = -5,       /* a bounded device wait gave up (lbm_set_wait_limit) */
   LBM_ERR_UNIMPLEMENTED = -6  /* entry point declared but not built */
 };
 
@@ -132,11 +133,39 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace,
  * stream, phi = sum g (Eq. 35), psi (Eq. 37, phi clipped to [0,1]),
  * isotropic stencils (Sec. 3.2), hbar (Eq. 2), F = hbar grad phi, u and p
  * (Eqs. 28-29), MRT collision of f (Eqs. 21-25) and of g (Eqs. 31-33) with
- * d_t(phi u) by backward difference.  Asynchronous on the handle's stream;
- * long runs replay a captured CUDA graph.  Errors: LBM_ERR_ARG,
+ * d_t(phi u) by backward difference.  Asynchronous on the handle's stream:
+ * the steps run as captured CUDA graphs of up to 64 steps, built on first
+ * use of a step count and cached (a few per handle).  Errors: LBM_ERR_ARG,
  * LBM_ERR_CUDA (launch failure; device faults surface at the next
  * synchronising call). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Build (capture and instantiate) the graphs that a following
+ * lbm_step(h, nsteps) will replay, without running any step, so that the
+ * first call of a new step count does not pay for the capture.  Optional.
+ * Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
+int lbm_prepare_steps(lbm_handle* h, int64_t nsteps);
+
+/* Chains: the batch's cases are split into nchains contiguous groups of
+ * nearly equal node counts (1 <= nchains <= 4, at most one per case; the
+ * default is 2 when there are two cases or more).  The steps of each group
+ * are captured as a separate branch of the step graph, so that while the
+ * last CTAs of one group's step drain, the other group's CTAs keep the SMs
+ * busy; the groups are independent, so the results do not change.  Within
+ * a group the largest cases are scheduled first.  lbm_set_chains rebuilds
+ * the work-item table (synchronises).  Errors: LBM_ERR_ARG. */
+int lbm_set_chains(lbm_handle* h, int32_t nchains);
+int32_t lbm_get_chains(const lbm_handle* h);
+
+/* Bound of the device waits, in SM clock cycles: the bulk-copy kernel's
+ * waits for its staged rows and the persistent kernel's grid barrier.  A
+ * wait that gives up raises LBM_ERR_TIMEOUT (reported by the next
+ * synchronising call or lbm_status); the kernel first waits, with the
+ * default bound, for the copies it issued, then returns, and the step's
+ * results are not valid.  cycles < 0 restores the default, about 2 s
+ * (4e9 cycles); 0 gives up at the first poll that finds the data missing
+ * (used to test the timeout path).  Errors: LBM_ERR_ARG. */
+int lbm_set_wait_limit(lbm_handle* h, int64_t cycles);
 
 /* Declare the volume regions of case c: h_labels [ny][nx] with values in
  * [0, nregions) or -1 (no region); NULL means one region = whole grid.
@@ -233,24 +262,37 @@ int lbm_status(lbm_handle* h);
  * [f*: 9 planes][g*: 9 planes][phi*u: 2 planes], each nx*ny elements of the
  * device precision, in the pull layout (plane i, position x holds the
  * post-collision value that streams to x + c_i; f planes are zero in vortex
- * mode; under LBM_F32 the g_0 plane holds the high part of the float pair
- * only, and lbm_restore clears the low part).  lbm_restore writes such a
- * buffer back as the current state; the step index is set separately with
- * lbm_set_time.  All three are
- * asynchronous on the handle's stream. */
+ * mode).  Under LBM_F32 a 21st plane follows with the low part of the float
+ * pair that stores g_0 (the g_0 plane holds its high part), so that a
+ * restored state continues bit for bit.  lbm_snapshot_bytes gives the size.
+ * lbm_restore writes such a buffer back as the current state; the step index
+ * is set separately with lbm_set_time.  All three are asynchronous on the
+ * handle's stream. */
 size_t lbm_snapshot_bytes(const lbm_handle* h, int32_t c);
 int lbm_snapshot(lbm_handle* h, int32_t c, void* d_buf);
 int lbm_restore(lbm_handle* h, int32_t c, const void* d_buf);
 int lbm_set_time(lbm_handle* h, int64_t t);
 
-/* Reverse mode (discrete adjoint of the coupled step; FP64, single-case
- * handles).  An adjoint state has the snapshot layout above in FP64
- * (20 planes of nx*ny doubles): the derivative of a scalar objective with
- * respect to each stored value.
- *   lbm_adjoint_attach: device FP64 scratch of lbm_adjoint_workspace_bytes()
+/* Record and advance (single-case handles): for j = 0..count-1, snapshot
+ * the current state into d_states + j * stride_bytes (layout of
+ * lbm_snapshot), then advance one step.  One call for a whole run of
+ * recorded steps, for the reverse mode; asynchronous on the handle's stream.
+ * Errors: LBM_ERR_ARG (batch, null buffer, stride below
+ * lbm_snapshot_bytes), LBM_ERR_CUDA. */
+int lbm_record_steps(lbm_handle* h, int64_t count, void* d_states, int64_t stride_bytes);
+
+/* Reverse mode (discrete adjoint of the coupled step; single-case handles,
+ * FP64 or FP32).  An adjoint state has the first 20 planes of the snapshot
+ * layout above, in the handle's precision: the derivative of a scalar
+ * objective with respect to each stored value.  An FP32 handle runs the
+ * adjoint arithmetic in FP32 and accumulates the parameter derivatives in
+ * FP64; it differentiates the FP32 step at its stored states (g_0 taken as
+ * the high part of its float pair, a difference of at most half an FP32 ulp
+ * of g_0 in phi).
+ *   lbm_adjoint_attach: device scratch of lbm_adjoint_workspace_bytes()
  *     bytes (256-byte aligned, caller-owned, outlives the handle).
  *   lbm_adjoint_seed_phi: adjoint state of an objective that depends on the
- *     current phi only, from its field derivative d_dphi [ny][nx]
+ *     current phi only, from its FP64 field derivative d_dphi [ny][nx]
  *     (phi = sum of the pulled g, Eq. 35).
  *   lbm_adjoint_step: the handle must hold the state S_t at step index t;
  *     given the adjoint of S_{t+1} (d_adj_in), writes the adjoint of S_t
@@ -263,10 +305,11 @@ int lbm_set_time(lbm_handle* h, int64_t t);
  *     zero when tau_f varies with phi or in vortex mode, the wall entries
  *     without walls.  Walls are transposed with the rest (bounce-back, the
  *     moving-wall term, the mirrored ghost rows).  The state is not modified.
- *     At the clip of Eq. 37 and where |grad psi| = 0 the derivative of the
- *     branch taken is used.
+ *     At the clip of Eq. 37 and where the normal of Eq. 17 is cut to 0
+ *     (|grad psi| below 0.1, the ridges of psi and the clipped bulk) the
+ *     derivative of the branch taken is used.
  *   lbm_adjoint_step_from: as lbm_adjoint_step, for the state S_t held in
- *     d_state (an FP64 snapshot of the case, layout of lbm_snapshot) at step
+ *     d_state (a snapshot of the case, layout of lbm_snapshot) at step
  *     index t instead of the handle's own state, which is neither read nor
  *     modified.  A reverse sweep over recorded states then needs no
  *     lbm_restore before each step.  d_adj_out must differ from d_adj_in and
@@ -274,15 +317,15 @@ int lbm_set_time(lbm_handle* h, int64_t t);
  *   lbm_adjoint_init: adjoint of the initial-state map of lbm_init: given the
  *     adjoint of S_0, writes d_adj_phi0 [ny][nx] and accumulates the sigma and
  *     lambda derivatives (h_param_grads as for lbm_adjoint_step); d_phi0
- *     [ny][nx] and d_u0 ([2][ny][nx] or NULL) are the device copies of the
- *     initial fields.
+ *     [ny][nx] and d_u0 ([2][ny][nx] or NULL) are FP64 device copies of the
+ *     initial fields, and d_adj_phi0 is FP64 whatever the precision.
  *   lbm_adjoint_take_param_grads: adds the accumulated parameter derivatives
  *     to h_param_grads[6] and clears the accumulator (synchronises).
  * Synchronise when h_param_grads is non-NULL.  Errors: LBM_ERR_ARG (batch,
- * FP32 handle, null buffers), LBM_ERR_WORKSPACE (no scratch), LBM_ERR_CUDA. */
+ * null buffers), LBM_ERR_WORKSPACE (no scratch), LBM_ERR_CUDA. */
 size_t lbm_adjoint_workspace_bytes(const lbm_handle* h);
 int lbm_adjoint_attach(lbm_handle* h, void* d_scratch, size_t bytes);
-int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, double* d_adj_state);
+int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, void* d_adj_state);
 int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out,
                      double* h_param_grads);
 int lbm_adjoint_step_from(lbm_handle* h, const void* d_state, int64_t t,
@@ -290,6 +333,16 @@ int lbm_adjoint_step_from(lbm_handle* h, const void* d_state, int64_t t,
 int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
                      const void* d_adj_state, double* d_adj_phi0,
                      double* h_param_grads);
+/* Reverse sweep over recorded states: d_adj holds the adjoint of
+ * S_{t0+count} on entry and the adjoint of S_{t0} on return; the state S_t,
+ * t0 <= t < t0+count, is read from d_states + (t - t0) * stride_bytes
+ * (snapshot layout, as lbm_record_steps writes it).  The count adjoint
+ * steps (lbm_adjoint_step_from each) are enqueued in one call, alternating
+ * between d_adj and d_spare (a second adjoint state); parameter derivatives
+ * accumulate on the device.  Asynchronous.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_WORKSPACE, LBM_ERR_CUDA. */
+int lbm_adjoint_sweep(lbm_handle* h, const void* d_states, int64_t stride_bytes, int64_t t0,
+                      int32_t count, void* d_adj, void* d_spare);
 int lbm_adjoint_take_param_grads(lbm_handle* h, double* h_param_grads);
 
 /* Allocation-free phase volumes, for callers that cannot allocate device
@@ -313,9 +366,11 @@ int lbm_adjoint_take_param_grads(lbm_handle* h, double* h_param_grads);
  * (4096 CTAs of 128 columns); larger sizes return LBM_ERR_ARG with a message
  * in lbm_last_error().  Allocates nothing: the per-CTA partial sums live in a
  * fixed static device array of 256 KiB that every GPU which loads the library
- * holds until the process exits.  The first call on a device looks up that
- * array's address on the current device, so make the first call before any
- * stream capture.  All calls share the array and each overwrites what it
+ * holds until the process exits.  Every call looks up that array's address
+ * on the current device (a host-side query that allocates nothing, so a
+ * device reset that reloads the library's kernels leaves no stale address);
+ * the first call on a device also loads them, so make it before any stream
+ * capture.  All calls share the array and each overwrites what it
  * uses; calls whose kernels overlap on the GPU (different streams, or
  * concurrent host threads) race on it and must be serialised by the caller.
  * Errors: LBM_ERR_ARG, LBM_ERR_CUDA. */
@@ -323,6 +378,17 @@ int lbm_phase_volume_noalloc(const void* d_g, int32_t precision, int32_t nx,
                              int32_t ny, int64_t plane_stride,
                              const int8_t* d_labels, int32_t nregions,
                              double* d_out, void* stream);
+
+/* Measurement aid: FP64 fused multiply-add throughput of the current
+ * device, the bound of the FP64 step on GB300.  Launches blocks_per_sm
+ * (1..8) CTAs of 256 threads per SM, each thread running 8 independent
+ * chains of 4 * trips dependent FMAs, once untimed and once timed with CUDA
+ * events; *out_per_s receives FMAs per second (count / event time) and
+ * *out_ms (may be NULL) the timed duration.  Allocates no device memory;
+ * synchronises.  The paper has no counterpart.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_CUDA. */
+int lbm_fp64_fma_rate(int64_t trips, int32_t blocks_per_sm, double* out_per_s,
+                      double* out_ms);
 
 void lbm_destroy(lbm_handle* h);
 const char* lbm_status_string(int status);

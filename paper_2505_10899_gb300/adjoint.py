@@ -1,8 +1,8 @@
 """Reverse mode of the coupled step for PyTorch: checkpointed recomputation
 around the library's discrete adjoint (lbm_adjoint_step / lbm_adjoint_init).
 
-``coupled_run(phi0, theta, case, nsteps, ckpt_every)`` advances one FP64 case
-and returns phi at the final step as a CUDA tensor; it is differentiable with
+``coupled_run(phi0, theta, case, nsteps, ckpt_every)`` advances one case (FP64
+or FP32) and returns phi at the final step as a CUDA tensor; it is differentiable with
 respect to the initial field phi0 and theta = (sigma, tau_g, lambda, tau_f) or,
 for a case with walls, (sigma, tau_g, lambda, tau_f, u_wall_top, u_wall_bottom).
 The forward pass records the states of the last steps in device memory, as
@@ -23,15 +23,21 @@ from . import lbm
 
 
 class AdjointSim:
-    """One FP64 case with device snapshots and reverse-mode scratch."""
+    """One case with device snapshots and reverse-mode scratch.  Under FP32
+    the states, adjoints and adjoint arithmetic are FP32 (the parameter
+    derivatives accumulate in FP64); a snapshot has a 21st plane (the low
+    part of the g_0 float pair)."""
 
-    def __init__(self, case, phi0, u0=None):
+    def __init__(self, case, phi0, u0=None, precision="f64"):
         self.case = dict(case)
-        self.sim = lbm.Sim(case, phi0, u0, precision="f64")
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "f64" else torch.float32
+        self.sim = lbm.Sim(case, phi0, u0, precision=precision)
         self.h = self.sim.h
         self.dev = self.sim.device
         ny, nx = case["ny"], case["nx"]
         self.shape = (ny, nx)
+        self.planes = lbm.lbm_snapshot_bytes(self.h, 0) // (self.dtype.itemsize * nx * ny)
         nb = lbm.lbm_adjoint_workspace_bytes(self.h)
         self._scratch = torch.empty(nb + 256, dtype=torch.uint8, device=self.dev)
         ptr = (self._scratch.data_ptr() + 255) // 256 * 256
@@ -42,11 +48,11 @@ class AdjointSim:
                                                           dtype=torch.float64, device=self.dev)
 
     def new_state(self):
-        return torch.zeros((20,) + self.shape, dtype=torch.float64, device=self.dev)
+        return torch.zeros((20,) + self.shape, dtype=self.dtype, device=self.dev)
 
     def snapshot(self, buf=None):
         if buf is None:
-            buf = torch.empty((20,) + self.shape, dtype=torch.float64, device=self.dev)
+            buf = torch.empty((self.planes,) + self.shape, dtype=self.dtype, device=self.dev)
         lbm.lbm_snapshot(self.h, 0, buf.data_ptr())
         return buf
 
@@ -74,7 +80,7 @@ class AdjointSim:
         """Adjoint of S_t from the adjoint of S_{t+1}.  Parameter derivatives
         accumulate on the device; with ``grads`` (numpy[6]) they are fetched."""
         if adj_out is None:
-            adj_out = torch.empty((20,) + self.shape, dtype=torch.float64, device=self.dev)
+            adj_out = torch.empty((20,) + self.shape, dtype=self.dtype, device=self.dev)
         rc = lbm.lbm_adjoint_step(self.h, adj_in.data_ptr(), adj_out.data_ptr(), grads)
         if rc != lbm.LBM_OK:
             raise lbm.LbmError(rc, "lbm_adjoint_step", lbm.lib().lbm_last_error().decode())
@@ -85,7 +91,7 @@ class AdjointSim:
         ``state`` of S_t (the handle's own state is not used).  Parameter
         derivatives accumulate on the device."""
         if adj_out is None:
-            adj_out = torch.empty((20,) + self.shape, dtype=torch.float64, device=self.dev)
+            adj_out = torch.empty((20,) + self.shape, dtype=self.dtype, device=self.dev)
         rc = lbm.lbm_adjoint_step_from(self.h, state.data_ptr(), int(t), adj_in.data_ptr(),
                                        adj_out.data_ptr(), None)
         if rc != lbm.LBM_OK:
@@ -125,15 +131,15 @@ def _stored_steps(nsteps, state_bytes, store_bytes, dev):
 
 class CoupledRun(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, phi0, theta, case, nsteps, ckpt_every, u0, store_bytes, tune):
+    def forward(ctx, phi0, theta, case, nsteps, ckpt_every, u0, store_bytes, tune, precision):
         th = theta.detach().cpu().numpy().astype(np.float64)
-        asim = AdjointSim(case_with(case, th), phi0.detach().cpu().numpy(), u0)
+        asim = AdjointSim(case_with(case, th), phi0.detach().cpu().numpy(), u0, precision)
         if (nsteps >= 1000) if tune is None else bool(tune):
             asim.sim.autotune(1)  # the forward and the recomputation step with the fastest kernel
-        state_bytes = 20 * 8 * asim.shape[0] * asim.shape[1]
+        state_bytes = lbm.lbm_snapshot_bytes(asim.h, 0)
         m = _stored_steps(nsteps, state_bytes, store_bytes, asim.dev)
         t_rec = nsteps - m  # states S_t, t in [t_rec, nsteps), stay on the device
-        rec = torch.empty((m, 20) + asim.shape, dtype=torch.float64, device=asim.dev)
+        rec = torch.empty((m, asim.planes) + asim.shape, dtype=asim.dtype, device=asim.dev)
         ckpts = {0: asim.snapshot()} if t_rec > 0 else {}
         t = 0
         while t < t_rec:  # whole segments: the library replays CUDA graphs
@@ -142,9 +148,8 @@ class CoupledRun(torch.autograd.Function):
             t += n
             if t < t_rec:
                 ckpts[t] = asim.snapshot()
-        for k in range(m):
-            asim.snapshot(rec[k])
-            asim.step(1)
+        if m:  # snapshot and step, m times, in one library call
+            lbm.lbm_record_steps(asim.h, m, rec.data_ptr(), rec[0].numel() * rec.element_size())
         phiT = asim.phi()
         ctx.asim, ctx.ckpts, ctx.rec, ctx.t_rec = asim, ckpts, rec, t_rec
         ctx.nsteps, ctx.k = nsteps, ckpt_every
@@ -159,21 +164,23 @@ class CoupledRun(torch.autograd.Function):
         grads = np.zeros(6)
         adj = asim.seed_phi(grad_phiT)
         spare = torch.empty_like(adj)
-        # recorded states: no recomputation
-        for t in reversed(range(t_rec, nsteps)):
-            adj, spare = asim.vjp_step_from(rec[t - t_rec], t, adj, spare), adj
+        # recorded states: no recomputation (one library call for the sweep)
+        if nsteps > t_rec:
+            lbm.lbm_adjoint_sweep(asim.h, rec.data_ptr(), rec[0].numel() * rec.element_size(),
+                                  t_rec, nsteps - t_rec, adj.data_ptr(), spare.data_ptr())
         ctx.rec = rec = None
-        # checkpointed segments below: recompute the states, then run backwards
-        seg = [torch.empty_like(adj) for _ in range(min(k, t_rec) - 1)]
+        # checkpointed segments below: recompute the states into one buffer,
+        # then run the segment backwards
+        if t_rec > 0:
+            seg = torch.empty((min(k, t_rec),) + tuple(ctx.ckpts[0].shape), dtype=adj.dtype,
+                              device=adj.device)
+            stride = seg[0].numel() * seg.element_size()
         for t0 in reversed(sorted(ctx.ckpts)):
             t1 = min(t0 + k, t_rec)
             asim.restore(ctx.ckpts[t0], t0)
-            states = {t0: ctx.ckpts[t0]}
-            for t in range(t0 + 1, t1):
-                asim.step(1)
-                states[t] = asim.snapshot(seg[t - t0 - 1])
-            for t in reversed(range(t0, t1)):
-                adj, spare = asim.vjp_step_from(states[t], t, adj, spare), adj
+            lbm.lbm_record_steps(asim.h, t1 - t0, seg.data_ptr(), stride)
+            lbm.lbm_adjoint_sweep(asim.h, seg.data_ptr(), stride, t0, t1 - t0, adj.data_ptr(),
+                                  spare.data_ptr())
         if 0 in ctx.ckpts:
             asim.restore(ctx.ckpts[0], 0)
         dphi0 = asim.vjp_init(adj, None)
@@ -182,18 +189,19 @@ class CoupledRun(torch.autograd.Function):
         gtheta = torch.as_tensor(grads[:ctx.ntheta], dtype=ctx.theta_dtype,
                                  device=ctx.theta_device)
         dphi0 = dphi0.to(device=ctx.phi0_device, dtype=ctx.phi0_dtype)
-        return dphi0, gtheta, None, None, None, None, None, None
+        return dphi0, gtheta, None, None, None, None, None, None, None
 
 
 def coupled_run(phi0, theta, case, nsteps, ckpt_every=16, u0=None, store_bytes=None,
-                tune=None):
+                tune=None, precision="f64"):
     """phi after nsteps coupled steps, differentiable in phi0 and theta.
     store_bytes bounds the device memory for recorded states (None: a
     quarter of the free memory; 0: checkpoints and recomputation only).
     tune: autotune the stepping kernel first (None: for runs of 1000 steps
-    or more, where it pays for its trial steps)."""
+    or more, where it pays for its trial steps).  precision: "f64", or "f32"
+    for FP32 states, steps and adjoint arithmetic (phi returned in FP64)."""
     return CoupledRun.apply(phi0, theta, case, int(nsteps), int(ckpt_every), u0, store_bytes,
-                            tune)
+                            tune, precision)
 
 
 def region_volume(phi, labels, region):

@@ -20,7 +20,7 @@ OBJDIR = os.path.join(LIBDIR, "obj")
 SO_NAME = "liblbm_gb300.so"
 SO_PATH = os.path.join(LIBDIR, SO_NAME)
 SOURCES = ["kern_f32.cu", "kern_f64.cu", "lbm_api.cu", "lbm_adjoint.cu", "lbm_noalloc.cu",
-           "kern3_f64.cu", "kern3_f32.cu", "kern3_f16.cu", "lbm3_api.cu"]
+           "kern3_f64.cu", "kern3_f32.cu", "kern3_f16.cu", "lbm3_api.cu", "lbm_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

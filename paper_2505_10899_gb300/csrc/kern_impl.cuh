@@ -145,13 +145,24 @@ size_t tma_smem_bytes<LBM_T>(int bx, bool coupled, int mode) {
 }
 
 template <>
-cudaError_t launch_init<LBM_T>(const CaseDev<LBM_T>& cd, double beta4, double kappa,
-                               double lambda, double rho_g, double drho,
-                               const double* phi0, const double* u0, int vortex,
-                               double vU, int parity, cudaStream_t s) {
-  const int64_t n = (int64_t)cd.nx * cd.ny;
-  init_kernel<LBM_T><<<grid_for(n, 256), 256, 0, s>>>(cd, beta4, kappa, lambda, rho_g,
-                                                      drho, phi0, u0, vortex, vU, parity);
+cudaError_t launch_init_items<LBM_T>(const CaseDev<LBM_T>* cases, const Item* items, int n_items,
+                                     int bx, const InitSrc* src, double beta4, double kappa,
+                                     double lambda, int vortex, double vU, int parity,
+                                     cudaStream_t s) {
+  if (n_items < 1) return cudaSuccess;
+  switch (bx) {
+    case 32:
+      init_items<LBM_T, 32><<<n_items, 32, 0, s>>>(cases, items, src, beta4, kappa, lambda,
+                                                    vortex, vU, parity);
+      break;
+    case 64:
+      init_items<LBM_T, 64><<<n_items, 64, 0, s>>>(cases, items, src, beta4, kappa, lambda,
+                                                    vortex, vU, parity);
+      break;
+    default:
+      init_items<LBM_T, 128><<<n_items, 128, 0, s>>>(cases, items, src, beta4, kappa, lambda,
+                                                      vortex, vU, parity);
+  }
   return cudaGetLastError();
 }
 

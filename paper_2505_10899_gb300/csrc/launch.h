@@ -34,11 +34,12 @@ cudaError_t prepare_tma();
 template <typename T>
 size_t tma_smem_bytes(int bx, bool coupled, int mode);
 
+// Initial state of every case in one launch over the work items (bx columns
+// per CTA); src: per-case device-readable pointers to phi0 and u0.
 template <typename T>
-cudaError_t launch_init(const CaseDev<T>& cd, double beta4, double kappa,
-                        double lambda, double rho_g, double drho,
-                        const double* phi0, const double* u0, int vortex,
-                        double vU, int parity, cudaStream_t s);
+cudaError_t launch_init_items(const CaseDev<T>* cases, const Item* items, int n_items, int bx,
+                              const InitSrc* src, double beta4, double kappa, double lambda,
+                              int vortex, double vU, int parity, cudaStream_t s);
 
 // buf: the 9-plane buffer with plane stride P (walls: bounce-back positions)
 template <typename T>

@@ -12,6 +12,7 @@
 #include "../../include/lbm3_api.h"
 #include "launch3.h"
 #include "lbm3_layout.h"
+#include "lbm_trace.h"
 
 namespace lbmk {
 int set_last_error(int code, const char* msg);  // lbm_api.cu: lbm_last_error()
@@ -243,6 +244,7 @@ size_t lbm3_workspace_bytes(const lbm3_params* p) {
 
 int lbm3_init(const lbm3_params* p, void* d_ws, size_t ws_bytes, const double* h_phi0,
               const double* h_u0, void* stream, lbm3_handle** out) {
+  lbmk::TraceRange trace("lbm3_init");
   if (!out) return fail(LBM_ERR_ARG, "null output handle");
   *out = nullptr;
   int rc = check(p);
@@ -308,6 +310,7 @@ int lbm3_init(const lbm3_params* p, void* d_ws, size_t ws_bytes, const double* h
 }
 
 int lbm3_step(lbm3_handle* h, int64_t nsteps) {
+  lbmk::TraceRange trace("lbm3_step");
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps must be >= 0");
   while (nsteps >= kGraphSteps) {
@@ -348,6 +351,7 @@ int lbm3_set_regions(lbm3_handle* h, const int8_t* h_labels, int32_t nregions) {
 }
 
 int lbm3_volume(lbm3_handle* h, double* h_out) {
+  lbmk::TraceRange trace("lbm3_volume");
   if (!h || !h_out) return fail(LBM_ERR_ARG, "null argument");
   L3_CUDA(dispatch(h->prm.precision, [&](auto k) {
     return decltype(k)::volume(h->b, h->hp, h->parity, h->labels, h->nregions, h->part,
@@ -440,6 +444,7 @@ int32_t lbm3_get_kernel(const lbm3_handle* h) { return h ? h->variant : -1; }
 
 int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* ovar, int32_t* obx, int32_t* oby,
                   int32_t* ozc, double* best_ms) {
+  lbmk::TraceRange trace("lbm3_autotune");
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (trials < 1 || trials > 100) return fail(LBM_ERR_ARG, "trials must lie in [1, 100]");
   cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -16,7 +16,8 @@
 //   ad_gather: every node sums the stencil adjoints that refer to its phi and
 //              psi, and adds the total to the adjoints of its 9 pulled g.
 // The clip of Eq. 37 and the normalisation of grad(psi) use the derivative
-// of the branch taken (0 outside (0,1) and where |grad psi| = 0).
+// of the branch taken (0 outside (0,1), and 0 where |grad psi| falls below the
+// cut of the normal, 0.1).
 // Walls (bounce-back rows, moving-wall term, mirrored ghost rows) are
 // transposed as well: the bounce-back keeps the pull a bijection between
 // buffer positions and (node, direction), and the mirrored ghost rows add
@@ -93,9 +94,10 @@ __device__ __forceinline__ int64_t ad_nb(int x, int y, int dx, int dy, int nx, i
 // node (x, y): the nodes s whose stencil entry j reads this node.  Without
 // walls s = (x, y) - c_j; with walls also the wall row's own uses of its
 // mirrored ghost row.
-__device__ __forceinline__ void gather_uses(const double* __restrict__ lP,
-                                            const double* __restrict__ lQ, int x, int y,
-                                            int nx, int ny, int walls, double& sp, double& sq) {
+template <typename R>
+__device__ __forceinline__ void gather_uses(const R* __restrict__ lP, const R* __restrict__ lQ,
+                                            int x, int y, int nx, int ny, int walls, R& sp,
+                                            R& sq) {
   const int64_t n = (int64_t)nx * ny;
   for (int j = 1; j < 9; ++j) {
     const int ys = y - kAY[j];
@@ -115,66 +117,100 @@ __device__ __forceinline__ void gather_uses(const double* __restrict__ lP,
   }
 }
 
+template <typename R>
 struct AdArgs {
-  const double* fA;  // f* source buffer (9 planes, stride P), null in vortex mode
-  const double* gA;  // g* source buffer
-  const double* JA;  // phi*u source buffer (2 planes)
-  int64_t P;         // plane stride of the state buffers
+  const R* fA;  // f* source buffer (9 planes, stride P), null in vortex mode
+  const R* gA;  // g* source buffer
+  const R* JA;  // phi*u source buffer (2 planes)
+  int64_t P;    // plane stride of the state buffers
   int nx, ny;
-  const double* phi;  // [n] scratch
-  const double* psi;  // [n] scratch
-  const double* ain;  // [20][n] adjoint of S_{t+1}
-  double* aout;       // [20][n] adjoint of S_t
-  double* lP;         // [9][n] scratch: adjoint of phi(x + c_j) used at node x
-  double* lQ;         // [8][n] scratch: adjoint of psi(x + c_j), j = 1..8
-  double* part;       // [gridDim][kNParam]
-  Phys<double> ph;
-  double rho_g, drho, mu_g, dmu, sD7, hD7, s7;
+  const R* phi;  // [n] scratch
+  const R* psi;  // [n] scratch
+  const R* ain;  // [20][n] adjoint of S_{t+1}
+  R* aout;       // [20][n] adjoint of S_t
+  R* lP;         // [9][n] scratch: adjoint of phi(x + c_j) used at node x
+  R* lQ;         // [8][n] scratch: adjoint of psi(x + c_j), j = 1..8
+  double* part;  // [gridDim][kNParam]
+  Phys<R> ph;
+  R rho_g, drho, mu_g, dmu, sD7, hD7, s7;
   int var_tau, coupled;
-  double ct;    // vortex: U cos(pi t / T)
-  double invW;  // 1/W: d(lambda/W)/d(lambda)
+  R ct;    // vortex: U cos(pi t / T)
+  R invW;  // 1/W: d(lambda/W)/d(lambda)
   int walls;
-  double u_top, u_bot;
+  R u_top, u_bot;
 };
 
-// phi (Eq. 35, pulled sum in the forward order) and psi = ln(a/b) (Eq. 37).
-__global__ void ad_phase(const double* __restrict__ gA, int64_t P, int nx, int ny, int walls,
-                         double xi, double* __restrict__ phi, double* __restrict__ psi) {
+// d psi / d phi inside the clip for the forward's psi: ln(a/b) in FP64,
+// log2(a/b) in FP32 (the FP32 kernels take psi up to the factor 1/ln 2,
+// which the normal of Eq. 17 does not see).
+template <typename R>
+__device__ __forceinline__ R dpsi_dphi(R p, R xi) {
+  const R d = R(1) / (p + xi) + R(1) / ((R(1) - p) + xi);
+  return sizeof(R) == 4 ? R(1.4426950408889634) * d : d;
+}
+
+// phi (Eq. 35, pulled sum in the forward order) and psi (Eq. 37).
+template <typename R>
+__global__ void ad_phase(const R* __restrict__ gA, int64_t P, int nx, int ny, int walls, R xi,
+                         R* __restrict__ phi, R* __restrict__ psi) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
-    double G[9];
+    R G[9];
     for (int i = 0; i < 9; ++i) {
       int pl;
       const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
       G[i] = gA[pl * P + pos];
     }
-    const double p = lbmk::sum9(G);
+    const R p = lbmk::sum9(G);
     phi[k] = p;
     psi[k] = lbmk::psi_of(p, xi);
   }
 }
 
-__global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
+// Deterministic CTA reduction of the parameter partials (FP64).
+__device__ __forceinline__ void ad_block_partials(double (&red)[kAdThreads / 32][kNParam],
+                                                  const double (&gacc)[kNParam],
+                                                  double* __restrict__ part) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q = 0; q < kNParam; ++q) {
+    double v = gacc[q];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[warp][q] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNParam) {
+    double v = 0.0;
+    for (int w = 0; w < kAdThreads / 32; ++w) v += red[w][threadIdx.x];
+    part[(int64_t)blockIdx.x * kNParam + threadIdx.x] = v;
+  }
+}
+
+// The per-node reverse sweep.  R is the arithmetic and storage type of the
+// states and adjoints (the handle's precision); the parameter partials are
+// accumulated in FP64.
+template <typename R>
+__global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs<R> a) {
   __shared__ double red[kAdThreads / 32][kNParam];
+  using N = lbmk::Num<R>;
   const int nx = a.nx, ny = a.ny;
   const int64_t n = (int64_t)nx * ny, P = a.P;
-  const Phys<double>& ph = a.ph;
+  const Phys<R>& ph = a.ph;
   double gacc[kNParam] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
     int64_t src[9];
     int spl[9];
-    double F[9], G[9];
+    R F[9], G[9];
     for (int i = 0; i < 9; ++i) {
       src[i] = ad_src(i, x, y, nx, ny, a.walls, &spl[i]);
       G[i] = a.gA[spl[i] * P + src[i]];
-      F[i] = a.coupled ? a.fA[spl[i] * P + src[i]] : 0.0;
+      F[i] = a.coupled ? a.fA[spl[i] * P + src[i]] : R(0);
     }
-    const double jpx = a.JA[k], jpy = a.JA[P + k];
-    double Pv[9], Qv[9];
+    const R jpx = a.JA[k], jpy = a.JA[P + k];
+    R Pv[9], Qv[9];
     for (int j = 0; j < 9; ++j) {
       const int64_t s = ad_nb(x, y, kAX[j], kAY[j], nx, ny, a.walls);
       Pv[j] = a.phi[s];
@@ -183,91 +219,91 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
     // moving-wall term of the bounced f (rho of this node)
     const bool wbot = a.walls && y == 0, wtop = a.walls && y == ny - 1;
     if (a.coupled && (wbot || wtop)) {
-      const double rw = a.rho_g + Pv[0] * a.drho;
+      const R rw = a.rho_g + Pv[0] * a.drho;
       if (wbot) {
-        F[5] += rw * a.u_bot / 6.0;
-        F[6] -= rw * a.u_bot / 6.0;
+        F[5] += rw * a.u_bot / R(6);
+        F[6] -= rw * a.u_bot / R(6);
       }
       if (wtop) {
-        F[7] -= rw * a.u_top / 6.0;
-        F[8] += rw * a.u_top / 6.0;
+        F[7] -= rw * a.u_top / R(6);
+        F[8] += rw * a.u_top / R(6);
       }
     }
     // ---------------- forward recompute (as node_update) ----------------
-    const double phi = Pv[0];
-    const double gpx = (1.0 / 3.0) * (Pv[1] - Pv[3]) + (1.0 / 12.0) * ((Pv[5] - Pv[6]) + (Pv[8] - Pv[7]));
-    const double gpy = (1.0 / 3.0) * (Pv[2] - Pv[4]) + (1.0 / 12.0) * ((Pv[5] - Pv[8]) + (Pv[6] - Pv[7]));
-    const double lap = (2.0 / 3.0) * (((Pv[1] + Pv[3]) + (Pv[2] + Pv[4])) - 4.0 * phi) +
-                       (1.0 / 6.0) * (((Pv[5] + Pv[6]) + (Pv[8] + Pv[7])) - 4.0 * phi);
-    const double qx = 4.0 * (Qv[1] - Qv[3]) + ((Qv[5] - Qv[6]) + (Qv[8] - Qv[7]));
-    const double qy = 4.0 * (Qv[2] - Qv[4]) + ((Qv[5] - Qv[8]) + (Qv[6] - Qv[7]));
-    const double poly = phi * (phi - 1.0) * (phi - 0.5);
-    const double mu = ph.beta4 * poly - ph.kappa * lap;
-    const double Fx = mu * gpx, Fy = mu * gpy;
-    double ux, uy;
-    double rho = 1.0, irho = 1.0, Rx = 0.0, Ry = 0.0, u2 = 0.0, mu_v = 0.0, s7 = a.s7;
-    double sD7 = a.sD7, hD7 = a.hD7;
-    Mom<double> mf{};
+    const R phi = Pv[0];
+    const R gpx = R(1.0 / 3.0) * (Pv[1] - Pv[3]) + R(1.0 / 12.0) * ((Pv[5] - Pv[6]) + (Pv[8] - Pv[7]));
+    const R gpy = R(1.0 / 3.0) * (Pv[2] - Pv[4]) + R(1.0 / 12.0) * ((Pv[5] - Pv[8]) + (Pv[6] - Pv[7]));
+    const R lap = R(2.0 / 3.0) * (((Pv[1] + Pv[3]) + (Pv[2] + Pv[4])) - R(4) * phi) +
+                  R(1.0 / 6.0) * (((Pv[5] + Pv[6]) + (Pv[8] + Pv[7])) - R(4) * phi);
+    const R qx = R(4) * (Qv[1] - Qv[3]) + ((Qv[5] - Qv[6]) + (Qv[8] - Qv[7]));
+    const R qy = R(4) * (Qv[2] - Qv[4]) + ((Qv[5] - Qv[8]) + (Qv[6] - Qv[7]));
+    const R poly = phi * (phi - R(1)) * (phi - R(0.5));
+    const R mu = ph.beta4 * poly - ph.kappa * lap;
+    const R Fx = mu * gpx, Fy = mu * gpy;
+    R ux, uy;
+    R rho = R(1), irho = R(1), Rx = R(0), Ry = R(0), u2 = R(0), mu_v = R(0), s7 = a.s7;
+    R sD7 = a.sD7, hD7 = a.hD7;
+    Mom<R> mf{};
     if (a.coupled) {
       rho = a.rho_g + phi * a.drho;
-      irho = 1.0 / rho;
+      irho = R(1) / rho;
       mf = lbmk::moments(F);
-      ux = (mf.m3 + 0.5 * Fx) * irho;
-      uy = (mf.m5 + 0.5 * Fy) * irho;
+      ux = (mf.m3 + R(0.5) * Fx) * irho;
+      uy = (mf.m5 + R(0.5) * Fy) * irho;
       Rx = a.drho * gpx;
       Ry = a.drho * gpy;
       u2 = ux * ux + uy * uy;
       if (a.var_tau) {
         mu_v = a.mu_g + phi * a.dmu;
-        const double tau = 3.0 * mu_v * irho + 0.5;
-        s7 = 1.0 / tau;
-        sD7 = -0.25 * s7;
-        hD7 = 0.25 - 0.125 * s7;
+        const R tau = R(3) * mu_v * irho + R(0.5);
+        s7 = R(1) / tau;
+        sD7 = R(-0.25) * s7;
+        hD7 = R(0.25) - R(0.125) * s7;
       }
     } else {
-      double sx, cx, sy, cy;
-      sincospi((x + 0.5) / nx, &sx, &cx);
-      sincospi((y + 0.5) / ny, &sy, &cy);
-      ux = -a.ct * (sx * sx) * (2.0 * sy * cy);
-      uy = a.ct * (sy * sy) * (2.0 * sx * cx);
+      R sx, cx, sy, cy;
+      N::sincospi_((R(x) + R(0.5)) / R(nx), &sx, &cx);
+      N::sincospi_((R(y) + R(0.5)) / R(ny), &sy, &cy);
+      ux = -a.ct * (sx * sx) * (R(2) * sy * cy);
+      uy = a.ct * (sy * sy) * (R(2) * sx * cx);
     }
-    const double Jx = phi * ux, Jy = phi * uy;
-    const double dJx = Jx - jpx, dJy = Jy - jpy;
-    const double pc = fmin(fmax(phi, 0.0), 1.0);
-    const double ta = pc + ph.xi, tb = (1.0 - pc) + ph.xi;
-    const double q2 = qx * qx + qy * qy;
-    const double iq = (q2 >= ph.qmin2) ? 1.0 / sqrt(q2) : 0.0;
-    const double sh = ph.lamW * ph.tfac * ta * tb * iq;
-    const double Vx = 3.0 * dJx + sh * qx, Vy = 3.0 * dJy + sh * qy;
-    const Mom<double> mg = lbmk::moments(G);
+    const R Jx = phi * ux, Jy = phi * uy;
+    const R dJx = Jx - jpx, dJy = Jy - jpy;
+    const R pc = N::clamp01(phi);
+    const R ta = pc + ph.xi, tb = (R(1) - pc) + ph.xi;
+    const R q2 = qx * qx + qy * qy;
+    const R iq = (q2 >= ph.qmin2) ? R(1) / sqrt(q2) : R(0);
+    const R sh = ph.lamW * ph.tfac * ta * tb * iq;
+    const R Vx = R(3) * dJx + sh * qx, Vy = R(3) * dJy + sh * qy;
+    const Mom<R> mg = lbmk::moments(G);
 
     // ---------------- reverse ----------------
-    double aF[9], aG[9];
+    R aF[9], aG[9];
     for (int i = 0; i < 9; ++i) {
       aF[i] = a.ain[i * n + k];
       aG[i] = a.ain[(9 + i) * n + k];
     }
-    const double aJx = a.ain[18 * n + k], aJy = a.ain[19 * n + k];
+    const R aJx = a.ain[18 * n + k], aJy = a.ain[19 * n + k];
 
-    double lphi = 0.0, lmu = 0.0, lgpx = 0.0, lgpy = 0.0, llap = 0.0, lqx = 0.0, lqy = 0.0;
-    double lux = 0.0, luy = 0.0;
+    R lphi = R(0), lmu = R(0), lgpx = R(0), lgpy = R(0), llap = R(0), lqx = R(0), lqy = R(0);
+    R lux = R(0), luy = R(0);
     // g*_0 = phi - sum_{i>=1} g*'_i; g*' = G + M^T e (e0 = 0)
     lphi += aG[0];
-    double aGp[9];
-    aGp[0] = 0.0;
+    R aGp[9];
+    aGp[0] = R(0);
     for (int i = 1; i < 9; ++i) aGp[i] = aG[i] - aG[0];
-    double lG[9];
+    R lG[9];
     for (int i = 0; i < 9; ++i) lG[i] = aGp[i];
-    const Mom<double> le = lbmk::moments(aGp);  // lambda_e = M lambda_g*'
-    double lmg[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    double lLam = 0.0, lJx = 0.0, lJy = 0.0, lVx = 0.0, lVy = 0.0;
+    const Mom<R> le = lbmk::moments(aGp);  // lambda_e = M lambda_g*'
+    R lmg[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+    R lLam = R(0), lJx = R(0), lJy = R(0), lVx = R(0), lVy = R(0);
     // e1, e2
     lmg[1] += ph.gsD[1] * le.m1;
-    lLam += -2.0 * ph.gsD[1] * le.m1;
-    lphi += 4.0 * ph.gsD[1] * le.m1;
+    lLam += R(-2) * ph.gsD[1] * le.m1;
+    lphi += R(4) * ph.gsD[1] * le.m1;
     lmg[2] += ph.gsD[2] * le.m2;
-    lphi += -4.0 * ph.gsD[2] * le.m2;
-    lLam += 3.0 * ph.gsD[2] * le.m2;
+    lphi += R(-4) * ph.gsD[2] * le.m2;
+    lLam += R(3) * ph.gsD[2] * le.m2;
     // e3..e6
     lmg[3] += ph.gsD[3] * le.m3;
     lJx += -ph.gsD[3] * le.m3;
@@ -284,62 +320,60 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
     lmg[7] += ph.gsD[7] * le.m7;
     lmg[8] += ph.gsD[8] * le.m8;
     {  // tau_g: s3 = s5 = 1/tau_g; gsD = -s/6, ghD3 = (1 - s/2)/18
-      const double lgs = (mg.m3 - Jx) * le.m3 + (mg.m5 - Jy) * le.m5;
-      const double lgh = Vx * le.m3 + Vy * le.m5;
-      const double ls = -lgs / 6.0 - lgh / 36.0;
-      const double sg = -6.0 * ph.gsD[3];  // = 1/tau_g
-      gacc[3] += -sg * sg * ls;
+      const R lgs = (mg.m3 - Jx) * le.m3 + (mg.m5 - Jy) * le.m5;
+      const R lgh = Vx * le.m3 + Vy * le.m5;
+      const R ls = -lgs / R(6) - lgh / R(36);
+      const R sg = R(-6) * ph.gsD[3];  // = 1/tau_g
+      gacc[3] += (double)(-sg * sg * ls);
     }
     // mg = M G
     lbmk::add_back(lG, lmg[0], lmg[1], lmg[2], lmg[3], lmg[4], lmg[5], lmg[6], lmg[7], lmg[8]);
     // Lam = mu + lambda phi
     lmu += lLam;
     lphi += ph.lambda * lLam;
-    gacc[2] += phi * lLam;
+    gacc[2] += (double)(phi * lLam);
     // V = 3 dJ + sh q
-    const double ldJx = 3.0 * lVx, ldJy = 3.0 * lVy;
-    const double lsh = qx * lVx + qy * lVy;
+    const R ldJx = R(3) * lVx, ldJy = R(3) * lVy;
+    const R lsh = qx * lVx + qy * lVy;
     lqx += sh * lVx;
     lqy += sh * lVy;
     // sh = lamW tfac ta tb iq
-    const double c0 = ph.lamW * ph.tfac;
-    const double lta = c0 * tb * iq * lsh, ltb = c0 * ta * iq * lsh, liq = c0 * ta * tb * lsh;
-    gacc[2] += ph.tfac * ta * tb * iq * lsh * a.invW;  // lamW = lambda / W
+    const R c0 = ph.lamW * ph.tfac;
+    const R lta = c0 * tb * iq * lsh, ltb = c0 * ta * iq * lsh, liq = c0 * ta * tb * lsh;
+    gacc[2] += (double)(ph.tfac * ta * tb * iq * lsh * a.invW);  // lamW = lambda / W
     if (q2 >= ph.qmin2) {  // below the threshold n = 0: no derivative
-      const double lq2 = -0.5 * iq * iq * iq * liq;
-      lqx += 2.0 * qx * lq2;
-      lqy += 2.0 * qy * lq2;
+      const R lq2 = R(-0.5) * iq * iq * iq * liq;
+      lqx += R(2) * qx * lq2;
+      lqy += R(2) * qy * lq2;
     }
-    if (phi > 0.0 && phi < 1.0) lphi += lta - ltb;
+    if (phi > R(0) && phi < R(1)) lphi += lta - ltb;
     // dJ = J - J_prev; J also stored
     lJx += ldJx + aJx;
     lJy += ldJy + aJy;
-    const double ljpx = -ldJx, ljpy = -ldJy;
+    const R ljpx = -ldJx, ljpy = -ldJy;
     // J = phi u
     lphi += ux * lJx + uy * lJy;
     lux += phi * lJx;
     luy += phi * lJy;
 
-    double lF[9];
-    for (int i = 0; i < 9; ++i) lF[i] = 0.0;
+    R lF[9];
+    for (int i = 0; i < 9; ++i) lF[i] = R(0);
     if (a.coupled) {
       for (int i = 0; i < 9; ++i) lF[i] = aF[i];
-      const Mom<double> ld = lbmk::moments(aF);  // lambda_d = M lambda_f*
-      double lm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-      double lp = 0.0, lru2 = 0.0, luR = 0.0, ljx = 0.0, ljy = 0.0, lFx = 0.0, lFy = 0.0;
-      double lrho = 0.0, lRx = 0.0, lRy = 0.0, lsD7 = 0.0, lhD7 = 0.0, lirho = 0.0, lu2 = 0.0;
-      const double p =
-          0.6 * ((mf.m0 - F[0]) + 0.5 * (ux * Rx + uy * Ry) - (2.0 / 3.0) * rho * u2);
-      const double jx = rho * ux;
+      const Mom<R> ld = lbmk::moments(aF);  // lambda_d = M lambda_f*
+      R lm[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
+      R lp = R(0), lru2 = R(0), luR = R(0), ljx = R(0), ljy = R(0), lFx = R(0), lFy = R(0);
+      R lrho = R(0), lRx = R(0), lRy = R(0), lsD7 = R(0), lhD7 = R(0), lirho = R(0), lu2 = R(0);
+      const R jx = rho * ux;
       // d0..d6
       lm[0] += ph.fsD[0] * ld.m0;
       luR += ph.fhD[0] * ld.m0;
       lm[1] += ph.fsD[1] * ld.m1;
-      lp += -6.0 * ph.fsD[1] * ld.m1;
-      lru2 += -3.0 * ph.fsD[1] * ld.m1;
+      lp += R(-6) * ph.fsD[1] * ld.m1;
+      lru2 += R(-3) * ph.fsD[1] * ld.m1;
       lm[2] += ph.fsD[2] * ld.m2;
-      lp += 9.0 * ph.fsD[2] * ld.m2;
-      lru2 += 3.0 * ph.fsD[2] * ld.m2;
+      lp += R(9) * ph.fsD[2] * ld.m2;
+      lru2 += R(3) * ph.fsD[2] * ld.m2;
       luR += -ph.fhD[2] * ld.m2;
       lm[3] += ph.fsD[3] * ld.m3;
       ljx += -ph.fsD[3] * ld.m3;
@@ -356,30 +390,30 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
       // d7 = sD7 (m7 - rho(ux^2 - uy^2)) + hD7 (2/3)(ux Rx - uy Ry)
       lm[7] += sD7 * ld.m7;
       lrho += -sD7 * (ux * ux - uy * uy) * ld.m7;
-      lux += -2.0 * sD7 * rho * ux * ld.m7 + hD7 * (2.0 / 3.0) * Rx * ld.m7;
-      luy += 2.0 * sD7 * rho * uy * ld.m7 - hD7 * (2.0 / 3.0) * Ry * ld.m7;
-      lRx += hD7 * (2.0 / 3.0) * ux * ld.m7;
-      lRy += -hD7 * (2.0 / 3.0) * uy * ld.m7;
+      lux += R(-2) * sD7 * rho * ux * ld.m7 + hD7 * R(2.0 / 3.0) * Rx * ld.m7;
+      luy += R(2) * sD7 * rho * uy * ld.m7 - hD7 * R(2.0 / 3.0) * Ry * ld.m7;
+      lRx += hD7 * R(2.0 / 3.0) * ux * ld.m7;
+      lRy += -hD7 * R(2.0 / 3.0) * uy * ld.m7;
       lsD7 += (mf.m7 - rho * (ux * ux - uy * uy)) * ld.m7;
-      lhD7 += (2.0 / 3.0) * (ux * Rx - uy * Ry) * ld.m7;
+      lhD7 += R(2.0 / 3.0) * (ux * Rx - uy * Ry) * ld.m7;
       // d8 = sD7 (m8 - jx uy) + hD7 (1/3)(ux Ry + uy Rx)
       lm[8] += sD7 * ld.m8;
       ljx += -sD7 * uy * ld.m8;
-      luy += -sD7 * jx * ld.m8 + hD7 * (1.0 / 3.0) * Rx * ld.m8;
-      lux += hD7 * (1.0 / 3.0) * Ry * ld.m8;
-      lRy += hD7 * (1.0 / 3.0) * ux * ld.m8;
-      lRx += hD7 * (1.0 / 3.0) * uy * ld.m8;
+      luy += -sD7 * jx * ld.m8 + hD7 * R(1.0 / 3.0) * Rx * ld.m8;
+      lux += hD7 * R(1.0 / 3.0) * Ry * ld.m8;
+      lRy += hD7 * R(1.0 / 3.0) * ux * ld.m8;
+      lRx += hD7 * R(1.0 / 3.0) * uy * ld.m8;
       lsD7 += (mf.m8 - jx * uy) * ld.m8;
-      lhD7 += (1.0 / 3.0) * (ux * Ry + uy * Rx) * ld.m8;
+      lhD7 += R(1.0 / 3.0) * (ux * Ry + uy * Rx) * ld.m8;
       // s7 (= s8): sD7 = -s7/4, hD7 = 1/4 - s7/8
-      const double ls7 = -0.25 * lsD7 - 0.125 * lhD7;
+      const R ls7 = R(-0.25) * lsD7 - R(0.125) * lhD7;
       if (a.var_tau) {
-        const double ltau = -s7 * s7 * ls7;  // s7 = 1/tau
-        const double lmuv = 3.0 * irho * ltau;
-        lirho += 3.0 * mu_v * ltau;
+        const R ltau = -s7 * s7 * ls7;  // s7 = 1/tau
+        const R lmuv = R(3) * irho * ltau;
+        lirho += R(3) * mu_v * ltau;
         lphi += a.dmu * lmuv;
       } else {
-        gacc[4] += -s7 * s7 * ls7;  // s7 = 1/tau_f
+        gacc[4] += (double)(-s7 * s7 * ls7);  // s7 = 1/tau_f
       }
       // jx = rho ux, jy = rho uy
       lrho += ux * ljx + uy * ljy;
@@ -389,15 +423,14 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
       lrho += u2 * lru2;
       lu2 += rho * lru2;
       // p = 0.6((m0 - F0) + uR/2 - (2/3) rho u2)
-      lm[0] += 0.6 * lp;
-      lF[0] += -0.6 * lp;
-      luR += 0.3 * lp;
-      lrho += -0.4 * u2 * lp;
-      lu2 += -0.4 * rho * lp;
-      (void)p;
+      lm[0] += R(0.6) * lp;
+      lF[0] += R(-0.6) * lp;
+      luR += R(0.3) * lp;
+      lrho += R(-0.4) * u2 * lp;
+      lu2 += R(-0.4) * rho * lp;
       // u2, uR
-      lux += 2.0 * ux * lu2 + Rx * luR;
-      luy += 2.0 * uy * lu2 + Ry * luR;
+      lux += R(2) * ux * lu2 + Rx * luR;
+      luy += R(2) * uy * lu2 + Ry * luR;
       lRx += ux * luR;
       lRy += uy * luR;
       // R = drho grad phi
@@ -405,23 +438,23 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
       lgpy += a.drho * lRy;
       // u = (m + F/2) irho
       lm[3] += irho * lux;
-      lFx += 0.5 * irho * lux;
-      lirho += (mf.m3 + 0.5 * Fx) * lux;
+      lFx += R(0.5) * irho * lux;
+      lirho += (mf.m3 + R(0.5) * Fx) * lux;
       lm[5] += irho * luy;
-      lFy += 0.5 * irho * luy;
-      lirho += (mf.m5 + 0.5 * Fy) * luy;
+      lFy += R(0.5) * irho * luy;
+      lirho += (mf.m5 + R(0.5) * Fy) * luy;
       // m = M F
       lbmk::add_back(lF, lm[0], lm[1], lm[2], lm[3], lm[4], lm[5], lm[6], lm[7], lm[8]);
       // moving-wall term: F_i += rho c_ix u_w / 6, rho = rho_g + phi drho
       if (wbot) {
-        const double l = (lF[5] - lF[6]) / 6.0;
+        const R l = (lF[5] - lF[6]) / R(6);
         lrho += a.u_bot * l;
-        gacc[6] += rho * l;
+        gacc[6] += (double)(rho * l);
       }
       if (wtop) {
-        const double l = (lF[8] - lF[7]) / 6.0;
+        const R l = (lF[8] - lF[7]) / R(6);
         lrho += a.u_top * l;
-        gacc[5] += rho * l;
+        gacc[5] += (double)(rho * l);
       }
       // irho = 1/rho, rho = rho_g + phi drho
       lrho += -irho * irho * lirho;
@@ -432,15 +465,15 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
       lgpy += mu * lFy;
     }
     // mu = beta4 poly - kappa lap
-    lphi += ph.beta4 * (3.0 * phi * phi - 3.0 * phi + 0.5) * lmu;
+    lphi += ph.beta4 * (R(3) * phi * phi - R(3) * phi + R(0.5)) * lmu;
     llap += -ph.kappa * lmu;
-    gacc[0] += poly * lmu;
-    gacc[1] += -lap * lmu;
+    gacc[0] += (double)(poly * lmu);
+    gacc[1] += (double)(-lap * lmu);
 
     // stencil adjoints (transpose of the difference forms above)
-    const double gx3 = lgpx / 3.0, gy3 = lgpy / 3.0, gx12 = lgpx / 12.0, gy12 = lgpy / 12.0;
-    const double la = (2.0 / 3.0) * llap, ld6 = llap / 6.0;
-    a.lP[0 * n + k] = -(10.0 / 3.0) * llap + lphi;
+    const R gx3 = lgpx / R(3), gy3 = lgpy / R(3), gx12 = lgpx / R(12), gy12 = lgpy / R(12);
+    const R la = R(2.0 / 3.0) * llap, ld6 = llap / R(6);
+    a.lP[0 * n + k] = R(-10.0 / 3.0) * llap + lphi;
     a.lP[1 * n + k] = gx3 + la;
     a.lP[3 * n + k] = -gx3 + la;
     a.lP[2 * n + k] = gy3 + la;
@@ -449,14 +482,14 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
     a.lP[6 * n + k] = -gx12 + gy12 + ld6;
     a.lP[7 * n + k] = -gx12 - gy12 + ld6;
     a.lP[8 * n + k] = gx12 - gy12 + ld6;
-    a.lQ[0 * n + k] = 4.0 * lqx;   // Q1
-    a.lQ[2 * n + k] = -4.0 * lqx;  // Q3
-    a.lQ[1 * n + k] = 4.0 * lqy;   // Q2
-    a.lQ[3 * n + k] = -4.0 * lqy;  // Q4
-    a.lQ[4 * n + k] = lqx + lqy;   // Q5
-    a.lQ[5 * n + k] = -lqx + lqy;  // Q6
-    a.lQ[6 * n + k] = -lqx - lqy;  // Q7
-    a.lQ[7 * n + k] = lqx - lqy;   // Q8
+    a.lQ[0 * n + k] = R(4) * lqx;   // Q1
+    a.lQ[2 * n + k] = R(-4) * lqx;  // Q3
+    a.lQ[1 * n + k] = R(4) * lqy;   // Q2
+    a.lQ[3 * n + k] = R(-4) * lqy;  // Q4
+    a.lQ[4 * n + k] = lqx + lqy;    // Q5
+    a.lQ[5 * n + k] = -lqx + lqy;   // Q6
+    a.lQ[6 * n + k] = -lqx - lqy;   // Q7
+    a.lQ[7 * n + k] = lqx - lqy;    // Q8
 
     // transpose of the pull: adjoint of the source positions (a bijection,
     // walls included)
@@ -467,36 +500,24 @@ __global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs a) {
     a.aout[18 * n + k] = ljpx;
     a.aout[19 * n + k] = ljpy;
   }
-  // deterministic CTA reduction of the parameter partials
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = 0; q < kNParam; ++q) {
-    double v = gacc[q];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][q] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < kNParam) {
-    double v = 0.0;
-    for (int w = 0; w < kAdThreads / 32; ++w) v += red[w][threadIdx.x];
-    a.part[(int64_t)blockIdx.x * kNParam + threadIdx.x] = v;
-  }
+  ad_block_partials(red, gacc, a.part);
 }
 
 // Sum the stencil adjoints referring to each node's phi and psi and add them
 // to the adjoints of the node's 9 pulled g (phi = sum g).
-__global__ void ad_gather(const double* __restrict__ phi, const double* __restrict__ lP,
-                          const double* __restrict__ lQ, int nx, int ny, int walls, double xi,
-                          double* __restrict__ aout) {
+template <typename R>
+__global__ void ad_gather(const R* __restrict__ phi, const R* __restrict__ lP,
+                          const R* __restrict__ lQ, int nx, int ny, int walls, R xi,
+                          R* __restrict__ aout) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(k % nx), y = (int)(k / nx);
-    double sp = lP[k], sq = 0.0;
+    R sp = lP[k], sq = R(0);
     gather_uses(lP, lQ, x, y, nx, ny, walls, sp, sq);
-    const double p = phi[k];
-    double dpsi = 0.0;  // d ln(a/b) / d phi inside the clip
-    if (p > 0.0 && p < 1.0) dpsi = 1.0 / (p + xi) + 1.0 / ((1.0 - p) + xi);
-    const double tot = sp + dpsi * sq;
+    const R p = phi[k];
+    const R dpsi = (p > R(0) && p < R(1)) ? dpsi_dphi(p, xi) : R(0);
+    const R tot = sp + dpsi * sq;
     for (int i = 0; i < 9; ++i) {
       int pl;
       const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
@@ -507,12 +528,15 @@ __global__ void ad_gather(const double* __restrict__ phi, const double* __restri
 
 // Adjoint of the initial state map (local part): phi0 -> hbar0, g_eq, f_eq,
 // phi0 u0.  Writes the local phi0 adjoint and the adjoint of lap(phi0).
+// The initial fields are FP64 (as lbm_init takes them) and so is this
+// once-per-gradient arithmetic; the adjoint state is of type R.
+template <typename R>
 struct AdInitArgs {
   const double* phi0;
   const double* u0;  // [2][n] or null
-  const double* ain;  // adjoint of S_0 [20][n]
-  double* lphi;       // [n]
-  double* llap;       // [n]
+  const R* ain;      // adjoint of S_0 [20][n]
+  double* lphi;      // [n]
+  double* llap;      // [n]
   double* part;
   int nx, ny;
   Phys<double> ph;
@@ -523,7 +547,8 @@ struct AdInitArgs {
   double u_top, u_bot;
 };
 
-__global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs a) {
+template <typename R>
+__global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs<R> a) {
   __shared__ double red[kAdThreads / 32][kNParam];
   const int nx = a.nx, ny = a.ny;
   const int64_t n = (int64_t)nx * ny;
@@ -590,18 +615,7 @@ __global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs a) 
     a.lphi[k] = lphi;
     a.llap[k] = -ph.kappa * lmu;
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int q = 0; q < kNParam; ++q) {
-    double v = gacc[q];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][q] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < kNParam) {
-    double v = 0.0;
-    for (int w = 0; w < kAdThreads / 32; ++w) v += red[w][threadIdx.x];
-    a.part[(int64_t)blockIdx.x * kNParam + threadIdx.x] = v;
-  }
+  ad_block_partials(red, gacc, a.part);
 }
 
 // lambda_phi0(y) = local - (10/3) llap(y) + sum over the nodes s whose
@@ -627,11 +641,12 @@ __global__ void ad_init_gather(const double* __restrict__ lphi, const double* __
   }
 }
 
-// The adjoint of phi = sum of pulled g, seeded from a field adjoint: every
-// node scatters dphi to the positions of its 9 pulled g (the f and phi*u
-// planes are cleared beforehand).
+// The adjoint of phi = sum of pulled g, seeded from an FP64 field adjoint:
+// every node scatters dphi to the positions of its 9 pulled g (the f and
+// phi*u planes are cleared beforehand).
+template <typename R>
 __global__ void ad_seed_phi(const double* __restrict__ dphi, int nx, int ny, int walls,
-                            double* __restrict__ aout) {
+                            R* __restrict__ aout) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
@@ -639,7 +654,7 @@ __global__ void ad_seed_phi(const double* __restrict__ dphi, int nx, int ny, int
     for (int i = 0; i < 9; ++i) {
       int pl;
       const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
-      aout[(9 + pl) * n + pos] = dphi[k];
+      aout[(9 + pl) * n + pos] = (R)dphi[k];
     }
   }
 }
@@ -658,30 +673,43 @@ __global__ void ad_sum_partials(const double* __restrict__ part, int nb, double*
   if (lane == 0) acc[q] += v;
 }
 
-// Scratch layout inside the caller's adjoint workspace (doubles).
+// Scratch layout inside the caller's adjoint workspace: 19 planes of n
+// values in the handle's precision (phi, psi, 9 phi-stencil and 8
+// psi-stencil adjoints), then the FP64 per-block partials and accumulators.
+// The initial-state adjoint reuses the stencil planes as two FP64 planes.
 struct AdScratch {
-  double *phi, *psi, *lP, *lQ, *part, *sums;
+  void *phi, *psi, *lP, *lQ;
+  double *part, *sums;
+  double *init_lphi, *init_llap;
 };
+
+size_t elem_bytes(const lbm_handle* h) { return h->precision == LBM_F64 ? 8 : 4; }
+
+size_t planes_bytes(int64_t n, size_t es) { return (19 * (size_t)n * es + 255) / 256 * 256; }
 
 AdScratch carve(lbm_handle* h) {
   const int64_t n = (int64_t)h->params[0].nx * h->params[0].ny;
-  double* b = (double*)h->adj_ws;
+  const size_t es = elem_bytes(h);
+  char* b = h->adj_ws;
   AdScratch s;
   s.phi = b;
-  s.psi = b + n;
-  s.lP = b + 2 * n;
-  s.lQ = b + 11 * n;
-  s.part = b + 19 * n;
+  s.psi = b + n * es;
+  s.lP = b + 2 * n * es;
+  s.lQ = b + 11 * n * es;
+  s.part = (double*)(b + planes_bytes(n, es));
   s.sums = s.part + kAdBlocks * kNParam;
+  s.init_lphi = (double*)s.lP;  // 9 planes of es bytes hold 2 FP64 planes
+  s.init_llap = s.init_lphi + n;
   return s;
 }
 
-size_t scratch_bytes(int64_t n) { return (size_t)(19 * n + kAdBlocks * kNParam + 8) * sizeof(double); }
+size_t scratch_bytes(int64_t n, size_t es) {
+  return planes_bytes(n, es) + (size_t)(kAdBlocks * kNParam + 8) * sizeof(double);
+}
 
 int check_handle(lbm_handle* h, bool need_ws) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (h->ncases != 1) return fail(LBM_ERR_ARG, "reverse mode needs a single-case handle");
-  if (h->precision != LBM_F64) return fail(LBM_ERR_ARG, "reverse mode needs an FP64 handle");
   if (need_ws && !h->adj_ws) return fail(LBM_ERR_WORKSPACE, "call lbm_adjoint_attach first");
   return LBM_OK;
 }
@@ -710,13 +738,23 @@ int take_grads(lbm_handle* h, double* out) {
   return LBM_OK;
 }
 
+template <typename R>
+const CaseDev<R>& case0(const lbm_handle* h) {
+  if constexpr (sizeof(R) == 4) return h->cf[0]; else return h->cd[0];
+}
+
+template <typename R>
+const Phys<R>& phys(const lbm_handle* h) {
+  if constexpr (sizeof(R) == 4) return h->pf; else return h->pd;
+}
+
 }  // namespace
 
 extern "C" {
 
 size_t lbm_adjoint_workspace_bytes(const lbm_handle* h) {
   if (!h || h->ncases != 1) return 0;
-  return scratch_bytes((int64_t)h->params[0].nx * h->params[0].ny);
+  return scratch_bytes((int64_t)h->params[0].nx * h->params[0].ny, elem_bytes(h));
 }
 
 int lbm_adjoint_attach(lbm_handle* h, void* d_scratch, size_t bytes) {
@@ -739,15 +777,20 @@ int lbm_adjoint_take_param_grads(lbm_handle* h, double* h_param_grads) {
   return take_grads(h, h_param_grads);
 }
 
-int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, double* d_adj_state) {
+int lbm_adjoint_seed_phi(lbm_handle* h, const double* d_dphi, void* d_adj_state) {
   int rc = check_handle(h, false);
   if (rc) return rc;
   if (!d_dphi || !d_adj_state) return fail(LBM_ERR_ARG, "null pointer");
   const lbm_params& p = h->params[0];
-  cudaError_t e = cudaMemsetAsync(d_adj_state, 0, 20 * sizeof(double) * p.nx * (size_t)p.ny,
+  cudaError_t e = cudaMemsetAsync(d_adj_state, 0, 20 * elem_bytes(h) * p.nx * (size_t)p.ny,
                                   h->stream);
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
-  ad_seed_phi<<<kAdBlocks, kAdThreads, 0, h->stream>>>(d_dphi, p.nx, p.ny, p.walls, d_adj_state);
+  if (h->precision == LBM_F32)
+    ad_seed_phi<float><<<kAdBlocks, kAdThreads, 0, h->stream>>>(d_dphi, p.nx, p.ny, p.walls,
+                                                                (float*)d_adj_state);
+  else
+    ad_seed_phi<double><<<kAdBlocks, kAdThreads, 0, h->stream>>>(d_dphi, p.nx, p.ny, p.walls,
+                                                                 (double*)d_adj_state);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   return LBM_OK;
@@ -759,51 +802,86 @@ namespace {
 
 // One adjoint step from the state S_t held in (fA, gA, JA) with plane stride
 // P at step index t (the handle's own buffers, or a snapshot).
-int adjoint_step_impl(lbm_handle* h, const double* fA, const double* gA, const double* JA,
-                      int64_t P, int64_t t, const void* d_adj_in, void* d_adj_out,
-                      double* h_param_grads) {
+template <typename R>
+int adjoint_step_impl(lbm_handle* h, const R* fA, const R* gA, const R* JA, int64_t P, int64_t t,
+                      const void* d_adj_in, void* d_adj_out, double* h_param_grads) {
   const lbm_params& p = h->params[0];
-  const CaseDev<double>& cd = h->cd[0];
+  const CaseDev<R>& cd = case0<R>(h);
   const bool coupled = h->flow == LBM_FLOW_COUPLED;
   AdScratch s = carve(h);
-  ad_phase<<<kAdBlocks, kAdThreads, 0, h->stream>>>(gA, P, p.nx, p.ny, p.walls, p.xi, s.phi,
-                                                    s.psi);
-  AdArgs a{};
+  ad_phase<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>(gA, P, p.nx, p.ny, p.walls, (R)p.xi,
+                                                       (R*)s.phi, (R*)s.psi);
+  AdArgs<R> a{};
   a.fA = coupled ? fA : nullptr;
   a.gA = gA;
   a.JA = JA;
   a.P = P;
   a.nx = p.nx;
   a.ny = p.ny;
-  a.phi = s.phi;
-  a.psi = s.psi;
-  a.ain = (const double*)d_adj_in;
-  a.aout = (double*)d_adj_out;
-  a.lP = s.lP;
-  a.lQ = s.lQ;
+  a.phi = (const R*)s.phi;
+  a.psi = (const R*)s.psi;
+  a.ain = (const R*)d_adj_in;
+  a.aout = (R*)d_adj_out;
+  a.lP = (R*)s.lP;
+  a.lQ = (R*)s.lQ;
   a.part = s.part;
-  a.ph = h->pd;
+  a.ph = phys<R>(h);
   a.rho_g = cd.rho_g;
   a.drho = cd.drho;
   a.mu_g = cd.mu_g;
   a.dmu = cd.dmu;
   a.sD7 = cd.sD7;
   a.hD7 = cd.hD7;
-  a.s7 = 1.0 / p.tau_f_l;
+  a.s7 = (R)(1.0 / p.tau_f_l);
   a.var_tau = cd.var_tau;
   a.coupled = coupled ? 1 : 0;
-  a.ct = coupled ? 0.0 : cospi((double)t / p.vortex_T) * p.vortex_U;
-  a.invW = 1.0 / p.W;
+  a.ct = (R)(coupled ? 0.0 : cospi((double)t / p.vortex_T) * p.vortex_U);
+  a.invW = (R)(1.0 / p.W);
+  a.walls = p.walls;
+  a.u_top = (R)(p.walls ? p.u_wall_top : 0.0);
+  a.u_bot = (R)(p.walls ? p.u_wall_bottom : 0.0);
+  if (!coupled) {  // the f planes and the tau_f entry stay zero
+    cudaError_t e = cudaMemsetAsync(d_adj_out, 0, 9 * sizeof(R) * p.nx * (size_t)p.ny, h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  }
+  ad_node<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
+  ad_gather<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>((const R*)s.phi, (const R*)s.lP,
+                                                        (const R*)s.lQ, p.nx, p.ny, p.walls,
+                                                        (R)p.xi, (R*)d_adj_out);
+  ad_sum_partials<<<1, 32 * kNParam, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  if (h_param_grads) return take_grads(h, h_param_grads);
+  return LBM_OK;
+}
+
+template <typename R>
+int adjoint_init_impl(lbm_handle* h, const double* d_phi0, const double* d_u0,
+                      const void* d_adj_state, double* d_adj_phi0, double* h_param_grads) {
+  const lbm_params& p = h->params[0];
+  AdScratch s = carve(h);
+  AdInitArgs<R> a{};
+  a.phi0 = d_phi0;
+  a.u0 = d_u0;
+  a.ain = (const R*)d_adj_state;
+  a.lphi = s.init_lphi;
+  a.llap = s.init_llap;
+  a.part = s.part;
+  a.nx = p.nx;
+  a.ny = p.ny;
+  a.ph = h->pd;
+  const bool coupled = h->flow == LBM_FLOW_COUPLED;
+  a.rho_g = coupled ? p.rho_g : 1.0;
+  a.drho = coupled ? p.rho_l - p.rho_g : 0.0;
+  a.coupled = coupled;
+  a.vortex = h->flow == LBM_FLOW_VORTEX;
+  a.vU = p.vortex_U;
   a.walls = p.walls;
   a.u_top = p.walls ? p.u_wall_top : 0.0;
   a.u_bot = p.walls ? p.u_wall_bottom : 0.0;
-  if (!coupled) {  // the f planes and the tau_f entry stay zero
-    cudaError_t e = cudaMemsetAsync(d_adj_out, 0, 9 * sizeof(double) * p.nx * (size_t)p.ny, h->stream);
-    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
-  }
-  ad_node<<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
-  ad_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.lP, s.lQ, p.nx, p.ny, p.walls,
-                                                     p.xi, (double*)d_adj_out);
+  ad_init_local<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
+  ad_init_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.init_lphi, s.init_llap, p.nx, p.ny,
+                                                          p.walls, d_adj_phi0);
   ad_sum_partials<<<1, 32 * kNParam, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
@@ -820,9 +898,14 @@ int lbm_adjoint_step(lbm_handle* h, const void* d_adj_in, void* d_adj_out, doubl
   if (rc) return rc;
   if (!d_adj_in || !d_adj_out) return fail(LBM_ERR_ARG, "null adjoint buffer");
   if (d_adj_in == d_adj_out) return fail(LBM_ERR_ARG, "d_adj_in and d_adj_out must differ");
+  if (h->precision == LBM_F32) {
+    const CaseDev<float>& cd = h->cf[0];
+    return adjoint_step_impl<float>(h, cd.f[h->parity], cd.g[h->parity], cd.J[h->parity],
+                                    cd.plane, h->t, d_adj_in, d_adj_out, h_param_grads);
+  }
   const CaseDev<double>& cd = h->cd[0];
-  return adjoint_step_impl(h, cd.f[h->parity], cd.g[h->parity], cd.J[h->parity], cd.plane, h->t,
-                           d_adj_in, d_adj_out, h_param_grads);
+  return adjoint_step_impl<double>(h, cd.f[h->parity], cd.g[h->parity], cd.J[h->parity], cd.plane,
+                                   h->t, d_adj_in, d_adj_out, h_param_grads);
 }
 
 int lbm_adjoint_step_from(lbm_handle* h, const void* d_state, int64_t t, const void* d_adj_in,
@@ -834,9 +917,49 @@ int lbm_adjoint_step_from(lbm_handle* h, const void* d_state, int64_t t, const v
   if (d_adj_in == d_adj_out || d_state == d_adj_out)
     return fail(LBM_ERR_ARG, "d_adj_out must differ from d_adj_in and d_state");
   const int64_t n = (int64_t)h->params[0].nx * h->params[0].ny;
+  if (h->precision == LBM_F32) {
+    const float* st = (const float*)d_state;
+    return adjoint_step_impl<float>(h, st, st + 9 * n, st + 18 * n, n, t, d_adj_in, d_adj_out,
+                                    h_param_grads);
+  }
   const double* st = (const double*)d_state;
-  return adjoint_step_impl(h, st, st + 9 * n, st + 18 * n, n, t, d_adj_in, d_adj_out,
-                           h_param_grads);
+  return adjoint_step_impl<double>(h, st, st + 9 * n, st + 18 * n, n, t, d_adj_in, d_adj_out,
+                                   h_param_grads);
+}
+
+int lbm_adjoint_sweep(lbm_handle* h, const void* d_states, int64_t stride_bytes, int64_t t0,
+                      int32_t count, void* d_adj, void* d_spare) {
+  int rc = check_handle(h, true);
+  if (rc) return rc;
+  if (!d_states || !d_adj || !d_spare || d_adj == d_spare)
+    return fail(LBM_ERR_ARG, "null or aliased buffers");
+  if (t0 < 0 || count < 0) return fail(LBM_ERR_ARG, "t0 and count must be >= 0");
+  const int64_t n = (int64_t)h->params[0].nx * h->params[0].ny;
+  const size_t es = elem_bytes(h);
+  if (count > 1 && stride_bytes < (int64_t)(20 * n * es))
+    return fail(LBM_ERR_ARG, "stride_bytes smaller than a state");
+  void* cur = d_adj;
+  void* nxt = d_spare;
+  for (int32_t j = count - 1; j >= 0; --j) {
+    const char* st = (const char*)d_states + (int64_t)j * stride_bytes;
+    if (h->precision == LBM_F32) {
+      const float* sf = (const float*)st;
+      rc = adjoint_step_impl<float>(h, sf, sf + 9 * n, sf + 18 * n, n, t0 + j, cur, nxt, nullptr);
+    } else {
+      const double* sd = (const double*)st;
+      rc = adjoint_step_impl<double>(h, sd, sd + 9 * n, sd + 18 * n, n, t0 + j, cur, nxt,
+                                     nullptr);
+    }
+    if (rc) return rc;
+    void* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  if (cur != d_adj) {  // an odd count ends in the spare buffer
+    cudaError_t e = cudaMemcpyAsync(d_adj, cur, 20 * n * es, cudaMemcpyDeviceToDevice, h->stream);
+    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return LBM_OK;
 }
 
 int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
@@ -844,35 +967,9 @@ int lbm_adjoint_init(lbm_handle* h, const double* d_phi0, const double* d_u0,
   int rc = check_handle(h, true);
   if (rc) return rc;
   if (!d_phi0 || !d_adj_state || !d_adj_phi0) return fail(LBM_ERR_ARG, "null pointer");
-  const lbm_params& p = h->params[0];
-  const CaseDev<double>& cd = h->cd[0];
-  AdScratch s = carve(h);
-  AdInitArgs a{};
-  a.phi0 = d_phi0;
-  a.u0 = d_u0;
-  a.ain = (const double*)d_adj_state;
-  a.lphi = s.phi;  // reuse scratch planes
-  a.llap = s.psi;
-  a.part = s.part;
-  a.nx = p.nx;
-  a.ny = p.ny;
-  a.ph = h->pd;
-  a.rho_g = cd.rho_g;
-  a.drho = cd.drho;
-  a.coupled = h->flow == LBM_FLOW_COUPLED;
-  a.vortex = h->flow == LBM_FLOW_VORTEX;
-  a.vU = p.vortex_U;
-  a.walls = p.walls;
-  a.u_top = p.walls ? p.u_wall_top : 0.0;
-  a.u_bot = p.walls ? p.u_wall_bottom : 0.0;
-  ad_init_local<<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
-  ad_init_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.phi, s.psi, p.nx, p.ny, p.walls,
-                                                          d_adj_phi0);
-  ad_sum_partials<<<1, 32 * kNParam, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
-  if (h_param_grads) return take_grads(h, h_param_grads);
-  return LBM_OK;
+  if (h->precision == LBM_F32)
+    return adjoint_init_impl<float>(h, d_phi0, d_u0, d_adj_state, d_adj_phi0, h_param_grads);
+  return adjoint_init_impl<double>(h, d_phi0, d_u0, d_adj_state, d_adj_phi0, h_param_grads);
 }
 
 }  // extern "C"

@@ -15,6 +15,7 @@
 #include "launch.h"
 #include "lbm_handle.h"
 #include "lbm_layout.h"
+#include "lbm_trace.h"
 
 using lbmk::CaseDev;
 using lbmk::Item;
@@ -110,19 +111,52 @@ int check_params(const lbm_params* c, int n) {
 
 size_t elem_size(int precision) { return precision == LBM_F64 ? 8 : 4; }
 
-// Work items: strips of bx columns, runs of `rows` rows.
+// Chains: contiguous case ranges of nearly equal node counts.
+std::vector<int> split_chains(const lbm_params* c, int n, int nchains) {
+  nchains = std::max(1, std::min(nchains, n));
+  int64_t total = 0;
+  for (int k = 0; k < n; ++k) total += (int64_t)c[k].nx * c[k].ny;
+  std::vector<int> b(nchains + 1, 0);
+  b[nchains] = n;
+  int64_t acc = 0;
+  int k = 0;
+  for (int ch = 1; ch < nchains; ++ch) {
+    const int64_t want = total * ch / nchains;
+    while (k < n - (nchains - ch) && (k < b[ch - 1] + 1 || acc + (int64_t)c[k].nx * c[k].ny / 2 < want))
+      acc += (int64_t)c[k].nx * c[k].ny, ++k;
+    b[ch] = k;
+  }
+  return b;
+}
+
+// Work items: strips of bx columns, runs of `rows` rows.  Items are grouped
+// by chain; within a chain the cases go largest first (their items are the
+// slowest), so the small ones fill the end of the step.  The items of one
+// case stay contiguous: [beg[k], end[k]).
 std::vector<Item> make_items(const lbm_params* c, int n, const Tiling& t,
-                             std::vector<int>* beg, std::vector<int>* end) {
+                             const std::vector<int>& chain_case, std::vector<int>* beg,
+                             std::vector<int>* end, std::vector<int>* chain_item) {
   std::vector<Item> it;
   beg->assign(n, 0);
   end->assign(n, 0);
-  for (int k = 0; k < n; ++k) {
-    (*beg)[k] = (int)it.size();
-    for (int y0 = 0; y0 < c[k].ny; y0 += t.rows)
-      for (int x0 = 0; x0 < c[k].nx; x0 += t.bx)
-        it.push_back(Item{k, x0, y0, std::min(t.rows, c[k].ny - y0)});
-    (*end)[k] = (int)it.size();
+  const int nch = (int)chain_case.size() - 1;
+  chain_item->assign(nch + 1, 0);
+  for (int ch = 0; ch < nch; ++ch) {
+    (*chain_item)[ch] = (int)it.size();
+    std::vector<int> order;
+    for (int k = chain_case[ch]; k < chain_case[ch + 1]; ++k) order.push_back(k);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      return (int64_t)c[a].nx * c[a].ny > (int64_t)c[b].nx * c[b].ny;
+    });
+    for (int k : order) {
+      (*beg)[k] = (int)it.size();
+      for (int y0 = 0; y0 < c[k].ny; y0 += t.rows)
+        for (int x0 = 0; x0 < c[k].nx; x0 += t.bx)
+          it.push_back(Item{k, x0, y0, std::min(t.rows, c[k].ny - y0)});
+      (*end)[k] = (int)it.size();
+    }
   }
+  (*chain_item)[nch] = (int)it.size();
   return it;
 }
 
@@ -176,6 +210,8 @@ Layout make_layout(const lbm_params* c, int n, int n_items, int total_regions) {
   off = align_up(off + (size_t)n_items * lbmk::kMaxRegions * sizeof(double));
   L.vol = off;
   off = align_up(off + (size_t)std::max(total_regions, n * lbmk::kMaxRegions) * sizeof(double));
+  L.init = off;
+  off = align_up(off + (size_t)n * sizeof(lbmk::InitSrc));
   int64_t maxp = 0;
   for (int k = 0; k < n; ++k) maxp = std::max<int64_t>(maxp, (int64_t)c[k].nx * c[k].ny);
   L.staging = off;
@@ -337,12 +373,15 @@ StepArgs<T> step_args(const lbm_handle* h, int parity, int64_t t_off) {
   a.t_off = t_off;
   a.parity = parity;
   a.flags = h->flags;
+  a.wait_cycles = h->wait_cycles;
   return a;
 }
 
 int launch_persist(lbm_handle* h, cudaStream_t s, int parity, int nsteps, int flip) {
   const bool coupled = h->flow == LBM_FLOW_COUPLED;
   const int n = (int)h->items.size();
+  // a launch whose barrier wait gave up leaves arrivals counted: start at 0
+  LBM_CUDA(cudaMemsetAsync(bar_count(h), 0, sizeof(unsigned int), s));
   cudaError_t e;
   if (h->precision == LBM_F32)
     e = lbmk::launch_persistent<float>(step_args<float>(h, parity, 0), h->tile.bx, coupled, n,
@@ -354,45 +393,72 @@ int launch_persist(lbm_handle* h, cudaStream_t s, int parity, int nsteps, int fl
   return LBM_OK;
 }
 
-// Enqueue `count` consecutive steps starting from source buffer `parity`,
-// then advance the device clock.
-int enqueue_steps(lbm_handle* h, cudaStream_t s, int parity, int count) {
+// Enqueue `count` consecutive steps starting from source buffer `parity`.
+// Each chain runs on its own stream (chain 0 on s, the others on the
+// handle's auxiliary streams, forked from and joined back into s), so that
+// under stream capture the chains become parallel branches of one graph.
+// flip = false: every step reads the same source buffers (autotuning
+// trials; the state is not changed).  vol: fused per-case volumes into
+// h->track.  clock: advance the device step clock by `count` at the end.
+int enqueue_steps(lbm_handle* h, cudaStream_t s, int parity, int count, bool flip, bool vol,
+                  bool clock) {
   const bool coupled = h->flow == LBM_FLOW_COUPLED;
-  const int n = (int)h->items.size();
-  for (int j = 0; j < count; ++j) {
-    const int par = (parity + j) & 1;
-    cudaError_t e;
-    if (h->precision == LBM_F32) {
-      StepArgs<float> a = step_args<float>(h, par, j);
-      a.vol_part = h->track ? h->part : nullptr;
-      e = lbmk::launch_step<float>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), n, s);
-      if (e == cudaSuccess && h->track)
-        e = lbmk::launch_volume_final<float>((const CaseDev<float>*)h->cases_dev, h->ncases,
-                                             h->part, h->track, s);
-    } else {
-      StepArgs<double> a = step_args<double>(h, par, j);
-      a.vol_part = h->track ? h->part : nullptr;
-      e = lbmk::launch_step<double>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), n, s);
-      if (e == cudaSuccess && h->track)
-        e = lbmk::launch_volume_final<double>((const CaseDev<double>*)h->cases_dev, h->ncases,
-                                              h->part, h->track, s);
-    }
-    if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+  const int nch = h->nchains;
+  if (nch > 1) {
+    LBM_CUDA(cudaEventRecord(h->fork_ev, s));
+    for (int c = 1; c < nch; ++c) LBM_CUDA(cudaStreamWaitEvent(h->aux[c - 1], h->fork_ev, 0));
   }
-  LBM_CUDA(lbmk::launch_clock(h->t_dev, count, s));
+  for (int c = 0; c < nch; ++c) {
+    cudaStream_t sc = c == 0 ? s : h->aux[c - 1];
+    const int i0 = h->chain_item[c], ni = h->chain_item[c + 1] - i0;
+    const int c0 = h->chain_case[c], nc = h->chain_case[c + 1] - c0;
+    for (int j = 0; j < count; ++j) {
+      const int par = flip ? (parity + j) & 1 : parity;
+      const int64_t toff = flip ? j : 0;
+      cudaError_t e;
+      if (h->precision == LBM_F32) {
+        StepArgs<float> a = step_args<float>(h, par, toff);
+        a.items = h->items_dev + i0;
+        a.vol_part = (vol && h->track) ? h->part + (int64_t)i0 * lbmk::kMaxRegions : nullptr;
+        e = lbmk::launch_step<float>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), ni, sc);
+        if (e == cudaSuccess && vol && h->track)
+          e = lbmk::launch_volume_final<float>((const CaseDev<float>*)h->cases_dev + c0, nc,
+                                               h->part, h->track, sc);
+      } else {
+        StepArgs<double> a = step_args<double>(h, par, toff);
+        a.items = h->items_dev + i0;
+        a.vol_part = (vol && h->track) ? h->part + (int64_t)i0 * lbmk::kMaxRegions : nullptr;
+        e = lbmk::launch_step<double>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), ni, sc);
+        if (e == cudaSuccess && vol && h->track)
+          e = lbmk::launch_volume_final<double>((const CaseDev<double>*)h->cases_dev + c0, nc,
+                                                h->part, h->track, sc);
+      }
+      if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+    }
+  }
+  for (int c = 1; c < nch; ++c) {
+    LBM_CUDA(cudaEventRecord(h->join_ev[c - 1], h->aux[c - 1]));
+    LBM_CUDA(cudaStreamWaitEvent(s, h->join_ev[c - 1], 0));
+  }
+  if (clock) LBM_CUDA(lbmk::launch_clock(h->t_dev, count, s));
   return LBM_OK;
 }
 
 void drop_graph(lbm_handle* h) {
-  if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  h->gexec = nullptr;
-  h->graph_parity = -1;
+  // launches of these graphs that are still queued must run first
+  if (!h->graphs.empty()) cudaStreamSynchronize(h->stream);
+  for (auto& g : h->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
 }
 
-int build_graph(lbm_handle* h) {
-  drop_graph(h);
+// Capture `count` steps from source buffer `parity` (with or without flipping
+// buffers) on the private capture stream and instantiate them.
+int capture_steps(lbm_handle* h, int parity, int count, bool flip, bool vol, bool clock,
+                  cudaGraphExec_t* out) {
+  *out = nullptr;
   LBM_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  int rc = enqueue_steps(h, h->cap, h->parity, kGraphSteps);
+  int rc = enqueue_steps(h, h->cap, parity, count, flip, vol, clock);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap, &g);
   if (rc != LBM_OK) {
@@ -400,13 +466,37 @@ int build_graph(lbm_handle* h) {
     return rc;
   }
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&h->gexec, g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    h->gexec = nullptr;
+    *out = nullptr;
     return fail(LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
-  h->graph_parity = h->parity;
+  return LBM_OK;
+}
+
+constexpr size_t kGraphCache = 8;
+
+// The graph of `count` steps from source buffer `parity`, built on first use.
+int step_graph(lbm_handle* h, int count, int parity, cudaGraphExec_t* out) {
+  for (const auto& g : h->graphs)
+    if (g.count == count && g.parity == parity) {
+      *out = g.exec;
+      return LBM_OK;
+    }
+  lbmk::StepGraph g;
+  g.count = count;
+  g.parity = parity;
+  int rc = capture_steps(h, parity, count, true, true, true, &g.exec);
+  if (rc) return rc;
+  if (h->graphs.size() >= kGraphCache) {
+    // the oldest entry goes, once its queued launches have run
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+    cudaGraphExecDestroy(h->graphs.front().exec);
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back(g);
+  *out = g.exec;
   return LBM_OK;
 }
 
@@ -536,6 +626,28 @@ size_t state_bytes_case(const lbm_handle* h, int k) {
   return (size_t)planes * n * es;
 }
 
+// New tiling or chain count: rebuild the item table and the case table.
+int retile(lbm_handle* h, const Tiling& t, int nchains) {
+  std::vector<int> b, e, ci;
+  std::vector<int> cc = split_chains(h->params.data(), h->ncases, nchains);
+  std::vector<Item> it = make_items(h->params.data(), h->ncases, t, cc, &b, &e, &ci);
+  if ((int64_t)it.size() > max_items(h->params.data(), h->ncases))
+    return fail(LBM_ERR_ARG, "tiling needs more work items than the workspace holds");
+  drop_graph(h);
+  // the previous step's kernels may still read the item table
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  h->tile = t;
+  h->nchains = (int)cc.size() - 1;
+  h->chain_case.swap(cc);
+  h->chain_item.swap(ci);
+  h->items.swap(it);
+  h->item_begin.swap(b);
+  h->item_end.swap(e);
+  LBM_CUDA(cudaMemcpyAsync(h->items_dev, h->items.data(), h->items.size() * sizeof(Item),
+                           cudaMemcpyHostToDevice, h->stream));
+  return upload_cases(h);
+}
+
 }  // namespace
 
 namespace lbmk {
@@ -572,6 +684,7 @@ size_t lbm_workspace_bytes(const lbm_params* cases, int32_t ncases) {
 int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t ws_bytes,
              const double* const* h_phi0, const double* const* h_u0, void* stream,
              lbm_handle** out) {
+  lbmk::TraceRange trace("lbm_init");
   if (!out) return fail(LBM_ERR_ARG, "out is null");
   *out = nullptr;
   int rc = check_params(cases, ncases);
@@ -589,7 +702,10 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   h->flow = cases[0].flow;
   h->stream = (cudaStream_t)stream;
   h->tile = choose_tiling(cases, ncases);
-  h->items = make_items(cases, ncases, h->tile, &h->item_begin, &h->item_end);
+  h->nchains = std::min(2, ncases);
+  h->chain_case = split_chains(cases, ncases, h->nchains);
+  h->items = make_items(cases, ncases, h->tile, h->chain_case, &h->item_begin, &h->item_end,
+                        &h->chain_item);
   h->nregions.assign(ncases, 1);
   h->vol_base.resize(ncases);
   for (int k = 0; k < ncases; ++k) h->vol_base[k] = k;
@@ -628,6 +744,12 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   };
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(fail(LBM_ERR_CUDA, "cannot create capture stream"));
+  for (int c = 0; c < lbmk::kMaxChains - 1; ++c)
+    if (cudaStreamCreateWithFlags(&h->aux[c], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join_ev[c], cudaEventDisableTiming) != cudaSuccess)
+      return cleanup(fail(LBM_ERR_CUDA, "cannot create chain streams"));
+  if (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(LBM_ERR_CUDA, "cannot create chain events"));
   {
     cudaError_t e = h->precision == LBM_F32 ? lbmk::prepare_tma<float>() : lbmk::prepare_tma<double>();
     if (e != cudaSuccess)
@@ -641,70 +763,80 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   rc = upload_cases(h);
   if (rc) return cleanup(rc);
 
+  // Initial fields.  Where the device can read the caller's arrays itself
+  // (page-locked host memory, over the CPU-GPU link, or device memory), the
+  // init kernel reads them in place; other (pageable) arrays are first
+  // copied into the case's buffer of parity 1 (f planes, or g planes
+  // without hydrodynamics), which the init kernel does not write and the
+  // first step overwrites.  Then one launch initialises every case.  One
+  // synchronisation at the end: on return the host arrays are no longer read.
   const bool vortex = h->flow == LBM_FLOW_VORTEX;
-  // The initial fields of each case go straight into that case's buffer of
-  // parity 1 (f planes, or g planes without hydrodynamics), which the init
-  // kernel does not write and the first step overwrites.  The uploads run on
-  // a second stream, so that the upload of one case overlaps the (FP64)
-  // init kernel of the one before; each init waits for its own upload on an
-  // event.  One synchronisation at the end: on return the host buffers are
-  // no longer read.
   const size_t es = elem_size(h->precision);
-  cudaStream_t up = nullptr;
-  cudaEvent_t ev[8] = {};
-  auto release = [&]() {
-    if (up) cudaStreamSynchronize(up);
-    for (auto& e : ev)
-      if (e) cudaEventDestroy(e);
-    if (up) cudaStreamDestroy(up);
+  std::vector<lbmk::InitSrc> src(ncases);
+  auto readable = [](const void* p) -> const double* {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+      cudaGetLastError();  // clear the error of an unknown pointer
+      return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged ||
+        a.type == cudaMemoryTypeHost)
+      return (const double*)a.devicePointer;
+    return nullptr;
   };
-  bool ok = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) == cudaSuccess;
-  for (auto& e : ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
-  // the uploads start after what the caller's stream already holds
-  ok = ok && cudaEventRecord(ev[0], h->stream) == cudaSuccess &&
-       cudaStreamWaitEvent(up, ev[0], 0) == cudaSuccess;
-  if (!ok) {
-    release();
-    return cleanup(fail(LBM_ERR_CUDA, "upload stream set-up failed"));
-  }
   for (int k = 0; k < ncases; ++k) {
     const lbm_params& p = cases[k];
     const int64_t n = (int64_t)p.nx * p.ny;
     const size_t pb = (size_t)h->L.plane[k] * es;
     double* st = (double*)(h->ws + (vortex ? h->L.g[k] : h->L.f[k]) + 9 * pb);
-    const double* u0d = nullptr;
-    cudaError_t e = cudaMemcpyAsync(st, h_phi0[k], n * sizeof(double), cudaMemcpyHostToDevice, up);
-    if (e == cudaSuccess && !vortex && h_u0 && h_u0[k]) {
-      e = cudaMemcpyAsync(st + n, h_u0[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice, up);
-      u0d = st + n;
+    lbmk::InitSrc& q = src[k];
+    q.rho_g = vortex ? 1.0 : p.rho_g;
+    q.drho = vortex ? 0.0 : p.rho_l - p.rho_g;
+    q.phi = readable(h_phi0[k]);
+    if (!q.phi) {
+      if (cudaMemcpyAsync(st, h_phi0[k], n * sizeof(double), cudaMemcpyHostToDevice,
+                          h->stream) != cudaSuccess)
+        return cleanup(fail(LBM_ERR_CUDA, "initial-field upload failed"));
+      q.phi = st;
     }
-    if (e == cudaSuccess) e = cudaEventRecord(ev[k & 7], up);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(h->stream, ev[k & 7], 0);
-    if (e != cudaSuccess) {
-      release();
-      return cleanup(fail(LBM_ERR_CUDA, "initial-field upload failed"));
-    }
-    const double beta4 = 4.0 * (12.0 * p.sigma / p.W), kappa = 1.5 * p.sigma * p.W;
-    const double rho_g = vortex ? 1.0 : p.rho_g, drho = vortex ? 0.0 : p.rho_l - p.rho_g;
-    if (h->precision == LBM_F32)
-      e = lbmk::launch_init<float>(h->cf[k], beta4, kappa, p.lambda, rho_g, drho, st, u0d,
-                                   vortex, p.vortex_U, 0, h->stream);
-    else
-      e = lbmk::launch_init<double>(h->cd[k], beta4, kappa, p.lambda, rho_g, drho, st, u0d,
-                                    vortex, p.vortex_U, 0, h->stream);
-    if (e != cudaSuccess) {
-      release();
-      return cleanup(fail(LBM_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e)));
+    q.u = nullptr;
+    if (!vortex && h_u0 && h_u0[k]) {
+      q.u = readable(h_u0[k]);
+      if (!q.u) {
+        if (cudaMemcpyAsync(st + n, h_u0[k], 2 * n * sizeof(double), cudaMemcpyHostToDevice,
+                            h->stream) != cudaSuccess)
+          return cleanup(fail(LBM_ERR_CUDA, "initial-field upload failed"));
+        q.u = st + n;
+      }
     }
   }
-  const cudaError_t es2 = cudaStreamSynchronize(h->stream);
-  release();
-  if (es2 != cudaSuccess) return cleanup(fail(LBM_ERR_CUDA, "init sync failed"));
+  const lbmk::InitSrc* src_dev = (const lbmk::InitSrc*)(h->ws + h->L.init);
+  if (cudaMemcpyAsync((void*)src_dev, src.data(), src.size() * sizeof(lbmk::InitSrc),
+                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return cleanup(fail(LBM_ERR_CUDA, "init table upload failed"));
+  {
+    const lbm_params& p = cases[0];  // launch-uniform physics
+    const double beta4 = 4.0 * (12.0 * p.sigma / p.W), kappa = 1.5 * p.sigma * p.W;
+    const int ni = (int)h->items.size();
+    cudaError_t e;
+    if (h->precision == LBM_F32)
+      e = lbmk::launch_init_items<float>((const CaseDev<float>*)h->cases_dev, h->items_dev, ni,
+                                         h->tile.bx, src_dev, beta4, kappa, p.lambda, vortex,
+                                         p.vortex_U, 0, h->stream);
+    else
+      e = lbmk::launch_init_items<double>((const CaseDev<double>*)h->cases_dev, h->items_dev, ni,
+                                          h->tile.bx, src_dev, beta4, kappa, p.lambda, vortex,
+                                          p.vortex_U, 0, h->stream);
+    if (e != cudaSuccess) return cleanup(fail(LBM_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e)));
+  }
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return cleanup(fail(LBM_ERR_CUDA, "init sync failed"));
   *out = h;
   return LBM_OK;
 }
 
 int lbm_step(lbm_handle* h, int64_t nsteps) {
+  lbmk::TraceRange trace("lbm_step");
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps < 0");
   if (h->kernel == 3 && !h->track) {
@@ -720,32 +852,33 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     }
     return LBM_OK;
   }
+  // chunks of kGraphSteps steps, then the remainder, each a cached graph
   while (nsteps > 0) {
-    if (nsteps >= kGraphSteps) {
-      if (!h->gexec || h->graph_parity != h->parity) {
-        if (h->gexec && h->graph_parity != h->parity) {
-          // realign the buffer parity with the captured graph by one step
-          int rc = enqueue_steps(h, h->stream, h->parity, 1);
-          if (rc) return rc;
-          h->parity ^= 1;
-          h->t += 1;
-          nsteps -= 1;
-          continue;
-        }
-        int rc = build_graph(h);
-        if (rc) return rc;
-      }
-      LBM_CUDA(cudaGraphLaunch(h->gexec, h->stream));
-      h->t += kGraphSteps;  // kGraphSteps is even: parity unchanged
-      nsteps -= kGraphSteps;
-    } else {
-      const int cnt = (int)nsteps;
-      int rc = enqueue_steps(h, h->stream, h->parity, cnt);
-      if (rc) return rc;
-      h->parity ^= (cnt & 1);
-      h->t += cnt;
-      nsteps = 0;
-    }
+    const int cnt = (int)std::min<int64_t>(nsteps, kGraphSteps);
+    cudaGraphExec_t gx = nullptr;
+    int rc = step_graph(h, cnt, h->parity, &gx);
+    if (rc) return rc;
+    LBM_CUDA(cudaGraphLaunch(gx, h->stream));
+    h->parity ^= (cnt & 1);
+    h->t += cnt;
+    nsteps -= cnt;
+  }
+  return LBM_OK;
+}
+
+int lbm_prepare_steps(lbm_handle* h, int64_t nsteps) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps < 0");
+  if (h->kernel == 3 && !h->track) return LBM_OK;  // one cooperative launch, nothing to capture
+  int parity = h->parity;
+  while (nsteps > 0) {
+    const int cnt = (int)std::min<int64_t>(nsteps, kGraphSteps);
+    cudaGraphExec_t gx = nullptr;
+    int rc = step_graph(h, cnt, parity, &gx);
+    if (rc) return rc;
+    parity ^= (cnt & 1);
+    nsteps -= cnt;
+    if (cnt == kGraphSteps && nsteps >= kGraphSteps) nsteps = nsteps % kGraphSteps;  // same graph
   }
   return LBM_OK;
 }
@@ -800,6 +933,7 @@ int32_t lbm_get_kernel(const lbm_handle* h) {
 
 int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel, int32_t* best_bx,
                  int32_t* best_rows, double* best_ms) {
+  lbmk::TraceRange trace("lbm_autotune");
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (trials < 1 || trials > 100) return fail(LBM_ERR_ARG, "trials must lie in [1, 100]");
   const bool coupled = h->flow == LBM_FLOW_COUPLED;
@@ -812,35 +946,12 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel, int32_t* b
   // Trial launches read the current source buffers and write the other
   // buffer set (populations and phi*u), which the next real step overwrites
   // completely: the state is not changed and the clock does not advance.
-  auto trial = [&](int n, cudaStream_t st) -> cudaError_t {
-    for (int j = 0; j < n; ++j) {
-      cudaError_t e;
-      if (h->precision == LBM_F32)
-        e = lbmk::launch_step<float>(step_args<float>(h, h->parity, 0), h->tile.bx, coupled,
-                                     lbmk::kModeStep, use_tma(h), (int)h->items.size(), st);
-      else
-        e = lbmk::launch_step<double>(step_args<double>(h, h->parity, 0), h->tile.bx, coupled,
-                                      lbmk::kModeStep, use_tma(h), (int)h->items.size(), st);
-      if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-  };
-  // lbm_step replays the step kernels of variants 1 and 2 as CUDA graphs:
-  // time their trials the same way, as one captured graph of n launches
-  // (replayed once untimed, then timed).  At least 8 trial steps, so that a
-  // small grid is timed in steady state rather than by its launch overhead.
+  // lbm_step replays the step kernels of variants 1 and 2 as CUDA graphs
+  // (one branch per chain): time their trials the same way, as one captured
+  // graph of n steps (replayed once untimed, then timed).  At least 8 trial
+  // steps, so that a small grid is timed in steady state rather than by its
+  // launch overhead.
   const int n_trial = trials < 8 ? 8 : trials;
-  auto graph_trial = [&](cudaGraphExec_t* gx) -> cudaError_t {
-    cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return e;
-    e = trial(n_trial, h->cap);
-    cudaGraph_t g = nullptr;
-    const cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
-    if (e == cudaSuccess) e = e2;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(gx, g, 0);
-    if (g) cudaGraphDestroy(g);
-    return e;
-  };
   const Tiling keep_tile = h->tile;
   const int keep_kernel = h->kernel;
   double best = 1e300;
@@ -851,7 +962,7 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel, int32_t* b
     if (kv == 2 && !h->tma_ok) continue;
     if (kv == 3 && total_nodes(h) > kPersistMaxNodes) continue;
     for (int bx : {128, 64, 32}) {
-      for (int rows : {2, 4, 8, 16, 32, 64}) {
+      for (int rows : {2, 4, 8, 16, 32, 64, 128}) {
         h->kernel = kv;
         rc = lbm_set_tiling(h, bx, rows);
         if (rc != LBM_OK) break;
@@ -863,8 +974,9 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel, int32_t* b
           if (rc != LBM_OK) break;
         } else {
           cudaGraphExec_t gx = nullptr;
-          e = graph_trial(&gx);
-          if (e == cudaSuccess) e = cudaGraphLaunch(gx, h->stream);
+          rc = capture_steps(h, h->parity, n_trial, false, false, false, &gx);
+          if (rc != LBM_OK) break;
+          e = cudaGraphLaunch(gx, h->stream);
           if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
           if (e == cudaSuccess) e = cudaGraphLaunch(gx, h->stream);
           if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
@@ -922,21 +1034,25 @@ int lbm_set_tiling(lbm_handle* h, int32_t bx, int32_t rows) {
   Tiling t;
   t.bx = bx;
   t.rows = rows;
-  std::vector<int> b, e;
-  std::vector<Item> it = make_items(h->params.data(), h->ncases, t, &b, &e);
-  if ((int64_t)it.size() > max_items(h->params.data(), h->ncases))
-    return fail(LBM_ERR_ARG, "tiling needs more work items than the workspace holds");
-  // the previous step's kernels may still read the item table
-  LBM_CUDA(cudaStreamSynchronize(h->stream));
-  h->tile = t;
-  h->items.swap(it);
-  h->item_begin.swap(b);
-  h->item_end.swap(e);
-  LBM_CUDA(cudaMemcpyAsync(h->items_dev, h->items.data(), h->items.size() * sizeof(Item),
-                           cudaMemcpyHostToDevice, h->stream));
-  drop_graph(h);
-  return upload_cases(h);
+  return retile(h, t, h->nchains);
 }
+
+int lbm_set_wait_limit(lbm_handle* h, int64_t cycles) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (cycles < 0) cycles = lbmk::kWaitCycles;
+  if (cycles != h->wait_cycles) drop_graph(h);
+  h->wait_cycles = cycles;
+  return LBM_OK;
+}
+
+int lbm_set_chains(lbm_handle* h, int32_t nchains) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (nchains < 1 || nchains > lbmk::kMaxChains)
+    return fail(LBM_ERR_ARG, "nchains must lie in [1, 4]");
+  return retile(h, h->tile, std::min<int>(nchains, h->ncases));
+}
+
+int32_t lbm_get_chains(const lbm_handle* h) { return h ? h->nchains : 0; }
 
 int lbm_track_volume(lbm_handle* h, double* d_out) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
@@ -951,6 +1067,7 @@ int lbm_track_volume(lbm_handle* h, double* d_out) {
 }
 
 int lbm_volume_async(lbm_handle* h, double* d_out) {
+  lbmk::TraceRange trace("lbm_volume");
   if (!h || !d_out) return fail(LBM_ERR_ARG, "null argument");
   cudaError_t e;
   const int n = (int)h->items.size();
@@ -1088,7 +1205,8 @@ int lbm_load(lbm_handle* h, const void* h_buf, size_t bytes) {
 
 size_t lbm_snapshot_bytes(const lbm_handle* h, int32_t c) {
   if (!h || c < 0 || c >= h->ncases) return 0;
-  return (size_t)20 * h->params[c].nx * h->params[c].ny * elem_size(h->precision);
+  const int planes = h->precision == LBM_F32 ? 21 : 20;  // FP32: + low part of g_0
+  return (size_t)planes * h->params[c].nx * h->params[c].ny * elem_size(h->precision);
 }
 
 // Device copy of the state of case c: [f*: 9][g*: 9][phi*u: 2] planes of
@@ -1110,6 +1228,9 @@ int lbm_snapshot(lbm_handle* h, int32_t c, void* d_buf) {
                              cudaMemcpyDeviceToDevice, h->stream));
   LBM_CUDA(cudaMemcpy2DAsync(out + 18 * nb, nb, h->ws + h->L.J[c] + h->parity * 2 * pb, pb, nb, 2,
                              cudaMemcpyDeviceToDevice, h->stream));
+  if (es == 4)  // FP32: the low part of the g_0 float pair
+    LBM_CUDA(cudaMemcpyAsync(out + 20 * nb, h->ws + h->L.glo[c] + h->parity * pb, nb,
+                             cudaMemcpyDeviceToDevice, h->stream));
   return LBM_OK;
 }
 
@@ -1127,8 +1248,25 @@ int lbm_restore(lbm_handle* h, int32_t c, const void* d_buf) {
                              cudaMemcpyDeviceToDevice, h->stream));
   LBM_CUDA(cudaMemcpy2DAsync(h->ws + h->L.J[c] + h->parity * 2 * pb, pb, in + 18 * nb, nb, nb, 2,
                              cudaMemcpyDeviceToDevice, h->stream));
-  if (es == 4)  // FP32: the snapshot holds g_0 rounded to its high part
-    LBM_CUDA(cudaMemsetAsync(h->ws + h->L.glo[c] + h->parity * pb, 0, nb, h->stream));
+  if (es == 4)  // FP32: the low part of the g_0 float pair
+    LBM_CUDA(cudaMemcpyAsync(h->ws + h->L.glo[c] + h->parity * pb, in + 20 * nb, nb,
+                             cudaMemcpyDeviceToDevice, h->stream));
+  return LBM_OK;
+}
+
+int lbm_record_steps(lbm_handle* h, int64_t count, void* d_states, int64_t stride_bytes) {
+  lbmk::TraceRange trace("lbm_record_steps");
+  if (!h || !d_states) return fail(LBM_ERR_ARG, "null argument");
+  if (h->ncases != 1) return fail(LBM_ERR_ARG, "recording needs a single-case handle");
+  if (count < 0) return fail(LBM_ERR_ARG, "count < 0");
+  if (count > 1 && stride_bytes < (int64_t)lbm_snapshot_bytes(h, 0))
+    return fail(LBM_ERR_ARG, "stride_bytes smaller than a snapshot");
+  for (int64_t j = 0; j < count; ++j) {
+    int rc = lbm_snapshot(h, 0, (char*)d_states + j * stride_bytes);
+    if (rc) return rc;
+    rc = lbm_step(h, 1);
+    if (rc) return rc;
+  }
   return LBM_OK;
 }
 
@@ -1155,6 +1293,11 @@ void lbm_destroy(lbm_handle* h) {
   if (!h) return;
   drop_graph(h);
   if (h->cap) cudaStreamDestroy(h->cap);
+  for (int c = 0; c < lbmk::kMaxChains - 1; ++c) {
+    if (h->aux[c]) cudaStreamDestroy(h->aux[c]);
+    if (h->join_ev[c]) cudaEventDestroy(h->join_ev[c]);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   delete h;
 }
 

@@ -60,69 +60,108 @@ __device__ __forceinline__ double phi_at(const CaseDev<T>& cd, int par, int x, i
   return phi;
 }
 
-// Initial state (Sec. 4 set-ups), computed in FP64 and rounded once:
-// hbar0 = 4 beta phi0 (phi0-1)(phi0-1/2) - kappa lap(phi0) (Eq. 2),
+// Initial state of one node (Sec. 4 set-ups), computed in FP64 and rounded
+// once: hbar0 = 4 beta phi0 (phi0-1)(phi0-1/2) - kappa lap(phi0) (Eq. 2),
 // g = g_eq(phi0, hbar0, u0) (Eq. 31), f = f_eq(p=0, rho(phi0), u0) (Eq. 22),
-// phi*u at t-1 = phi0 u0.
+// phi*u at t-1 = phi0 u0.  nb: phi0 at the eight neighbours E, W, N, S, NE,
+// NW, SE, SW (with walls, the ghost rows mirror the wall rows).
 template <typename T>
-__global__ void init_kernel(CaseDev<T> cd, double beta4, double kappa,
-                            double lambda, double rho_g, double drho,
-                            const double* __restrict__ phi0,
-                            const double* __restrict__ u0, int vortex,
-                            double vU, int parity) {
+__device__ __forceinline__ void init_node(const CaseDev<T>& cd, int x, int y, double p,
+                                          const double nb[8], double ux, double uy,
+                                          double beta4, double kappa, double lambda,
+                                          double rho_g, double drho, int parity) {
   const int nx = cd.nx, ny = cd.ny;
-  const int64_t n = (int64_t)nx * ny;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % nx), y = (int)(k / nx);
-    const int xm = x == 0 ? nx - 1 : x - 1, xp = x == nx - 1 ? 0 : x + 1;
-    // rows above and below; with walls the ghost row mirrors the wall row
-    const int ym = y == 0 ? (cd.walls ? 0 : ny - 1) : y - 1;
-    const int yp = y == ny - 1 ? (cd.walls ? ny - 1 : 0) : y + 1;
-    const double p = phi0[k];
-    const double pE = phi0[(int64_t)y * nx + xp], pW = phi0[(int64_t)y * nx + xm];
-    const double pN = phi0[(int64_t)yp * nx + x], pS = phi0[(int64_t)ym * nx + x];
-    const double pNE = phi0[(int64_t)yp * nx + xp], pNW = phi0[(int64_t)yp * nx + xm];
-    const double pSE = phi0[(int64_t)ym * nx + xp], pSW = phi0[(int64_t)ym * nx + xm];
-    const double lap = (2.0 / 3.0) * (((pE + pW) + (pN + pS)) - 4.0 * p) +
-                       (1.0 / 6.0) * (((pNE + pNW) + (pSE + pSW)) - 4.0 * p);
-    const double mu = beta4 * p * (p - 1.0) * (p - 0.5) - kappa * lap;
-    double ux = 0.0, uy = 0.0;
-    if (vortex) {
-      double sx, cx, sy, cy;
-      sincospi((x + 0.5) / nx, &sx, &cx);
-      sincospi((y + 0.5) / ny, &sy, &cy);
-      ux = -vU * sx * sx * (2.0 * sy * cy);
-      uy = vU * sy * sy * (2.0 * sx * cx);
-    } else if (u0) {
-      ux = u0[k];
-      uy = u0[n + k];
+  const int64_t k = (int64_t)y * nx + x;
+  const double lap = (2.0 / 3.0) * (((nb[0] + nb[1]) + (nb[2] + nb[3])) - 4.0 * p) +
+                     (1.0 / 6.0) * (((nb[4] + nb[5]) + (nb[6] + nb[7])) - 4.0 * p);
+  const double mu = beta4 * p * (p - 1.0) * (p - 0.5) - kappa * lap;
+  const double lam = mu + lambda * p;
+  const double Jx = p * ux, Jy = p * uy;
+  const double rho = rho_g + p * drho;
+  const double u2 = ux * ux + uy * uy;
+  T* gb = cd.g[parity];
+  T* fb = cd.f[parity];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const double w = (i == 0) ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    const double cu = kCX[i] * ux + kCY[i] * uy;
+    const double cJ = kCX[i] * Jx + kCY[i] * Jy;
+    const double gi = (i == 0) ? p + (w - 1.0) * lam : w * lam + 3.0 * w * cJ;
+    int pl;
+    const int64_t dst = pull_loc(i, x, y, nx, ny, cd.walls, &pl) + (int64_t)pl * cd.plane;
+    gb[dst] = (T)gi;
+    // FP32: the rest population is a float pair (high part + low part)
+    if (i == 0 && cd.g0lo[parity]) cd.g0lo[parity][k] = (T)(gi - (double)(T)gi);
+    // f arriving from a wall carries the moving-wall term on top of the
+    // stored value: store f_eq minus that term
+    if (fb)
+      fb[dst] = (T)(rho * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2) - wall_term(cd, i, y, rho));
+  }
+  cd.J[parity][k] = (T)Jx;
+  cd.J[parity][cd.plane + k] = (T)Jy;
+}
+
+// Initial state of every case of a batch in one launch: one CTA per work
+// item (case, strip of BX columns from x0, run of nrows rows from y0), as
+// the step kernel tiles the batch.  The rows of phi0 the item needs (its own
+// and one halo row above and below, each with one halo column on either
+// side) pass through a ring of four shared-memory rows, so every value of
+// phi0 is read once per item, coalesced along x.
+template <typename T, int BX>
+__global__ void __launch_bounds__(BX) init_items(const CaseDev<T>* __restrict__ cases,
+                                                 const Item* __restrict__ items,
+                                                 const InitSrc* __restrict__ src, double beta4,
+                                                 double kappa, double lambda, int vortex,
+                                                 double vU, int parity) {
+  __shared__ double ring[4][BX + 2];
+  const Item it = items[blockIdx.x];
+  const CaseDev<T> cd = cases[it.c];
+  const InitSrc sc = src[it.c];
+  const int nx = cd.nx, ny = cd.ny, tid = threadIdx.x;
+  const int wact = min(BX, nx - it.x0);
+  const bool act = tid < wact;
+  const int x = it.x0 + (act ? tid : 0);
+  // halo columns: x0 - 1 (thread 0) and x0 + wact (thread BX - 1), periodic
+  const int xl = it.x0 == 0 ? nx - 1 : it.x0 - 1;
+  const int xr = it.x0 + wact == nx ? 0 : it.x0 + wact;
+  auto row_of = [&](int r) -> int {  // with walls the ghost row mirrors the wall row
+    if (r < 0) return cd.walls ? 0 : ny - 1;
+    if (r >= ny) return cd.walls ? ny - 1 : 0;
+    return r;
+  };
+  auto load = [&](int r) {
+    const int64_t base = (int64_t)row_of(r) * nx;
+    double* dst = ring[r & 3];
+    if (act) dst[tid + 1] = sc.phi[base + x];
+    if (tid == 0) dst[0] = sc.phi[base + xl];
+    if (tid == BX - 1) dst[wact + 1] = sc.phi[base + xr];
+  };
+  load(it.y0 - 1);
+  load(it.y0);
+  for (int y = it.y0; y < it.y0 + it.nrows; ++y) {
+    load(y + 1);
+    __syncthreads();
+    if (act) {
+      const double* rS = ring[(y - 1) & 3];
+      const double* rC = ring[y & 3];
+      const double* rN = ring[(y + 1) & 3];
+      const int c = tid + 1;
+      const double nb[8] = {rC[c + 1], rC[c - 1], rN[c], rS[c],
+                            rN[c + 1], rN[c - 1], rS[c + 1], rS[c - 1]};
+      double ux = 0.0, uy = 0.0;
+      if (vortex) {
+        double sx, cx, sy, cy;
+        sincospi((x + 0.5) / nx, &sx, &cx);
+        sincospi((y + 0.5) / ny, &sy, &cy);
+        ux = -vU * sx * sx * (2.0 * sy * cy);
+        uy = vU * sy * sy * (2.0 * sx * cx);
+      } else if (sc.u) {
+        const int64_t k = (int64_t)y * nx + x;
+        ux = sc.u[k];
+        uy = sc.u[(int64_t)nx * ny + k];
+      }
+      init_node<T>(cd, x, y, rC[c], nb, ux, uy, beta4, kappa, lambda, sc.rho_g, sc.drho, parity);
     }
-    const double lam = mu + lambda * p;
-    const double Jx = p * ux, Jy = p * uy;
-    const double rho = rho_g + p * drho;
-    const double u2 = ux * ux + uy * uy;
-    const int par = parity;
-    T* gb = cd.g[par];
-    T* fb = cd.f[par];
-    for (int i = 0; i < 9; ++i) {
-      const double w = (i == 0) ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-      const double cu = kCX[i] * ux + kCY[i] * uy;
-      const double cJ = kCX[i] * Jx + kCY[i] * Jy;
-      const double gi = (i == 0) ? p + (w - 1.0) * lam : w * lam + 3.0 * w * cJ;
-      int pl;
-      const int64_t dst = (int64_t)0 + pull_loc(i, x, y, nx, ny, cd.walls, &pl) +
-                          (int64_t)pl * cd.plane;
-      gb[dst] = (T)gi;
-      // FP32: the rest population is a float pair (high part + low part)
-      if (i == 0 && cd.g0lo[par]) cd.g0lo[par][k] = (T)(gi - (double)(T)gi);
-      // f arriving from a wall carries the moving-wall term on top of the
-      // stored value: store f_eq minus that term
-      if (fb)
-        fb[dst] = (T)(rho * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2) - wall_term(cd, i, y, rho));
-    }
-    cd.J[par][k] = (T)Jx;
-    cd.J[par][cd.plane + k] = (T)Jy;
   }
 }
 

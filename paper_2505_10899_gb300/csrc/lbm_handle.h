@@ -14,7 +14,7 @@
 namespace lbmk {
 
 struct Layout {
-  size_t hdr = 0, cases = 0, items = 0, part = 0, vol = 0, staging = 0;
+  size_t hdr = 0, cases = 0, items = 0, part = 0, vol = 0, init = 0, staging = 0;
   std::vector<size_t> f, g, J, lab;  // per-case offsets (f: 2 buffers back to back)
   std::vector<size_t> glo;           // FP32: low part of g_0, 2 planes per case
   std::vector<int64_t> plane;
@@ -24,6 +24,18 @@ struct Layout {
 struct Tiling {
   int bx = 128;
   int rows = 32;
+};
+
+// Independent case groups ("chains") whose steps are captured as parallel
+// branches of one CUDA graph, so that the last CTAs of one group's step run
+// beside the next group's work instead of leaving SMs idle.
+constexpr int kMaxChains = 4;
+
+// A captured and instantiated sequence of `count` steps starting from source
+// buffer `parity`.
+struct StepGraph {
+  int count = 0, parity = 0;
+  cudaGraphExec_t exec = nullptr;
 };
 
 }  // namespace lbmk
@@ -48,11 +60,17 @@ struct lbm_handle {
   lbmk::Phys<double> pd{};
   std::vector<lbmk::CaseDev<float>> cf;
   std::vector<lbmk::CaseDev<double>> cd;
-  cudaGraphExec_t gexec = nullptr;
-  int graph_parity = -1;
+  int nchains = 1;
+  std::vector<int> chain_case;  // chain c: cases [chain_case[c], chain_case[c+1])
+  std::vector<int> chain_item;  //          items [chain_item[c], chain_item[c+1])
+  cudaStream_t aux[lbmk::kMaxChains - 1] = {};  // capture streams of chains 1..
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[lbmk::kMaxChains - 1] = {};
+  std::vector<lbmk::StepGraph> graphs;  // cache, oldest first
   double* track = nullptr;  // fused volume output (device), or null
   bool tma_ok = false;      // every case allows the bulk-copy kernel
   int kernel = 0;           // 0 auto, 1 register-pipelined, 2 bulk-copy staged
+  long long wait_cycles = lbmk::kWaitCycles;  // bound of the device waits
   // device pointers
   int32_t* flags = nullptr;
   int64_t* t_dev = nullptr;

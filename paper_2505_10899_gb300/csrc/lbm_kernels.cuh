@@ -303,7 +303,8 @@ struct GridBar {
   unsigned int* gen;
 };
 
-__device__ __forceinline__ bool grid_barrier(const GridBar& b, int32_t* flags) {
+__device__ __forceinline__ bool grid_barrier(const GridBar& b, int32_t* flags,
+                                             long long wait_cycles) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -318,7 +319,7 @@ __device__ __forceinline__ bool grid_barrier(const GridBar& b, int32_t* flags) {
     } else {
       const long long t0 = clock64();
       while (*(volatile unsigned int*)b.gen == g) {
-        if (clock64() - t0 > 4000000000LL) {  // ~2 s
+        if (clock64() - t0 > wait_cycles) {
           atomicOr(flags, kFlagTimeout);
           ok = 0;
           break;
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(BX) step_kernel_persistent(const StepArgs<T> a
     }
     for (int item = blockIdx.x; item < n_items; item += gridDim.x)
       step_item<T, BX, COUPLED, kModeStep, true>(as, item, ring, vred);
-    if (s + 1 < nsteps && !grid_barrier(bar, a.flags)) return;
+    if (s + 1 < nsteps && !grid_barrier(bar, a.flags, a.wait_cycles)) return;
   }
 }
 

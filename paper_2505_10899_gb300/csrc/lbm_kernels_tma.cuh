@@ -13,8 +13,10 @@
 // never wait on DRAM latency.  The halo columns of the phi/psi ring come from
 // the same staged segments, without extra global loads.
 //
-// Every mbarrier wait is bounded (kWaitCycles); on expiry the CTA raises
-// kFlagTimeout, waits (bounded) for its own copies in flight and returns.
+// Every wait of the consumers is bounded (StepArgs::wait_cycles); on expiry
+// the CTA raises kFlagTimeout, waits for its own copies still in flight
+// (bounded by kWaitCycles, whatever wait_cycles is, so that no CTA leaves
+// while a copy into its shared memory is pending) and returns.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -25,7 +27,6 @@
 
 namespace lbmk {
 
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // D2Q9 velocity components (Eq. 19) as compile-time functions of i.
 __host__ __device__ constexpr int cx_of(int i) {
@@ -175,10 +176,19 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
     const int last = min(S - 2, nrows);
     for (int k = -1; k <= last; ++k) issue(k);
   }
-  bool bad = !mbar_wait_bounded(&bars[slot_of(-1)], parity_of(-1), kWaitCycles);
-  if (!bad) put_row(-1);
-  bad = bad || !mbar_wait_bounded(&bars[slot_of(0)], parity_of(0), kWaitCycles);
-  if (!bad) put_row(0);
+  // rows up to `landed` have been seen complete by this thread
+  int landed = -2;
+  const long long lim = a.wait_cycles;
+  bool bad = !mbar_wait_bounded(&bars[slot_of(-1)], parity_of(-1), lim);
+  if (!bad) {
+    landed = -1;
+    put_row(-1);
+  }
+  bad = bad || !mbar_wait_bounded(&bars[slot_of(0)], parity_of(0), lim);
+  if (!bad) {
+    landed = 0;
+    put_row(0);
+  }
 
   int issued_last = min(S - 2, nrows);  // highest row issued so far
   // FP32: low part of g_0 of the own node, loaded one row ahead
@@ -191,13 +201,17 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
     T glo = lo_next;
     lo_next = lo_of(k + 1);
     // row k+1 (own row or the halo row below the item) into the ring
-    bad = bad || !mbar_wait_bounded(&bars[slot_of(k + 1)], parity_of(k + 1), kWaitCycles);
-    if (!bad) put_row(k + 1);
+    bad = bad || !mbar_wait_bounded(&bars[slot_of(k + 1)], parity_of(k + 1), lim);
+    if (!bad) {
+      landed = k + 1;
+      put_row(k + 1);
+    }
     if (__syncthreads_or(bad)) {
-      // a bulk copy never completed: report, drain what is in flight, leave
+      // a wait gave up: report, wait for every row issued but not yet seen
+      // complete (its copies write into this CTA's shared memory), leave
       if (tid == 0) atomicOr(a.flags, kFlagTimeout);
-      for (int m = k + 1; m <= issued_last; ++m)
-        mbar_wait_bounded(&bars[slot_of(m)], parity_of(m), kWaitCycles / 8);
+      for (int m = landed + 1; m <= issued_last; ++m)
+        mbar_wait_bounded(&bars[slot_of(m)], parity_of(m), kWaitCycles);
       return;
     }
     // the stage of row k-1 is free: refill it with row k-1+S

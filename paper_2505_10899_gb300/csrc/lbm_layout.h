@@ -49,6 +49,9 @@ struct CaseDev {
 // amplify any perturbation by 1/|grad(psi)|.
 constexpr double kNormalMin = 0.1;
 
+// Default bound of the device waits: ~2 s at 2 GHz.
+constexpr long long kWaitCycles = 4000000000LL;
+
 template <typename T>
 struct Phys {
   T beta4;   // 4 beta, beta = 12 sigma / W
@@ -67,6 +70,18 @@ struct Item {
   int32_t c, x0, y0, nrows;  // case, first column, first row, rows
 };
 
+// Initial fields of one case as the init kernel reads them: device
+// pointers to [ny][nx] FP64 phi0 and [2][ny][nx] u0 (u0 may be null: at
+// rest), either in the workspace (staged copies) or in host memory that the
+// device reads directly (page-locked memory, over the CPU-GPU link); and
+// rho(phi) = rho_g + phi drho in FP64.
+struct InitSrc {
+  const double* phi;
+  const double* u;
+  double rho_g, drho;
+};
+
+
 enum { kModeStep = 0, kModeFields = 1 };
 enum { kFlagNonFinite = 1, kFlagTimeout = 2 };
 
@@ -80,6 +95,10 @@ struct StepArgs {
   int32_t parity;         // source buffer index
   int32_t pad_;
   int32_t* flags;         // device error flags (kFlag*)
+  // bound of every wait on data or on other CTAs, in SM clock cycles (the
+  // TMA kernel's waits for its staged rows, the persistent kernel's grid
+  // barrier); on expiry the kernel raises kFlagTimeout and returns
+  long long wait_cycles;
   // kModeStep: if non-null, each CTA writes the FP64 sum of the phi it
   // collided (the pre-collision phi of Eq. 35) to vol_part[blockIdx.x * 8]
   double* vol_part;

@@ -10,7 +10,6 @@
 // 256 KiB), which every GPU that loads the library holds until the process
 // exits.
 #include <cstdint>
-#include <mutex>
 #include <string>
 
 #include <cuda_runtime.h>
@@ -27,15 +26,10 @@ namespace {
 constexpr int kNaMaxBlocks = 4096;  // partial-sum slots (CTAs per call)
 constexpr int kNaMaxRegions = 8;
 constexpr int kNaBX = 128;          // columns per CTA
-constexpr int kNaMaxDevices = 64;
 
 // Scratch shared by every call on a device; each call overwrites the slots it
 // uses before reading them, so nothing has to start at zero.
 static __device__ __align__(256) double g_na_partials[kNaMaxBlocks * kNaMaxRegions];
-
-// Device address of the scratch array, looked up once per device.
-std::mutex g_na_mutex;
-double* g_na_ptr[kNaMaxDevices] = {};
 
 int na_fail(int code, const std::string& msg) {
   return lbmk::set_last_error(code, ("lbm_phase_volume_noalloc: " + msg).c_str());
@@ -83,32 +77,30 @@ __global__ void __launch_bounds__(kNaBX)
   }
 }
 
-// Sum the partials of all CTAs in CTA order; lane r of the single warp
-// handles region r.
+// Sum the partials of all CTAs: warp r handles region r.  Lane l adds the
+// partials of CTAs l, l + 32, l + 64, ... in that order, then the 32 lane sums
+// are combined by a fixed shuffle tree, so the result is the same bits on
+// every call.
 __global__ void na_volume_final(const double* __restrict__ part, int nblocks, int nregions,
                                 double* __restrict__ out) {
-  const int r = threadIdx.x;
+  const int r = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (r >= nregions) return;
   double v = 0.0;
-  for (int b = 0; b < nblocks; ++b) v += part[(int64_t)b * kNaMaxRegions + r];
-  out[r] = v;
+  for (int b = lane; b < nblocks; b += 32) v += part[(int64_t)b * kNaMaxRegions + r];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) out[r] = v;
 }
 
-// Set-up on the current device: look up the scratch array's device address.
+// Device address of the scratch array on the current device.  It is looked
+// up on every call (a host-side query that allocates nothing): an address
+// cached across calls would go stale if the device were reset and the module
+// loaded again at another address.
 int na_scratch(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return na_fail(LBM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kNaMaxDevices) return na_fail(LBM_ERR_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_na_mutex);
-  if (!g_na_ptr[dev]) {
-    double* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_na_partials);
-    if (e != cudaSuccess || !p)
-      return na_fail(LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_na_ptr[dev] = p;
-  }
-  *out = g_na_ptr[dev];
+  double* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress((void**)&p, g_na_partials);
+  if (e != cudaSuccess || !p)
+    return na_fail(LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = p;
   return LBM_OK;
 }
 
@@ -147,7 +139,7 @@ extern "C" int lbm_phase_volume_noalloc(const void* d_g, int32_t precision, int3
                                                              ny, rows, d_labels, nregions, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(LBM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
-  na_volume_final<<<1, 32, 0, s>>>(part, (int)nblocks, nregions, d_out);
+  na_volume_final<<<1, 32 * nregions, 0, s>>>(part, (int)nblocks, nregions, d_out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return na_fail(LBM_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return LBM_OK;

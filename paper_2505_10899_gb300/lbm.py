@@ -63,6 +63,14 @@ def _load():
         "lbm_init": ([_P, ctypes.c_int32, _VP, ctypes.c_size_t, ctypes.POINTER(_D),
                       ctypes.POINTER(_D), _VP, ctypes.POINTER(_H)], ctypes.c_int),
         "lbm_step": ([_H, ctypes.c_int64], ctypes.c_int),
+        "lbm_prepare_steps": ([_H, ctypes.c_int64], ctypes.c_int),
+        "lbm_set_chains": ([_H, ctypes.c_int32], ctypes.c_int),
+        "lbm_get_chains": ([_H], ctypes.c_int32),
+        "lbm_set_wait_limit": ([_H, ctypes.c_int64], ctypes.c_int),
+        "lbm_fp64_fma_rate": ([ctypes.c_int64, ctypes.c_int32, _D, _D], ctypes.c_int),
+        "lbm_record_steps": ([_H, ctypes.c_int64, _VP, ctypes.c_int64], ctypes.c_int),
+        "lbm_adjoint_sweep": ([_H, _VP, ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, _VP,
+                               _VP], ctypes.c_int),
         "lbm_set_regions": ([_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int8), ctypes.c_int32],
                             ctypes.c_int),
         "lbm_volume": ([_H, _D], ctypes.c_int),
@@ -182,6 +190,42 @@ def lbm_init(params, d_workspace: int, ws_bytes: int, phi0s, u0s=None, stream: i
 
 def lbm_step(h, nsteps: int):
     return _check(_lib.lbm_step(h, int(nsteps)), "lbm_step")
+
+
+def lbm_prepare_steps(h, nsteps: int):
+    return _check(_lib.lbm_prepare_steps(h, int(nsteps)), "lbm_prepare_steps")
+
+
+def lbm_set_chains(h, nchains: int):
+    return _check(_lib.lbm_set_chains(h, int(nchains)), "lbm_set_chains")
+
+
+def lbm_get_chains(h) -> int:
+    return int(_lib.lbm_get_chains(h))
+
+
+def lbm_fp64_fma_rate(trips: int = 40000, blocks_per_sm: int = 4):
+    """FP64 FMAs per second of the current device and the timed milliseconds."""
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib.lbm_fp64_fma_rate(int(trips), int(blocks_per_sm), ctypes.byref(r),
+                                  ctypes.byref(ms)), "lbm_fp64_fma_rate")
+    return float(r.value), float(ms.value)
+
+
+def lbm_record_steps(h, count: int, d_states: int, stride_bytes: int):
+    return _check(_lib.lbm_record_steps(h, int(count), ctypes.c_void_p(d_states),
+                                        int(stride_bytes)), "lbm_record_steps")
+
+
+def lbm_adjoint_sweep(h, d_states: int, stride_bytes: int, t0: int, count: int, d_adj: int,
+                      d_spare: int):
+    return _check(_lib.lbm_adjoint_sweep(h, ctypes.c_void_p(d_states), int(stride_bytes),
+                                         int(t0), int(count), ctypes.c_void_p(d_adj),
+                                         ctypes.c_void_p(d_spare)), "lbm_adjoint_sweep")
+
+
+def lbm_set_wait_limit(h, cycles: int):
+    return _check(_lib.lbm_set_wait_limit(h, int(cycles)), "lbm_set_wait_limit")
 
 
 def lbm_set_regions(h, c: int, labels, nregions: int):
@@ -396,6 +440,15 @@ class Sim:
     def step(self, n):
         lbm_step(self.h, n)
         return self
+
+    def prepare(self, n):
+        lbm_prepare_steps(self.h, n)
+
+    def set_chains(self, n):
+        lbm_set_chains(self.h, n)
+
+    def chains(self):
+        return lbm_get_chains(self.h)
 
     def set_regions(self, c, labels, nregions):
         lbm_set_regions(self.h, c, labels, nregions)

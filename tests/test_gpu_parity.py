@@ -184,6 +184,64 @@ def test_batch_of_uneven_cases_fp64(L, specs):
         assert abs(v[k] / o.volume()[0] - 1) < 1e-13
 
 
+def _chain_batch():
+    cases, phis, us = [], [], []
+    for k, (nx, ny, ratio) in enumerate([(64, 64, 1.0), (96, 40, 4.0), (128, 52, 10.0),
+                                         (32, 48, 2.0), (160, 36, 1.0)]):
+        cases.append(W.base_case(nx, ny, rho_l=ratio, tau_f_l=0.8, tau_f_g=0.9))
+        phi = W.tanh_disc(nx, ny, nx / 2, ny / 2, min(nx, ny) / 4, 4.0, periodic=True)
+        phis.append(phi + W.uniform(20 + k, phi.shape, -1e-3, 1e-3))
+        u = np.zeros((2, ny, nx))
+        u[k % 2] = 0.01 * (k + 1) * (-1) ** k
+        us.append(u)
+    return cases, phis, us
+
+
+def test_chains_do_not_change_results(L):
+    # The chains split the cases into groups whose steps run as parallel
+    # branches of the step graph; the kernels and their per-node arithmetic
+    # are the same, so states and fused volumes are bitwise equal for any
+    # chain count and any chunking of the steps into graphs.
+    cases, phis, us = _chain_batch()
+    ref = None
+    for nch in (1, 2, 3, 4):
+        s = L.Sim(cases, phis, us, precision="f32")
+        s.set_tiling(32, 8)
+        s.set_chains(nch)
+        assert s.chains() == nch
+        vol = s.track_volume(True)
+        s.prepare(7)
+        for n in (1, 5, 64, 7):  # graphs of both parities, the 64-step graph and a remainder
+            s.step(n)
+        assert s.t == 77 and s.status() == L.LBM_OK
+        out = [s.get_state(k)[:3] for k in range(len(cases))] + [vol.cpu().numpy()]
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(ref[:-1], out[:-1]):
+                for x, y in zip(a, b):
+                    assert np.array_equal(x, y)
+            assert np.array_equal(ref[-1], out[-1])
+        s.close()
+    s = L.Sim(cases[:2], phis[:2], us[:2], precision="f32")
+    s.set_chains(4)
+    assert s.chains() == 2  # at most one chain per case
+    with pytest.raises(L.LbmError):
+        s.set_chains(5)
+
+
+def test_three_chains_match_oracle_fp64(L):
+    cases, phis, us = _chain_batch()
+    oracles = [oracle.Oracle(c, p, u).step(30) for c, p, u in zip(cases, phis, us)]
+    s = L.Sim(cases, phis, us, precision="f64")
+    s.set_chains(3)
+    s.step(30)
+    for k, o in enumerate(oracles):
+        f, g, j, t = s.get_state(k)
+        assert maxdiff(f, o.f) <= TOL64 and maxdiff(g, o.g) <= TOL64
+        assert maxdiff(j, o.j) <= TOL64
+
+
 def test_checkpoint_roundtrip_bitwise(L):
     case, phi0, u0, _, _ = W.two_droplets(noise=1e-3)
     for prec in ("f32", "f64"):

@@ -70,6 +70,38 @@ def test_noalloc_volume_matches_lbm_volume(L, prec):
     assert abs(v1.sum() / v2[0] - 1.0) < TOL_VOL  # regions partition the grid
 
 
+@pytest.mark.parametrize("prec,nx,ny,pad", [("f32", 200, 3000, 64), ("f64", 200, 3000, 64),
+                                           ("f32", 300, 20000, 0), ("f64", 131, 5, 3)])
+def test_noalloc_volume_ragged_strips_and_row_runs(L, prec, nx, ny, pad):
+    """Several 128-column strips with a ragged last one, more rows than CTA
+    slots (each CTA sums a run of rows), a padded plane stride, and labels
+    in {-1, 0, 1, 2}: every region against a host FP64 sum of the planes as
+    passed, on two calls in a row (labelled, then one region)."""
+    import torch
+    stride = nx * ny + pad
+    dtype = torch.float32 if prec == "f32" else torch.float64
+    g = W.uniform(4242 + nx, (9 * stride,), 0.0, 0.2)
+    g_dev = torch.from_numpy(g).to(device="cuda", dtype=dtype).contiguous()
+    lab = (W.splitmix64(77 + ny, nx * ny) % np.uint64(4)).astype(np.int8) - np.int8(1)
+    lab_dev = torch.from_numpy(lab).to("cuda")
+    out = torch.empty(8, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    gp = g_dev.double().cpu().numpy().reshape(9, stride)[:, :nx * ny].sum(axis=0)
+    exact = np.array([gp[lab == r].sum() for r in range(3)])
+    for _ in range(2):
+        out.fill_(float("nan"))
+        L.lbm_phase_volume_noalloc(g_dev.data_ptr(), prec, nx, ny, stride, lab_dev.data_ptr(),
+                                   3, out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        v = out[:3].cpu().numpy()
+        assert np.all(np.abs(v / exact - 1.0) < TOL_VOL), (v, exact)
+        out.fill_(float("nan"))
+        L.lbm_phase_volume_noalloc(g_dev.data_ptr(), prec, nx, ny, stride, 0, 1,
+                                   out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        assert abs(out[0].item() / gp.sum() - 1.0) < TOL_VOL
+
+
 def test_noalloc_volume_rejects_sizes_beyond_its_limit(L):
     import torch
     out = torch.empty(1, dtype=torch.float64, device="cuda")
