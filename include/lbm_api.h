@@ -61,7 +61,9 @@ enum {
   LBM_ERR_WORKSPACE = -3,     /* workspace missing, too small or misaligned */
   LBM_ERR_NONFINITE = -4,     /* a NaN/Inf appeared in the macroscopic fields */
   LBM_ERR_TIMEOUT = -5,       /* a bounded device wait gave up (lbm_set_wait_limit) */
-  LBM_ERR_UNIMPLEMENTED = -6  /* entry point declared but not built */
+  LBM_ERR_UNIMPLEMENTED = -6, /* entry point declared but not built */
+  LBM_ERR_BOUNDS = -7         /* the library built with index checks found an
+                                 index out of range (liblbm_gb300_checked.so) */
 };
 
 /* Storage and arithmetic precision.  Under LBM_F32 the rest population g_0

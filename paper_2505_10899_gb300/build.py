@@ -45,17 +45,24 @@ def _newest_input() -> float:
     return max(t, os.path.getmtime(__file__))
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link; returns the path of the shared library."""
-    if (not force and os.path.exists(SO_PATH)
-            and os.path.getmtime(SO_PATH) >= _newest_input()):
-        return SO_PATH
-    os.makedirs(OBJDIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False,
+          checked: bool = False) -> str:
+    """Compile and link; returns the path of the shared library.  checked:
+    the debug build with index checks in the step kernels (LBM_CHECK_BOUNDS),
+    liblbm_gb300_checked.so beside the normal library."""
+    so_path = SO_PATH.replace(".so", "_checked.so") if checked else SO_PATH
+    objdir = OBJDIR + ("_checked" if checked else "")
+    if (not force and os.path.exists(so_path)
+            and os.path.getmtime(so_path) >= _newest_input()):
+        return so_path
+    os.makedirs(objdir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if checked:
+        extra = extra + ["-DLBM_CHECK_BOUNDS"]
 
     def compile_one(src):
-        obj = os.path.join(OBJDIR, src.replace(".cu", ".o"))
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
         cmd = [cc, *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -67,15 +74,15 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     if verbose or ptxas_info:
         for _, err in results:
             sys.stderr.write(err)
-    tmp = SO_PATH + f".tmp{os.getpid()}"
+    tmp = so_path + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, SO_PATH)
-    return SO_PATH
+    os.replace(tmp, so_path)
+    return so_path
 
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose=True,
-                ptxas_info="--ptxas-info" in sys.argv))
+                ptxas_info="--ptxas-info" in sys.argv, checked="--checked" in sys.argv))

@@ -14,6 +14,7 @@
 #include "../../include/lbm_api.h"
 #include "launch.h"
 #include "lbm_handle.h"
+#include "lbm_check.h"
 #include "lbm_layout.h"
 #include "lbm_trace.h"
 
@@ -510,6 +511,8 @@ int read_flags(lbm_handle* h) {
   int32_t fl = 0;
   LBM_CUDA(cudaMemcpyAsync(&fl, h->flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (fl & lbmk::kFlagBounds)
+    return fail(LBM_ERR_BOUNDS, "index out of range (build with index checks)");
   if (fl & lbmk::kFlagTimeout) return fail(LBM_ERR_TIMEOUT, "a bounded device wait timed out");
   if (fl & lbmk::kFlagNonFinite) return fail(LBM_ERR_NONFINITE, "non-finite macroscopic field");
   return LBM_OK;
@@ -672,6 +675,7 @@ const char* lbm_status_string(int s) {
     case LBM_ERR_NONFINITE: return "non-finite value in the fields";
     case LBM_ERR_TIMEOUT: return "device wait timed out";
     case LBM_ERR_UNIMPLEMENTED: return "not implemented";
+    case LBM_ERR_BOUNDS: return "index out of range (build with index checks)";
     default: return "unknown status";
   }
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm_layout.h"
+#include "lbm_node.cuh"
 
 namespace lbmk {
 
@@ -60,42 +61,64 @@ __device__ __forceinline__ double phi_at(const CaseDev<T>& cd, int par, int x, i
   return phi;
 }
 
-// Initial state of one node (Sec. 4 set-ups), computed in FP64 and rounded
-// once: hbar0 = 4 beta phi0 (phi0-1)(phi0-1/2) - kappa lap(phi0) (Eq. 2),
-// g = g_eq(phi0, hbar0, u0) (Eq. 31), f = f_eq(p=0, rho(phi0), u0) (Eq. 22),
-// phi*u at t-1 = phi0 u0.  nb: phi0 at the eight neighbours E, W, N, S, NE,
-// NW, SE, SW (with walls, the ghost rows mirror the wall rows).
-template <typename T>
-__device__ __forceinline__ void init_node(const CaseDev<T>& cd, int x, int y, double p,
-                                          const double nb[8], double ux, double uy,
-                                          double beta4, double kappa, double lambda,
-                                          double rho_g, double drho, int parity) {
+// Initial state of one node (Sec. 4 set-ups): hbar0 = 4 beta phi0 (phi0-1)
+// (phi0-1/2) - kappa lap(phi0) (Eq. 2), g = g_eq(phi0, hbar0, u0) (Eq. 31),
+// f = f_eq(p=0, rho(phi0), u0) (Eq. 22), phi*u at t-1 = phi0 u0.  nb: phi0
+// at the eight neighbours E, W, N, S, NE, NW, SE, SW (with walls, the ghost
+// rows mirror the wall rows).
+// R is the arithmetic type: FP64 for FP64 state (computed in FP64, rounded
+// once); FP32 for FP32 state (the FP64 pipe of the GPU is narrow and an FP64
+// init of a large batch takes it ~165 FP64 instructions per node), except
+// the rest population, which takes the remainder phi0 - sum of the stored
+// movers in FP64 and is stored as the float pair of the FP32 step, so that
+// the stored populations sum to phi0 to FP64 rounding.
+template <typename T, typename R>
+__device__ __forceinline__ void init_node(const CaseDev<T>& cd, int x, int y, double p64,
+                                          const double nb64[8], R ux, R uy, R beta4, R kappa,
+                                          R lambda, R rho_g, R drho, int parity) {
   const int nx = cd.nx, ny = cd.ny;
   const int64_t k = (int64_t)y * nx + x;
-  const double lap = (2.0 / 3.0) * (((nb[0] + nb[1]) + (nb[2] + nb[3])) - 4.0 * p) +
-                     (1.0 / 6.0) * (((nb[4] + nb[5]) + (nb[6] + nb[7])) - 4.0 * p);
-  const double mu = beta4 * p * (p - 1.0) * (p - 0.5) - kappa * lap;
-  const double lam = mu + lambda * p;
-  const double Jx = p * ux, Jy = p * uy;
-  const double rho = rho_g + p * drho;
-  const double u2 = ux * ux + uy * uy;
+  const R p = (R)p64;
+  R nb[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) nb[j] = (R)nb64[j];
+  const R lap = R(2.0 / 3.0) * (((nb[0] + nb[1]) + (nb[2] + nb[3])) - R(4) * p) +
+                R(1.0 / 6.0) * (((nb[4] + nb[5]) + (nb[6] + nb[7])) - R(4) * p);
+  const R mu = beta4 * p * (p - R(1)) * (p - R(0.5)) - kappa * lap;
+  const R lam = mu + lambda * p;
+  const R Jx = p * ux, Jy = p * uy;
+  const R rho = rho_g + p * drho;
+  const R u2 = ux * ux + uy * uy;
   T* gb = cd.g[parity];
   T* fb = cd.f[parity];
+  double movers = 0.0;  // FP32: sum of the stored movers, in FP64
+  int64_t dst0 = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    const double w = (i == 0) ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
-    const double cu = kCX[i] * ux + kCY[i] * uy;
-    const double cJ = kCX[i] * Jx + kCY[i] * Jy;
-    const double gi = (i == 0) ? p + (w - 1.0) * lam : w * lam + 3.0 * w * cJ;
+    const R w = (i == 0) ? R(4.0 / 9.0) : (i < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+    const R cu = R(kCX[i]) * ux + R(kCY[i]) * uy;
+    const R cJ = R(kCX[i]) * Jx + R(kCY[i]) * Jy;
     int pl;
     const int64_t dst = pull_loc(i, x, y, nx, ny, cd.walls, &pl) + (int64_t)pl * cd.plane;
-    gb[dst] = (T)gi;
-    // FP32: the rest population is a float pair (high part + low part)
-    if (i == 0 && cd.g0lo[parity]) cd.g0lo[parity][k] = (T)(gi - (double)(T)gi);
+    if (i == 0) {
+      dst0 = dst;
+      if (sizeof(R) == 8) gb[dst] = (T)(p + (w - R(1)) * lam);
+    } else {
+      const T gi = (T)(w * lam + R(3) * w * cJ);
+      gb[dst] = gi;
+      movers += (double)gi;
+    }
     // f arriving from a wall carries the moving-wall term on top of the
     // stored value: store f_eq minus that term
     if (fb)
-      fb[dst] = (T)(rho * w * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2) - wall_term(cd, i, y, rho));
+      fb[dst] = (T)(rho * w * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2) -
+                    (R)wall_term(cd, i, y, (double)rho));
+  }
+  if (sizeof(R) == 4) {  // FP32: g_0 = phi0 - movers as a float pair (high + low part)
+    const double g0 = p64 - movers;
+    const T hi = (T)g0;
+    gb[dst0] = hi;
+    if (cd.g0lo[parity]) cd.g0lo[parity][k] = (T)(g0 - (double)hi);
   }
   cd.J[parity][k] = (T)Jx;
   cd.J[parity][cd.plane + k] = (T)Jy;
@@ -105,15 +128,18 @@ __device__ __forceinline__ void init_node(const CaseDev<T>& cd, int x, int y, do
 // item (case, strip of BX columns from x0, run of nrows rows from y0), as
 // the step kernel tiles the batch.  The rows of phi0 the item needs (its own
 // and one halo row above and below, each with one halo column on either
-// side) pass through a ring of four shared-memory rows, so every value of
-// phi0 is read once per item, coalesced along x.
+// side) pass through a ring of eight shared-memory rows, loaded two rows
+// ahead of the row being initialised, so every value of phi0 is read once
+// per item, coalesced along x; u0 of a node is read two rows ahead into
+// registers.  The fields may sit in host memory read over the CPU-GPU link,
+// whose latency the two rows in flight hide.
 template <typename T, int BX>
 __global__ void __launch_bounds__(BX) init_items(const CaseDev<T>* __restrict__ cases,
                                                  const Item* __restrict__ items,
                                                  const InitSrc* __restrict__ src, double beta4,
                                                  double kappa, double lambda, int vortex,
                                                  double vU, int parity) {
-  __shared__ double ring[4][BX + 2];
+  __shared__ double ring[8][BX + 2];
   const Item it = items[blockIdx.x];
   const CaseDev<T> cd = cases[it.c];
   const InitSrc sc = src[it.c];
@@ -121,6 +147,7 @@ __global__ void __launch_bounds__(BX) init_items(const CaseDev<T>* __restrict__ 
   const int wact = min(BX, nx - it.x0);
   const bool act = tid < wact;
   const int x = it.x0 + (act ? tid : 0);
+  const int yend = it.y0 + it.nrows;
   // halo columns: x0 - 1 (thread 0) and x0 + wact (thread BX - 1), periodic
   const int xl = it.x0 == 0 ? nx - 1 : it.x0 - 1;
   const int xr = it.x0 + wact == nx ? 0 : it.x0 + wact;
@@ -131,37 +158,53 @@ __global__ void __launch_bounds__(BX) init_items(const CaseDev<T>* __restrict__ 
   };
   auto load = [&](int r) {
     const int64_t base = (int64_t)row_of(r) * nx;
-    double* dst = ring[r & 3];
+    double* dst = ring[r & 7];
     if (act) dst[tid + 1] = sc.phi[base + x];
     if (tid == 0) dst[0] = sc.phi[base + xl];
     if (tid == BX - 1) dst[wact + 1] = sc.phi[base + xr];
   };
+  // u0 of the own node of row r (rows of this item only)
+  const bool has_u = !vortex && sc.u != nullptr;
+  auto load_u = [&](int r, double& ux, double& uy) {
+    if (has_u && act && r < yend) {
+      const int64_t k = (int64_t)r * nx + x;
+      ux = sc.u[k];
+      uy = sc.u[(int64_t)nx * ny + k];
+    }
+  };
+  double ux0 = 0.0, uy0 = 0.0, ux1 = 0.0, uy1 = 0.0;
   load(it.y0 - 1);
   load(it.y0);
-  for (int y = it.y0; y < it.y0 + it.nrows; ++y) {
-    load(y + 1);
-    __syncthreads();
+  load(it.y0 + 1);
+  load_u(it.y0, ux0, uy0);
+  load_u(it.y0 + 1, ux1, uy1);
+  for (int y = it.y0; y < yend; ++y) {
+    // two rows ahead: phi0 of row y + 2 (slot (y+2) & 7, last read for row
+    // y - 5, long done) and u0 of row y + 2
+    double ux2 = 0.0, uy2 = 0.0;
+    if (y + 2 <= yend) load(y + 2);
+    load_u(y + 2, ux2, uy2);
+    __syncthreads();  // rows up to y + 1 are in the ring
     if (act) {
-      const double* rS = ring[(y - 1) & 3];
-      const double* rC = ring[y & 3];
-      const double* rN = ring[(y + 1) & 3];
+      const double* rS = ring[(y - 1) & 7];
+      const double* rC = ring[y & 7];
+      const double* rN = ring[(y + 1) & 7];
       const int c = tid + 1;
       const double nb[8] = {rC[c + 1], rC[c - 1], rN[c], rS[c],
                             rN[c + 1], rN[c - 1], rS[c + 1], rS[c - 1]};
-      double ux = 0.0, uy = 0.0;
+      using R = T;  // arithmetic type of the init, see init_node
+      R ux = (R)ux0, uy = (R)uy0;
       if (vortex) {
-        double sx, cx, sy, cy;
-        sincospi((x + 0.5) / nx, &sx, &cx);
-        sincospi((y + 0.5) / ny, &sy, &cy);
-        ux = -vU * sx * sx * (2.0 * sy * cy);
-        uy = vU * sy * sy * (2.0 * sx * cx);
-      } else if (sc.u) {
-        const int64_t k = (int64_t)y * nx + x;
-        ux = sc.u[k];
-        uy = sc.u[(int64_t)nx * ny + k];
+        R sx, cx, sy, cy;
+        Num<R>::sincospi_((R(x) + R(0.5)) / R(nx), &sx, &cx);
+        Num<R>::sincospi_((R(y) + R(0.5)) / R(ny), &sy, &cy);
+        ux = -(R)vU * sx * sx * (R(2) * sy * cy);
+        uy = (R)vU * sy * sy * (R(2) * sx * cx);
       }
-      init_node<T>(cd, x, y, rC[c], nb, ux, uy, beta4, kappa, lambda, sc.rho_g, sc.drho, parity);
+      init_node<T, R>(cd, x, y, rC[c], nb, ux, uy, (R)beta4, (R)kappa, (R)lambda, (R)sc.rho_g,
+                      (R)sc.drho, parity);
     }
+    ux0 = ux1, uy0 = uy1, ux1 = ux2, uy1 = uy2;
   }
 }
 

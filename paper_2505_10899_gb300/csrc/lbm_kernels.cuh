@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "lbm_layout.h"
+#include "lbm_check.h"
 #include "lbm_node.cuh"
 
 namespace lbmk {
@@ -34,17 +35,15 @@ __device__ __forceinline__ T ld(const T* p) {
 template <bool COHERENT = false, typename T>
 __device__ __forceinline__ void pull9(const T* __restrict__ b, uint32_t P,
                                       uint32_t o0, uint32_t om, uint32_t op,
-                                      uint32_t x, uint32_t xm, uint32_t xp, T v[9]) {
+                                      uint32_t x, uint32_t xm, uint32_t xp, T v[9],
+                                      int32_t* flags = nullptr) {
   // 32-bit element offsets: a buffer of 9 planes holds < 2^31 elements
-  v[0] = ld<COHERENT>(b + (o0 + x));
-  v[1] = ld<COHERENT>(b + (P + o0 + xm));
-  v[2] = ld<COHERENT>(b + (2u * P + om + x));
-  v[3] = ld<COHERENT>(b + (3u * P + o0 + xp));
-  v[4] = ld<COHERENT>(b + (4u * P + op + x));
-  v[5] = ld<COHERENT>(b + (5u * P + om + xm));
-  v[6] = ld<COHERENT>(b + (6u * P + om + xp));
-  v[7] = ld<COHERENT>(b + (7u * P + op + xp));
-  v[8] = ld<COHERENT>(b + (8u * P + op + xm));
+  const uint32_t off[9] = {o0 + x,           P + o0 + xm,      2u * P + om + x,
+                           3u * P + o0 + xp, 4u * P + op + x,  5u * P + om + xm,
+                           6u * P + om + xp, 7u * P + op + xp, 8u * P + op + xm};
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    v[i] = LBM_BOUND(flags, off[i], 9ull * P) ? ld<COHERENT>(b + off[i]) : T(0);
 }
 
 // The same pull at a row next to a wall (bot: row 0, top: row ny-1):
@@ -54,16 +53,20 @@ __device__ __forceinline__ void pull9(const T* __restrict__ b, uint32_t P,
 template <bool COHERENT = false, typename T>
 __device__ __forceinline__ void pull9w(const T* __restrict__ b, uint32_t P, uint32_t o0,
                                        uint32_t om, uint32_t op, uint32_t x, uint32_t xm,
-                                       uint32_t xp, bool bot, bool top, T v[9]) {
-  v[0] = ld<COHERENT>(b + (o0 + x));
-  v[1] = ld<COHERENT>(b + (P + o0 + xm));
-  v[3] = ld<COHERENT>(b + (3u * P + o0 + xp));
-  v[2] = ld<COHERENT>(b + (bot ? 4u * P + o0 + x : 2u * P + om + x));
-  v[5] = ld<COHERENT>(b + (bot ? 7u * P + o0 + x : 5u * P + om + xm));
-  v[6] = ld<COHERENT>(b + (bot ? 8u * P + o0 + x : 6u * P + om + xp));
-  v[4] = ld<COHERENT>(b + (top ? 2u * P + o0 + x : 4u * P + op + x));
-  v[7] = ld<COHERENT>(b + (top ? 5u * P + o0 + x : 7u * P + op + xp));
-  v[8] = ld<COHERENT>(b + (top ? 6u * P + o0 + x : 8u * P + op + xm));
+                                       uint32_t xp, bool bot, bool top, T v[9],
+                                       int32_t* flags = nullptr) {
+  const uint32_t off[9] = {o0 + x,
+                           P + o0 + xm,
+                           bot ? 4u * P + o0 + x : 2u * P + om + x,
+                           3u * P + o0 + xp,
+                           top ? 2u * P + o0 + x : 4u * P + op + x,
+                           bot ? 7u * P + o0 + x : 5u * P + om + xm,
+                           bot ? 8u * P + o0 + x : 6u * P + om + xp,
+                           top ? 5u * P + o0 + x : 7u * P + op + xp,
+                           top ? 6u * P + o0 + x : 8u * P + op + xm};
+#pragma unroll
+  for (int i = 0; i < 9; ++i)
+    v[i] = LBM_BOUND(flags, off[i], 9ull * P) ? ld<COHERENT>(b + off[i]) : T(0);
 }
 
 // Moving-wall term of the bounced f (walls along x at u_bot below row 0 and
@@ -148,6 +151,7 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
   const CaseK<T> K = case_consts<T, COUPLED>(a, cdp, xc);
 
   auto rowoff = [&](int r) -> uint32_t { return (uint32_t)r * (uint32_t)nx; };
+  const uint32_t nn = (uint32_t)nx * (uint32_t)ny;  // nodes of the case (checked build)
   // row index for r in [-1, ny]: periodic, or with walls the mirrored ghost
   // row (rows -1 and ny only feed phi and psi to the stencils)
   const bool walls = cdp->walls != 0;
@@ -171,16 +175,17 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
     const bool bt = at_bot(rr), tp = at_top(rr);
     if (bt || tp) {  // a wall row (uniform over the CTA)
-      pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, bt, tp, R.G);
-      if (COUPLED) pull9w<COHERENT>(fs, P, o0, om, op, xc, xm, xp, bt, tp, R.F);
+      pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, bt, tp, R.G, a.flags);
+      if (COUPLED) pull9w<COHERENT>(fs, P, o0, om, op, xc, xm, xp, bt, tp, R.F, a.flags);
     } else {
-      pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G);
-      if (COUPLED) pull9<COHERENT>(fs, P, o0, om, op, xc, xm, xp, R.F);
+      pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G, a.flags);
+      if (COUPLED) pull9<COHERENT>(fs, P, o0, om, op, xc, xm, xp, R.F, a.flags);
     }
-    R.lo = LO ? ld<COHERENT>(los + (o0 + xc)) : T(0);
+    const bool own_ok = LBM_BOUND(a.flags, o0 + xc, nn);
+    R.lo = (LO && own_ok) ? ld<COHERENT>(los + (o0 + xc)) : T(0);
     if (MODE == kModeStep) {  // phi*u of the previous step at the own node
-      R.J[0] = ld<COHERENT>(Js + (o0 + xc));
-      R.J[1] = ld<COHERENT>(Js + (P + o0 + xc));
+      R.J[0] = own_ok ? ld<COHERENT>(Js + (o0 + xc)) : T(0);
+      R.J[1] = own_ok ? ld<COHERENT>(Js + (P + o0 + xc)) : T(0);
     }
   };
   auto fetch_g = [&](int r, Regs& R) {
@@ -188,18 +193,18 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
     if (at_bot(rr) || at_top(rr))
-      pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, at_bot(rr), at_top(rr), R.G);
+      pull9w<COHERENT>(gs, P, o0, om, op, xc, xm, xp, at_bot(rr), at_top(rr), R.G, a.flags);
     else
-      pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G);
+      pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G, a.flags);
   };
   auto fetch_halo = [&](int r, T H[9]) {
     const int rr = wrap(r);
     const uint32_t o0 = rowoff(rr), om = rowoff(rr == 0 ? ny - 1 : rr - 1),
                    op = rowoff(rr == ny - 1 ? 0 : rr + 1);
     if (at_bot(rr) || at_top(rr))
-      pull9w<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, at_bot(rr), at_top(rr), H);
+      pull9w<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, at_bot(rr), at_top(rr), H, a.flags);
     else
-      pull9<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, H);
+      pull9<COHERENT>(gs, P, o0, om, op, hc, hcm, hcp, H, a.flags);
   };
   // write phi/psi of local row k (k >= -1) into the ring.  phi is the plain
   // sum of the nine pulled values (FP32: the low part of g_0 enters only the
@@ -258,9 +263,9 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
           node_update<T, COUPLED, MODE>(a.ph, K, C.F, C.G, C.lo, C.J[0], C.J[1], S, y);
       const uint32_t node = rowoff(y) + (uint32_t)xc;
       if (MODE == kModeStep) {
-        store_node<T, COUPLED>(fd, gd, Jd, lod, P, node, C.F, C.G, C.lo, o);
+        store_node<T, COUPLED>(fd, gd, Jd, lod, P, node, C.F, C.G, C.lo, o, a.flags, nn);
         if (!isfinite(S.p + o.ux + o.uy + o.p)) atomicOr(a.flags, kFlagNonFinite);
-      } else {
+      } else if (LBM_BOUND(a.flags, node, nn)) {
         a.out_phi[node] = (double)S.p;
         a.out_ux[node] = (double)o.ux;
         a.out_uy[node] = (double)o.uy;

@@ -114,20 +114,44 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
     const int nj = full ? NJ : 0;
     T* st = stage_of(k);
     uint64_t* bar = &bars[slot_of(k)];
-    const uint32_t seg_bytes = (uint32_t)(wact + 8) * sizeof(T);
-    if (lane == 0)
-      mbar_arrive_expect_tx(bar, np * seg_bytes + nj * (uint32_t)wact * sizeof(T));
+    // Staged column j holds global column (x0 - 4 + j) mod nx, j < wact + 8.
+    // Where the strip touches the periodic edge of the row, the four columns
+    // beyond it come from the other end of the row in a separate 16-byte
+    // copy, made only for the planes that read them: on the left (x0 = 0)
+    // the g planes with c_x >= 0 (the halo column -1 pulls from -1 - c_x)
+    // and the f planes with c_x = +1 (column 0 pulls from -1); on the right
+    // the mirror image.  That is 6 g and 3 f planes a side instead of 18.
+    // Lane l copies plane l (g planes 0-8, then f planes 9-17); bit l of
+    // kNeedL / kNeedR says whether it needs the left / right wrap columns.
+    constexpr uint32_t kNeedL = 0x137u | (0x122u << 9);  // g: c_x >= 0; f: c_x = +1
+    constexpr uint32_t kNeedR = 0x0DDu | (0x0C8u << 9);  // g: c_x <= 0; f: c_x = -1
+    const bool lw = (x0 == 0), rw = (x0 + wact >= nx);
+    uint32_t elems = (uint32_t)(np * (wact + 8) + nj * wact);
+    if (lw || rw) {  // the wrap columns that no plane reads are not copied
+      const int nwrap = (full && COUPLED) ? 9 : 6;  // 6 g planes, + 3 f planes on full rows
+      elems -= (uint32_t)((lw ? 4 * (np - nwrap) : 0) + (rw ? 4 * (np - nwrap) : 0));
+    }
+    if (lane == 0) mbar_arrive_expect_tx(bar, elems * (uint32_t)sizeof(T));
     __syncwarp();
     const int r = wrap(y0 + k);
+    const uint32_t nn = (uint32_t)nx * (uint32_t)ny;
+    // one bulk copy of n elements from position `first` of a plane (checked
+    // build: the source range must lie in the plane's nodes and the target
+    // in this stage; otherwise the copy is redirected, see lbm_check.h)
+    auto copy = [&](T* dst, const T* plane, const T* buf, int64_t first, uint32_t n) {
+      const bool ok = LBM_BOUND(a.flags, first, nn) && LBM_BOUND(a.flags, first + n - 1, nn) &&
+                      LBM_BOUND(a.flags, (dst - st) + n - 1, STAGE);
+      bulk_g2s(ok ? dst : st, ok ? plane + first : buf, n * sizeof(T), bar);
+    };
     if (lane < np) {
       const int i = lane < 9 ? lane : lane - 9;
-      const T* plane = (lane < 9 ? gs : fs) + (size_t)i * P;
-      const T* row = plane + (size_t)wrap(r - cy_of(i)) * nx;  // pull: source row r - c_iy
+      const T* buf = lane < 9 ? gs : fs;
+      const T* plane = buf + (size_t)i * P;
+      const int64_t row = (int64_t)wrap(r - cy_of(i)) * nx;  // pull: source row r - c_iy
       T* dst = st + lane * SEG;
-      // staged column j holds global column (x0 - 4 + j) mod nx, j < wact + 8
       int j = 0, g0, len;
-      if (x0 == 0) {
-        bulk_g2s(dst, row + (nx - 4), 4 * sizeof(T), bar);
+      if (lw) {
+        if ((kNeedL >> lane) & 1u) copy(dst, plane, buf, row + (nx - 4), 4);
         j = 4;
         g0 = 0;
         len = wact;
@@ -135,16 +159,15 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
         g0 = x0 - 4;
         len = wact + 4;
       }
-      if (x0 + wact < nx) {
-        bulk_g2s(dst + j, row + g0, (uint32_t)(len + 4) * sizeof(T), bar);
+      if (!rw) {
+        copy(dst + j, plane, buf, row + g0, (uint32_t)(len + 4));
       } else {
-        bulk_g2s(dst + j, row + g0, (uint32_t)len * sizeof(T), bar);
-        bulk_g2s(dst + j + len, row, 4 * sizeof(T), bar);
+        copy(dst + j, plane, buf, row + g0, (uint32_t)len);
+        if ((kNeedR >> lane) & 1u) copy(dst + j + len, plane, buf, row, 4);
       }
     } else if (lane >= NPL && lane < NPL + nj) {
       const int q = lane - NPL;
-      bulk_g2s(st + NPL * SEG + q * BX, Js + (size_t)q * P + (size_t)r * nx + x0,
-               (uint32_t)wact * sizeof(T), bar);
+      copy(st + NPL * SEG + q * BX, Js + (size_t)q * P, Js, (int64_t)r * nx + x0, (uint32_t)wact);
     }
   };
 
@@ -194,7 +217,8 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
   // FP32: low part of g_0 of the own node, loaded one row ahead
   auto lo_of = [&](int k) -> T {
     if (sizeof(T) != 4 || !act || k >= nrows) return T(0);
-    return __ldg(los + ((uint32_t)wrap(y0 + k) * (uint32_t)nx + (uint32_t)xc));
+    const uint32_t at = (uint32_t)wrap(y0 + k) * (uint32_t)nx + (uint32_t)xc;
+    return LBM_BOUND(a.flags, at, (uint32_t)nx * (uint32_t)ny) ? __ldg(los + at) : T(0);
   };
   T lo_next = lo_of(0);
   for (int k = 0; k < nrows; ++k) {
@@ -244,9 +268,10 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
       if (do_vol) vacc += (double)Sn.p;
       const NodeOut<T> o = node_update<T, COUPLED, MODE>(a.ph, K, F, G, glo, jpx, jpy, Sn, y);
       if (MODE == kModeStep) {
-        store_node<T, COUPLED>(fd, gd, Jd, lod, P, node, F, G, glo, o);
+        store_node<T, COUPLED>(fd, gd, Jd, lod, P, node, F, G, glo, o, a.flags,
+                               (uint32_t)nx * (uint32_t)ny);
         if (!isfinite(Sn.p + o.ux + o.uy + o.p)) atomicOr(a.flags, kFlagNonFinite);
-      } else {
+      } else if (LBM_BOUND(a.flags, node, (uint32_t)nx * (uint32_t)ny)) {
         a.out_phi[node] = (double)Sn.p;
         a.out_ux[node] = (double)o.ux;
         a.out_uy[node] = (double)o.uy;

@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "lbm_check.h"
 #include "lbm_layout.h"
 
 namespace lbmk {
@@ -352,7 +353,9 @@ template <typename T, bool COUPLED>
 __device__ __forceinline__ void store_node(T* __restrict__ fd, T* __restrict__ gd,
                                            T* __restrict__ Jd, T* __restrict__ lod, uint32_t P,
                                            uint32_t node, const T (&Fc)[9], const T (&Gc)[9],
-                                           T Glo, const NodeOut<T>& o) {
+                                           T Glo, const NodeOut<T>& o, int32_t* flags,
+                                           uint32_t nn) {
+  if (!LBM_BOUND(flags, node, nn)) return;  // checked build only
   if (sizeof(T) == 4) lod[node] = Glo;
   Jd[node] = o.Jx;
   Jd[P + node] = o.Jy;

@@ -14,11 +14,15 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "liblbm_gb300.so")
+# LBM_GB300_CHECKED=1 selects the debug build with index checks in the step
+# kernels (build.build(checked=True)), which reports LBM_ERR_BOUNDS
+LIB_PATH = os.path.join(_HERE, "_lib", "liblbm_gb300_checked.so"
+                        if os.environ.get("LBM_GB300_CHECKED") == "1" else "liblbm_gb300.so")
 
 LBM_ABI_VERSION = 2
 LBM_OK, LBM_ERR_ARG, LBM_ERR_CUDA, LBM_ERR_WORKSPACE = 0, -1, -2, -3
 LBM_ERR_NONFINITE, LBM_ERR_TIMEOUT, LBM_ERR_UNIMPLEMENTED = -4, -5, -6
+LBM_ERR_BOUNDS = -7
 LBM_F64, LBM_F32 = 0, 1
 LBM_FLOW_COUPLED, LBM_FLOW_VORTEX = 0, 1
 
