@@ -169,7 +169,11 @@ __global__ void ad_phase(const R* __restrict__ gA, int64_t P, int nx, int ny, in
   }
 }
 
-// Deterministic CTA reduction of the parameter partials (FP64).
+// Deterministic CTA reduction of the parameter partials (FP64), added to the
+// CTA's own slots: a CTA covers the same nodes in every launch (grid-stride
+// order over a fixed grid), so the slots accumulate over the adjoint steps in
+// a fixed order without atomics, and one final sum over the CTAs (at
+// take_grads) gives the same bits on every run.
 __device__ __forceinline__ void ad_block_partials(double (&red)[kAdThreads / 32][kNParam],
                                                   const double (&gacc)[kNParam],
                                                   double* __restrict__ part) {
@@ -183,7 +187,7 @@ __device__ __forceinline__ void ad_block_partials(double (&red)[kAdThreads / 32]
   if (threadIdx.x < kNParam) {
     double v = 0.0;
     for (int w = 0; w < kAdThreads / 32; ++w) v += red[w][threadIdx.x];
-    part[(int64_t)blockIdx.x * kNParam + threadIdx.x] = v;
+    part[(int64_t)blockIdx.x * kNParam + threadIdx.x] += v;
   }
 }
 
@@ -191,7 +195,7 @@ __device__ __forceinline__ void ad_block_partials(double (&red)[kAdThreads / 32]
 // states and adjoints (the handle's precision); the parameter partials are
 // accumulated in FP64.
 template <typename R>
-__global__ void __launch_bounds__(kAdThreads) ad_node(const AdArgs<R> a) {
+__global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(const AdArgs<R> a) {
   __shared__ double red[kAdThreads / 32][kNParam];
   using N = lbmk::Num<R>;
   const int nx = a.nx, ny = a.ny;
@@ -659,16 +663,19 @@ __global__ void ad_seed_phi(const double* __restrict__ dphi, int nx, int ny, int
   }
 }
 
-// Adds this sweep's parameter partials (in block order) to the device
-// accumulator `acc`, which lbm_adjoint_take_param_grads reads and clears.
-// Deterministic sum of the per-block partials (launch: one block of
-// 32 * kNParam threads): warp q sums parameter q, lane l the blocks
-// l, l + 32, ... in order, then a fixed shuffle tree.
-__global__ void ad_sum_partials(const double* __restrict__ part, int nb, double* __restrict__ acc) {
+// Adds the accumulated per-block parameter partials (in block order) to the
+// device accumulator `acc`, which lbm_adjoint_take_param_grads reads and
+// clears, and clears the partials.  Deterministic sum (launch: one block of
+// 32 * kNParam threads): warp q sums parameter q, lane l the blocks l, l + 32,
+// ... in order, then a fixed shuffle tree.
+__global__ void ad_sum_partials(double* __restrict__ part, int nb, double* __restrict__ acc) {
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (q >= kNParam) return;
   double v = 0.0;
-  for (int b = lane; b < nb; b += 32) v += part[(int64_t)b * kNParam + q];
+  for (int b = lane; b < nb; b += 32) {
+    v += part[(int64_t)b * kNParam + q];
+    part[(int64_t)b * kNParam + q] = 0.0;
+  }
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   if (lane == 0) acc[q] += v;
 }
@@ -730,7 +737,10 @@ void to_param_grads(const lbm_params& p, const double raw[kNParam], double* out)
 int take_grads(lbm_handle* h, double* out) {
   AdScratch s = carve(h);
   double raw[kNParam];
-  cudaError_t e = cudaMemcpyAsync(raw, s.sums, sizeof raw, cudaMemcpyDeviceToHost, h->stream);
+  ad_sum_partials<<<1, 32 * kNParam, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(raw, s.sums, sizeof raw, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(s.sums, 0, sizeof raw, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
@@ -765,7 +775,8 @@ int lbm_adjoint_attach(lbm_handle* h, void* d_scratch, size_t bytes) {
   if (bytes < lbm_adjoint_workspace_bytes(h)) return fail(LBM_ERR_WORKSPACE, "adjoint scratch too small");
   h->adj_ws = (char*)d_scratch;
   h->adj_ws_bytes = bytes;
-  cudaError_t e = cudaMemsetAsync(carve(h).sums, 0, kNParam * sizeof(double), h->stream);
+  cudaError_t e = cudaMemsetAsync(carve(h).part, 0, (kAdBlocks + 1) * kNParam * sizeof(double),
+                                  h->stream);  // partials and accumulator
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   return LBM_OK;
 }
@@ -848,7 +859,6 @@ int adjoint_step_impl(lbm_handle* h, const R* fA, const R* gA, const R* JA, int6
   ad_gather<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>((const R*)s.phi, (const R*)s.lP,
                                                         (const R*)s.lQ, p.nx, p.ny, p.walls,
                                                         (R)p.xi, (R*)d_adj_out);
-  ad_sum_partials<<<1, 32 * kNParam, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   if (h_param_grads) return take_grads(h, h_param_grads);
@@ -882,7 +892,6 @@ int adjoint_init_impl(lbm_handle* h, const double* d_phi0, const double* d_u0,
   ad_init_local<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
   ad_init_gather<<<kAdBlocks, kAdThreads, 0, h->stream>>>(s.init_lphi, s.init_llap, p.nx, p.ny,
                                                           p.walls, d_adj_phi0);
-  ad_sum_partials<<<1, 32 * kNParam, 0, h->stream>>>(s.part, kAdBlocks, s.sums);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   if (h_param_grads) return take_grads(h, h_param_grads);

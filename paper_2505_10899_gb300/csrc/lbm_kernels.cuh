@@ -38,12 +38,25 @@ __device__ __forceinline__ void pull9(const T* __restrict__ b, uint32_t P,
                                       uint32_t x, uint32_t xm, uint32_t xp, T v[9],
                                       int32_t* flags = nullptr) {
   // 32-bit element offsets: a buffer of 9 planes holds < 2^31 elements
+#ifdef LBM_CHECK_BOUNDS
   const uint32_t off[9] = {o0 + x,           P + o0 + xm,      2u * P + om + x,
                            3u * P + o0 + xp, 4u * P + op + x,  5u * P + om + xm,
                            6u * P + om + xp, 7u * P + op + xp, 8u * P + op + xm};
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     v[i] = LBM_BOUND(flags, off[i], 9ull * P) ? ld<COHERENT>(b + off[i]) : T(0);
+#else
+  (void)flags;
+  v[0] = ld<COHERENT>(b + (o0 + x));
+  v[1] = ld<COHERENT>(b + (P + o0 + xm));
+  v[2] = ld<COHERENT>(b + (2u * P + om + x));
+  v[3] = ld<COHERENT>(b + (3u * P + o0 + xp));
+  v[4] = ld<COHERENT>(b + (4u * P + op + x));
+  v[5] = ld<COHERENT>(b + (5u * P + om + xm));
+  v[6] = ld<COHERENT>(b + (6u * P + om + xp));
+  v[7] = ld<COHERENT>(b + (7u * P + op + xp));
+  v[8] = ld<COHERENT>(b + (8u * P + op + xm));
+#endif
 }
 
 // The same pull at a row next to a wall (bot: row 0, top: row ny-1):
@@ -55,6 +68,7 @@ __device__ __forceinline__ void pull9w(const T* __restrict__ b, uint32_t P, uint
                                        uint32_t om, uint32_t op, uint32_t x, uint32_t xm,
                                        uint32_t xp, bool bot, bool top, T v[9],
                                        int32_t* flags = nullptr) {
+#ifdef LBM_CHECK_BOUNDS
   const uint32_t off[9] = {o0 + x,
                            P + o0 + xm,
                            bot ? 4u * P + o0 + x : 2u * P + om + x,
@@ -67,6 +81,18 @@ __device__ __forceinline__ void pull9w(const T* __restrict__ b, uint32_t P, uint
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     v[i] = LBM_BOUND(flags, off[i], 9ull * P) ? ld<COHERENT>(b + off[i]) : T(0);
+#else
+  (void)flags;
+  v[0] = ld<COHERENT>(b + (o0 + x));
+  v[1] = ld<COHERENT>(b + (P + o0 + xm));
+  v[3] = ld<COHERENT>(b + (3u * P + o0 + xp));
+  v[2] = ld<COHERENT>(b + (bot ? 4u * P + o0 + x : 2u * P + om + x));
+  v[5] = ld<COHERENT>(b + (bot ? 7u * P + o0 + x : 5u * P + om + xm));
+  v[6] = ld<COHERENT>(b + (bot ? 8u * P + o0 + x : 6u * P + om + xp));
+  v[4] = ld<COHERENT>(b + (top ? 2u * P + o0 + x : 4u * P + op + x));
+  v[7] = ld<COHERENT>(b + (top ? 5u * P + o0 + x : 7u * P + op + xp));
+  v[8] = ld<COHERENT>(b + (top ? 6u * P + o0 + x : 8u * P + op + xm));
+#endif
 }
 
 // Moving-wall term of the bounced f (walls along x at u_bot below row 0 and
@@ -181,7 +207,11 @@ __device__ __forceinline__ void step_item(const StepArgs<T>& a, int item, Ring<T
       pull9<COHERENT>(gs, P, o0, om, op, xc, xm, xp, R.G, a.flags);
       if (COUPLED) pull9<COHERENT>(fs, P, o0, om, op, xc, xm, xp, R.F, a.flags);
     }
+#ifdef LBM_CHECK_BOUNDS
     const bool own_ok = LBM_BOUND(a.flags, o0 + xc, nn);
+#else
+    constexpr bool own_ok = true;
+#endif
     R.lo = (LO && own_ok) ? ld<COHERENT>(los + (o0 + xc)) : T(0);
     if (MODE == kModeStep) {  // phi*u of the previous step at the own node
       R.J[0] = own_ok ? ld<COHERENT>(Js + (o0 + xc)) : T(0);

@@ -355,7 +355,12 @@ __device__ __forceinline__ void store_node(T* __restrict__ fd, T* __restrict__ g
                                            uint32_t node, const T (&Fc)[9], const T (&Gc)[9],
                                            T Glo, const NodeOut<T>& o, int32_t* flags,
                                            uint32_t nn) {
-  if (!LBM_BOUND(flags, node, nn)) return;  // checked build only
+#ifdef LBM_CHECK_BOUNDS
+  if (!LBM_BOUND(flags, node, nn)) return;
+#else
+  (void)flags;
+  (void)nn;
+#endif
   if (sizeof(T) == 4) lod[node] = Glo;
   Jd[node] = o.Jx;
   Jd[P + node] = o.Jy;
