@@ -932,9 +932,13 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
         phi0_t = torch.tensor(phi0, dtype=torch.float64, requires_grad=True)
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        # device memory for recorded states (the rest is recomputed): 128 GiB,
-        # at most half of what is free
-        store = min(128 << 30, torch.cuda.mem_get_info(dev)[0] // 2)
+        # device memory for recorded states (the rest is recomputed): every
+        # state if they fit, leaving 24 GiB free for the rest of the run; the
+        # FP32 states of 2x10^4 steps (220 GB) fit in the GPU's 288 GB, the
+        # FP64 ones (420 GB) do not
+        state_bytes = (20 if prec == "f64" else 21) * (8 if prec == "f64" else 4) * 512 * 256
+        free = torch.cuda.mem_get_info(dev)[0]
+        store = max(0, min(grad_steps * state_bytes, free - (24 << 30)))
         phiT = A.coupled_run(phi0_t, th, case, grad_steps, ckpt, u0=u0, store_bytes=store,
                              precision=prec)
         D = A.taylor_deformation(phiT)
@@ -944,7 +948,6 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
         torch.cuda.synchronize(dev)
         t2 = time.perf_counter()
         g = th.grad.numpy()
-        state_bytes = (20 if prec == "f64" else 21) * (8 if prec == "f64" else 4) * 512 * 256
         plain_s = grad_steps * 512 * 256 / (out[prec]["mlups"] * 1e6)
         res = {"steps": grad_steps, "checkpoint_every": ckpt,
                "recorded_steps": min(grad_steps, store // state_bytes),

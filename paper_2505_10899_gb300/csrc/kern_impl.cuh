@@ -1,5 +1,6 @@
 // Explicit instantiation of the launch wrappers for precision LBM_T.
 // Included by kern_f32.cu (LBM_T = float) and kern_f64.cu (LBM_T = double).
+#include <algorithm>
 #include <type_traits>
 
 #include "launch.h"
@@ -163,6 +164,16 @@ cudaError_t launch_init_items<LBM_T>(const CaseDev<LBM_T>* cases, const Item* it
       init_items<LBM_T, 128><<<n_items, 128, 0, s>>>(cases, items, src, beta4, kappa, lambda,
                                                       vortex, vU, parity);
   }
+  return cudaGetLastError();
+}
+
+template <>
+cudaError_t launch_snapshot<LBM_T>(const LBM_T* f, const LBM_T* g, const LBM_T* J,
+                                   const LBM_T* lo, int64_t P, int64_t n, LBM_T* out,
+                                   cudaStream_t s) {
+  const int planes = lo ? 21 : 20;
+  const dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 4096), planes);
+  snapshot_kernel<LBM_T><<<grid, 256, 0, s>>>(f, g, J, lo, P, n, out);
   return cudaGetLastError();
 }
 

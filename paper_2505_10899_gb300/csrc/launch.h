@@ -52,6 +52,10 @@ cudaError_t launch_plane_export(double* dst, const T* buf, int64_t P, int i, int
 template <typename T>
 cudaError_t launch_wall_f_fix(double* v, const CaseDev<T>& cd, int par, int i, double sign,
                               cudaStream_t s);
+// One case's snapshot (lbm_snapshot layout) in one launch; lo may be null.
+template <typename T>
+cudaError_t launch_snapshot(const T* f, const T* g, const T* J, const T* lo, int64_t P,
+                            int64_t n, T* out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_copy_to_T(T* dst, const double* src, int64_t n, cudaStream_t s);
 template <typename T>

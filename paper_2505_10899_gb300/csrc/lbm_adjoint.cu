@@ -508,11 +508,15 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
 }
 
 // Sum the stencil adjoints referring to each node's phi and psi and add them
-// to the adjoints of the node's 9 pulled g (phi = sum g).
+// to the adjoints of the node's 9 pulled g (phi = sum g).  With gB non-null
+// the same launch also forms phi and psi of the state held in gB (plane
+// stride PB): the state of the next adjoint step of a reverse sweep, whose
+// ad_node reads them.  Each node reads its own phi before it overwrites it,
+// and no other node reads it in this launch, so the two share the planes.
 template <typename R>
-__global__ void ad_gather(const R* __restrict__ phi, const R* __restrict__ lP,
+__global__ void ad_gather(R* __restrict__ phi, R* __restrict__ psi, const R* __restrict__ lP,
                           const R* __restrict__ lQ, int nx, int ny, int walls, R xi,
-                          R* __restrict__ aout) {
+                          R* __restrict__ aout, const R* __restrict__ gB, int64_t PB) {
   const int64_t n = (int64_t)nx * ny;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x) {
@@ -522,10 +526,17 @@ __global__ void ad_gather(const R* __restrict__ phi, const R* __restrict__ lP,
     const R p = phi[k];
     const R dpsi = (p > R(0) && p < R(1)) ? dpsi_dphi(p, xi) : R(0);
     const R tot = sp + dpsi * sq;
+    R G[9];
     for (int i = 0; i < 9; ++i) {
       int pl;
       const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
       aout[(9 + pl) * n + pos] += tot;
+      if (gB) G[i] = gB[pl * PB + pos];
+    }
+    if (gB) {  // phi (Eq. 35) and psi (Eq. 37) of the next state, as ad_phase
+      const R q = lbmk::sum9(G);
+      phi[k] = q;
+      psi[k] = lbmk::psi_of(q, xi);
     }
   }
 }
@@ -813,15 +824,20 @@ namespace {
 
 // One adjoint step from the state S_t held in (fA, gA, JA) with plane stride
 // P at step index t (the handle's own buffers, or a snapshot).
+// phase_ready: phi and psi of S_t are already in the scratch planes (the
+// previous step of a sweep formed them); gB/PB: g planes of the state of the
+// next step of a sweep, whose phi and psi the gather launch forms, or null.
 template <typename R>
 int adjoint_step_impl(lbm_handle* h, const R* fA, const R* gA, const R* JA, int64_t P, int64_t t,
-                      const void* d_adj_in, void* d_adj_out, double* h_param_grads) {
+                      const void* d_adj_in, void* d_adj_out, double* h_param_grads,
+                      bool phase_ready = false, const R* gB = nullptr, int64_t PB = 0) {
   const lbm_params& p = h->params[0];
   const CaseDev<R>& cd = case0<R>(h);
   const bool coupled = h->flow == LBM_FLOW_COUPLED;
   AdScratch s = carve(h);
-  ad_phase<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>(gA, P, p.nx, p.ny, p.walls, (R)p.xi,
-                                                       (R*)s.phi, (R*)s.psi);
+  if (!phase_ready)
+    ad_phase<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>(gA, P, p.nx, p.ny, p.walls, (R)p.xi,
+                                                         (R*)s.phi, (R*)s.psi);
   AdArgs<R> a{};
   a.fA = coupled ? fA : nullptr;
   a.gA = gA;
@@ -856,9 +872,9 @@ int adjoint_step_impl(lbm_handle* h, const R* fA, const R* gA, const R* JA, int6
     if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   }
   ad_node<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>(a);
-  ad_gather<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>((const R*)s.phi, (const R*)s.lP,
+  ad_gather<R><<<kAdBlocks, kAdThreads, 0, h->stream>>>((R*)s.phi, (R*)s.psi, (const R*)s.lP,
                                                         (const R*)s.lQ, p.nx, p.ny, p.walls,
-                                                        (R)p.xi, (R*)d_adj_out);
+                                                        (R)p.xi, (R*)d_adj_out, gB, PB);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, cudaGetErrorString(e));
   if (h_param_grads) return take_grads(h, h_param_grads);
@@ -949,15 +965,21 @@ int lbm_adjoint_sweep(lbm_handle* h, const void* d_states, int64_t stride_bytes,
     return fail(LBM_ERR_ARG, "stride_bytes smaller than a state");
   void* cur = d_adj;
   void* nxt = d_spare;
+  // each gather launch also forms phi and psi of the state of the next step
   for (int32_t j = count - 1; j >= 0; --j) {
     const char* st = (const char*)d_states + (int64_t)j * stride_bytes;
+    const char* stB = j > 0 ? st - stride_bytes : nullptr;
+    const bool ready = j != count - 1;
     if (h->precision == LBM_F32) {
       const float* sf = (const float*)st;
-      rc = adjoint_step_impl<float>(h, sf, sf + 9 * n, sf + 18 * n, n, t0 + j, cur, nxt, nullptr);
+      const float* gB = stB ? (const float*)stB + 9 * n : nullptr;
+      rc = adjoint_step_impl<float>(h, sf, sf + 9 * n, sf + 18 * n, n, t0 + j, cur, nxt, nullptr,
+                                    ready, gB, n);
     } else {
       const double* sd = (const double*)st;
+      const double* gB = stB ? (const double*)stB + 9 * n : nullptr;
       rc = adjoint_step_impl<double>(h, sd, sd + 9 * n, sd + 18 * n, n, t0 + j, cur, nxt,
-                                     nullptr);
+                                     nullptr, ready, gB, n);
     }
     if (rc) return rc;
     void* tmp = cur;

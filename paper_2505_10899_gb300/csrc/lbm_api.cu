@@ -1220,21 +1220,20 @@ int lbm_snapshot(lbm_handle* h, int32_t c, void* d_buf) {
   if (rc) return rc;
   if (!d_buf) return fail(LBM_ERR_ARG, "d_buf is null");
   const int64_t n = (int64_t)h->params[c].nx * h->params[c].ny;
-  const size_t es = elem_size(h->precision), pb = (size_t)h->L.plane[c] * es, nb = n * es;
-  char* out = (char*)d_buf;
   const bool coupled = h->flow == LBM_FLOW_COUPLED;
-  if (coupled)
-    LBM_CUDA(cudaMemcpy2DAsync(out, nb, h->ws + h->L.f[c] + h->parity * 9 * pb, pb, nb, 9,
-                               cudaMemcpyDeviceToDevice, h->stream));
-  else
-    LBM_CUDA(cudaMemsetAsync(out, 0, 9 * nb, h->stream));
-  LBM_CUDA(cudaMemcpy2DAsync(out + 9 * nb, nb, h->ws + h->L.g[c] + h->parity * 9 * pb, pb, nb, 9,
-                             cudaMemcpyDeviceToDevice, h->stream));
-  LBM_CUDA(cudaMemcpy2DAsync(out + 18 * nb, nb, h->ws + h->L.J[c] + h->parity * 2 * pb, pb, nb, 2,
-                             cudaMemcpyDeviceToDevice, h->stream));
-  if (es == 4)  // FP32: the low part of the g_0 float pair
-    LBM_CUDA(cudaMemcpyAsync(out + 20 * nb, h->ws + h->L.glo[c] + h->parity * pb, nb,
-                             cudaMemcpyDeviceToDevice, h->stream));
+  cudaError_t e;
+  if (h->precision == LBM_F32) {
+    const CaseDev<float>& cd = h->cf[c];
+    e = lbmk::launch_snapshot<float>(coupled ? cd.f[h->parity] : nullptr, cd.g[h->parity],
+                                     cd.J[h->parity], cd.g0lo[h->parity], cd.plane, n,
+                                     (float*)d_buf, h->stream);
+  } else {
+    const CaseDev<double>& cd = h->cd[c];
+    e = lbmk::launch_snapshot<double>(coupled ? cd.f[h->parity] : nullptr, cd.g[h->parity],
+                                      cd.J[h->parity], nullptr, cd.plane, n, (double*)d_buf,
+                                      h->stream);
+  }
+  if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("snapshot: ") + cudaGetErrorString(e));
   return LBM_OK;
 }
 

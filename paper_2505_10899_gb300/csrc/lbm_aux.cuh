@@ -208,6 +208,23 @@ __global__ void __launch_bounds__(BX) init_items(const CaseDev<T>* __restrict__ 
   }
 }
 
+// Device snapshot of one case's state (the layout of lbm_snapshot): plane
+// blockIdx.y of [f: 9][g: 9][phi*u: 2][low part of g_0: 1, FP32 only], each
+// n values, from the buffers with plane stride P (f null: zero planes).  One
+// launch for the whole snapshot instead of a copy per buffer.
+template <typename T>
+__global__ void snapshot_kernel(const T* __restrict__ f, const T* __restrict__ g,
+                                const T* __restrict__ J, const T* __restrict__ lo, int64_t P,
+                                int64_t n, T* __restrict__ out) {
+  const int pl = blockIdx.y;
+  const T* src = pl < 9 ? (f ? f + pl * P : nullptr)
+                        : (pl < 18 ? g + (pl - 9) * P : (pl < 20 ? J + (pl - 18) * P : lo));
+  T* dst = out + (int64_t)pl * n;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = src ? src[k] : T(0);
+}
+
 // Import one population plane (FP64 host layout, value at the node it
 // belongs to after streaming) into a pull buffer, or export it.
 // buf: the 9-plane buffer (plane stride P); with walls the value of plane i
