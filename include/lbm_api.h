@@ -136,8 +136,9 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace,
  * isotropic stencils (Sec. 3.2), hbar (Eq. 2), F = hbar grad phi, u and p
  * (Eqs. 28-29), MRT collision of f (Eqs. 21-25) and of g (Eqs. 31-33) with
  * d_t(phi u) by backward difference.  Asynchronous on the handle's stream:
- * the steps run as captured CUDA graphs of up to 64 steps, built on first
- * use of a step count and cached (a few per handle).  Errors: LBM_ERR_ARG,
+ * runs of 4 steps or more replay captured CUDA graphs of up to 64 steps,
+ * built on first use of a step count and cached (a few per handle); shorter
+ * runs are launched directly.  Errors: LBM_ERR_ARG,
  * LBM_ERR_CUDA (launch failure; device faults surface at the next
  * synchronising call). */
 int lbm_step(lbm_handle* h, int64_t nsteps);

@@ -43,6 +43,7 @@ int fail(int code, const std::string& msg) {
 
 constexpr size_t kAlign = 256;
 constexpr int kGraphSteps = 64;  // steps per captured graph (even)
+constexpr int kDirectSteps = 4;  // shorter runs are launched without a graph
 
 size_t align_up(size_t v, size_t a = kAlign) { return (v + a - 1) / a * a; }
 
@@ -748,12 +749,14 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   };
   if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess)
     return cleanup(fail(LBM_ERR_CUDA, "cannot create capture stream"));
-  for (int c = 0; c < lbmk::kMaxChains - 1; ++c)
-    if (cudaStreamCreateWithFlags(&h->aux[c], cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->join_ev[c], cudaEventDisableTiming) != cudaSuccess)
-      return cleanup(fail(LBM_ERR_CUDA, "cannot create chain streams"));
-  if (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess)
-    return cleanup(fail(LBM_ERR_CUDA, "cannot create chain events"));
+  if (ncases > 1) {  // chains need a stream and an event each (one case: one chain)
+    for (int c = 0; c < lbmk::kMaxChains - 1; ++c)
+      if (cudaStreamCreateWithFlags(&h->aux[c], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&h->join_ev[c], cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(fail(LBM_ERR_CUDA, "cannot create chain streams"));
+    if (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+      return cleanup(fail(LBM_ERR_CUDA, "cannot create chain events"));
+  }
   {
     cudaError_t e = h->precision == LBM_F32 ? lbmk::prepare_tma<float>() : lbmk::prepare_tma<double>();
     if (e != cudaSuccess)
@@ -856,6 +859,16 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     }
     return LBM_OK;
   }
+  // short runs are launched directly: a graph pays off only over several
+  // steps, and a caller that steps many handles one step at a time would
+  // otherwise cycle through as many graphs
+  if (nsteps < kDirectSteps) {
+    int rc = enqueue_steps(h, h->stream, h->parity, (int)nsteps, true, true, true);
+    if (rc) return rc;
+    h->parity ^= (int)(nsteps & 1);
+    h->t += nsteps;
+    return LBM_OK;
+  }
   // chunks of kGraphSteps steps, then the remainder, each a cached graph
   while (nsteps > 0) {
     const int cnt = (int)std::min<int64_t>(nsteps, kGraphSteps);
@@ -874,6 +887,7 @@ int lbm_prepare_steps(lbm_handle* h, int64_t nsteps) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (nsteps < 0) return fail(LBM_ERR_ARG, "nsteps < 0");
   if (h->kernel == 3 && !h->track) return LBM_OK;  // one cooperative launch, nothing to capture
+  if (nsteps < kDirectSteps) return LBM_OK;         // launched directly
   int parity = h->parity;
   while (nsteps > 0) {
     const int cnt = (int)std::min<int64_t>(nsteps, kGraphSteps);
