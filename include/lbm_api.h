@@ -136,9 +136,12 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace,
  * isotropic stencils (Sec. 3.2), hbar (Eq. 2), F = hbar grad phi, u and p
  * (Eqs. 28-29), MRT collision of f (Eqs. 21-25) and of g (Eqs. 31-33) with
  * d_t(phi u) by backward difference.  Asynchronous on the handle's stream:
- * runs of 4 steps or more replay captured CUDA graphs of up to 64 steps,
- * built on first use of a step count and cached (a few per handle); shorter
- * runs are launched directly.  Errors: LBM_ERR_ARG,
+ * runs of 4 steps or more are cut into chunks of up to 64 steps; the first
+ * chunk of a given length (and source buffer) is launched directly, and
+ * when that length comes again its steps are captured into a CUDA graph,
+ * cached (a few per handle) and replayed from then on (lbm_prepare_steps
+ * builds them ahead of time).  Shorter runs are always launched directly.
+ * Errors: LBM_ERR_ARG,
  * LBM_ERR_CUDA (launch failure; device faults surface at the next
  * synchronising call). */
 int lbm_step(lbm_handle* h, int64_t nsteps);
@@ -195,6 +198,19 @@ int lbm_volume_async(lbm_handle* h, double* d_out);
  * batches whose cases all have one region (no labels): LBM_ERR_ARG
  * otherwise.  d_out = NULL switches tracking off. */
 int lbm_track_volume(lbm_handle* h, double* d_out);
+
+/* Fused volume tracking with a history: like lbm_track_volume, but the step
+ * from time t writes the per-case volumes of the state at time t to slot
+ * t mod nslots of out (slot k: out[k * ncases .. (k+1) * ncases)).  out may
+ * be device memory or page-locked host memory that the device can address
+ * (cudaHostAlloc, or pinned and registered memory): the step kernels' final
+ * reduction then writes each step's volumes to the host by itself, so a run
+ * of n <= nslots steps in one lbm_step call delivers every step's volumes
+ * without a copy or a synchronisation between steps.  The caller reads them
+ * after synchronising the stream.  nslots >= 1; lbm_track_volume(h, p) is
+ * nslots = 1.  out = NULL switches tracking off.  Errors: LBM_ERR_ARG
+ * (labelled regions, nslots < 1, out neither device nor page-locked). */
+int lbm_track_volume_history(lbm_handle* h, double* out, int64_t nslots);
 
 /* Work tiling of the step kernel: each CTA owns a strip of bx columns
  * (bx in {32, 64, 128}) and marches down runs of `rows` rows (2..1024).

@@ -240,15 +240,19 @@ cudaError_t launch_volume<LBM_T>(const CaseDev<LBM_T>* cases, int ncases,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int warps = 4;
-  volume_final<LBM_T><<<(ncases + warps - 1) / warps, 32 * warps, 0, s>>>(cases, ncases, part, out);
+  volume_final<LBM_T><<<(ncases + warps - 1) / warps, 32 * warps, 0, s>>>(cases, ncases, part, out,
+                                                                         nullptr, 0, 0, 0);
   return cudaGetLastError();
 }
 
 template <>
 cudaError_t launch_volume_final<LBM_T>(const CaseDev<LBM_T>* cases, int ncases,
-                                       const double* part, double* out, cudaStream_t s) {
+                                       const double* part, double* out, const int64_t* t,
+                                       int64_t toff, int64_t slots, int64_t stride,
+                                       cudaStream_t s) {
   const int warps = 4;
-  volume_final<LBM_T><<<(ncases + warps - 1) / warps, 32 * warps, 0, s>>>(cases, ncases, part, out);
+  volume_final<LBM_T><<<(ncases + warps - 1) / warps, 32 * warps, 0, s>>>(cases, ncases, part, out,
+                                                                         t, toff, slots, stride);
   return cudaGetLastError();
 }
 

@@ -73,7 +73,8 @@ cudaError_t launch_volume(const CaseDev<T>* cases, int ncases,
 // Per-case sums of the partials written by the step kernel (vol_part).
 template <typename T>
 cudaError_t launch_volume_final(const CaseDev<T>* cases, int ncases, const double* part,
-                                double* out, cudaStream_t s);
+                                double* out, const int64_t* t, int64_t toff, int64_t slots,
+                                int64_t stride, cudaStream_t s);
 
 cudaError_t launch_clock(int64_t* t, int64_t n, cudaStream_t s);
 cudaError_t launch_set_clock(int64_t* t, int64_t value, cudaStream_t s);

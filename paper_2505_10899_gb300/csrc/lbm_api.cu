@@ -425,7 +425,8 @@ int enqueue_steps(lbm_handle* h, cudaStream_t s, int parity, int count, bool fli
         e = lbmk::launch_step<float>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), ni, sc);
         if (e == cudaSuccess && vol && h->track)
           e = lbmk::launch_volume_final<float>((const CaseDev<float>*)h->cases_dev + c0, nc,
-                                               h->part, h->track, sc);
+                                               h->part, h->track, h->t_dev, toff,
+                                               h->track_slots, h->total_regions, sc);
       } else {
         StepArgs<double> a = step_args<double>(h, par, toff);
         a.items = h->items_dev + i0;
@@ -433,7 +434,8 @@ int enqueue_steps(lbm_handle* h, cudaStream_t s, int parity, int count, bool fli
         e = lbmk::launch_step<double>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), ni, sc);
         if (e == cudaSuccess && vol && h->track)
           e = lbmk::launch_volume_final<double>((const CaseDev<double>*)h->cases_dev + c0, nc,
-                                                h->part, h->track, sc);
+                                               h->part, h->track, h->t_dev, toff,
+                                               h->track_slots, h->total_regions, sc);
       }
       if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
     }
@@ -452,6 +454,7 @@ void drop_graph(lbm_handle* h) {
   for (auto& g : h->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   h->graphs.clear();
+  h->seen.clear();
 }
 
 // Capture `count` steps from source buffer `parity` (with or without flipping
@@ -478,6 +481,23 @@ int capture_steps(lbm_handle* h, int parity, int count, bool flip, bool vol, boo
 }
 
 constexpr size_t kGraphCache = 8;
+
+bool graph_cached(const lbm_handle* h, int count, int parity) {
+  for (const auto& g : h->graphs)
+    if (g.count == count && g.parity == parity) return true;
+  return false;
+}
+
+// Whether a run of (count, parity) was met before; records it if not (the
+// last 16 kinds of run are remembered).
+bool seen_before(lbm_handle* h, int count, int parity) {
+  const int key = 2 * count + parity;
+  for (int k : h->seen)
+    if (k == key) return true;
+  if (h->seen.size() >= 16) h->seen.erase(h->seen.begin());
+  h->seen.push_back(key);
+  return false;
+}
 
 // The graph of `count` steps from source buffer `parity`, built on first use.
 int step_graph(lbm_handle* h, int count, int parity, cudaGraphExec_t* out) {
@@ -869,13 +889,22 @@ int lbm_step(lbm_handle* h, int64_t nsteps) {
     h->t += nsteps;
     return LBM_OK;
   }
-  // chunks of kGraphSteps steps, then the remainder, each a cached graph
+  // chunks of kGraphSteps steps, then the remainder, each a cached graph.
+  // A (count, parity) met for the first time is launched directly: its
+  // graph is built when it comes again (or ahead of time by
+  // lbm_prepare_steps), so a one-off run does not pay for capturing and
+  // instantiating a graph that is never replayed.
   while (nsteps > 0) {
     const int cnt = (int)std::min<int64_t>(nsteps, kGraphSteps);
     cudaGraphExec_t gx = nullptr;
-    int rc = step_graph(h, cnt, h->parity, &gx);
-    if (rc) return rc;
-    LBM_CUDA(cudaGraphLaunch(gx, h->stream));
+    if (!graph_cached(h, cnt, h->parity) && !seen_before(h, cnt, h->parity)) {
+      int rc = enqueue_steps(h, h->stream, h->parity, cnt, true, true, true);
+      if (rc) return rc;
+    } else {
+      int rc = step_graph(h, cnt, h->parity, &gx);
+      if (rc) return rc;
+      LBM_CUDA(cudaGraphLaunch(gx, h->stream));
+    }
     h->parity ^= (cnt & 1);
     h->t += cnt;
     nsteps -= cnt;
@@ -1072,16 +1101,31 @@ int lbm_set_chains(lbm_handle* h, int32_t nchains) {
 
 int32_t lbm_get_chains(const lbm_handle* h) { return h ? h->nchains : 0; }
 
-int lbm_track_volume(lbm_handle* h, double* d_out) {
+int lbm_track_volume_history(lbm_handle* h, double* out, int64_t nslots) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
-  if (d_out)
+  if (out) {
+    if (nslots < 1) return fail(LBM_ERR_ARG, "nslots < 1");
     for (int k = 0; k < h->ncases; ++k)
       if (h->nregions[k] != 1 ||
           (h->precision == LBM_F32 ? h->cf[k].labels != nullptr : h->cd[k].labels != nullptr))
         return fail(LBM_ERR_ARG, "volume tracking needs one unlabelled region per case");
-  if (d_out != h->track) drop_graph(h);
-  h->track = d_out;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, out) != cudaSuccess) cudaGetLastError();
+    const bool ok = (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
+                     at.type == cudaMemoryTypeHost) && at.devicePointer != nullptr;
+    if (!ok) return fail(LBM_ERR_ARG, "volume output must be device or page-locked host memory");
+    out = static_cast<double*>(at.devicePointer);
+  } else {
+    nslots = 1;
+  }
+  if (out != h->track || nslots != h->track_slots) drop_graph(h);
+  h->track = out;
+  h->track_slots = nslots;
   return LBM_OK;
+}
+
+int lbm_track_volume(lbm_handle* h, double* d_out) {
+  return lbm_track_volume_history(h, d_out, 1);
 }
 
 int lbm_volume_async(lbm_handle* h, double* d_out) {

@@ -61,27 +61,38 @@ __device__ __forceinline__ double phi_at(const CaseDev<T>& cd, int par, int x, i
   return phi;
 }
 
+// The moving-wall term of wall_term in the arithmetic type R of the init.
+template <typename T, typename R>
+__device__ __forceinline__ R wall_term_r(const CaseDev<T>& cd, int i, int y, R rho) {
+  if (!cd.walls) return R(0);
+  const R w = (i == 0) ? R(4.0 / 9.0) : (i < 5 ? R(1.0 / 9.0) : R(1.0 / 36.0));
+  if (y == 0 && kCY[i] == 1) return R(6) * w * rho * R(kCX[i]) * (R)cd.u_bot;
+  if (y == cd.ny - 1 && kCY[i] == -1) return R(6) * w * rho * R(kCX[i]) * (R)cd.u_top;
+  return R(0);
+}
+
 // Initial state of one node (Sec. 4 set-ups): hbar0 = 4 beta phi0 (phi0-1)
 // (phi0-1/2) - kappa lap(phi0) (Eq. 2), g = g_eq(phi0, hbar0, u0) (Eq. 31),
-// f = f_eq(p=0, rho(phi0), u0) (Eq. 22), phi*u at t-1 = phi0 u0.  nb: phi0
-// at the eight neighbours E, W, N, S, NE, NW, SE, SW (with walls, the ghost
-// rows mirror the wall rows).
+// f = f_eq(p=0, rho(phi0), u0) (Eq. 22), phi*u at t-1 = phi0 u0.  p64: phi0
+// of the node in FP64, p: the same in R; nb: phi0 at the eight neighbours E,
+// W, N, S, NE, NW, SE, SW in R (with walls, the ghost rows mirror the wall
+// rows).
 // R is the arithmetic type: FP64 for FP64 state (computed in FP64, rounded
-// once); FP32 for FP32 state (the FP64 pipe of the GPU is narrow and an FP64
-// init of a large batch takes it ~165 FP64 instructions per node), except
-// the rest population, which takes the remainder phi0 - sum of the stored
-// movers in FP64 and is stored as the float pair of the FP32 step, so that
-// the stored populations sum to phi0 to FP64 rounding.
+// once); FP32 for FP32 state.  The FP64 pipe of this GPU runs at 1/64 of the
+// FP32 rate, so the FP32 init keeps off it: the rest population, the
+// remainder g_0 = phi0 - (sum of the stored movers) that makes the stored
+// populations sum to phi0, is formed in float-pair arithmetic -- the movers
+// summed by error-free TwoSums into a pair, phi0 split into a pair (one FP64
+// subtraction), their difference by another TwoSum -- and stored as the float
+// pair (hi + lo) of the FP32 step.  The pair sums to phi0 within about 2^-42
+// of phi0 (the FP32 rounding of the summed TwoSum errors), far below the
+// FP32 state's own rounding.
 template <typename T, typename R>
-__device__ __forceinline__ void init_node(const CaseDev<T>& cd, int x, int y, double p64,
-                                          const double nb64[8], R ux, R uy, R beta4, R kappa,
+__device__ __forceinline__ void init_node(const CaseDev<T>& cd, int x, int y, double p64, R p,
+                                          const R nb[8], R ux, R uy, R beta4, R kappa,
                                           R lambda, R rho_g, R drho, int parity) {
   const int nx = cd.nx, ny = cd.ny;
   const int64_t k = (int64_t)y * nx + x;
-  const R p = (R)p64;
-  R nb[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) nb[j] = (R)nb64[j];
   const R lap = R(2.0 / 3.0) * (((nb[0] + nb[1]) + (nb[2] + nb[3])) - R(4) * p) +
                 R(1.0 / 6.0) * (((nb[4] + nb[5]) + (nb[6] + nb[7])) - R(4) * p);
   const R mu = beta4 * p * (p - R(1)) * (p - R(0.5)) - kappa * lap;
@@ -91,7 +102,7 @@ __device__ __forceinline__ void init_node(const CaseDev<T>& cd, int x, int y, do
   const R u2 = ux * ux + uy * uy;
   T* gb = cd.g[parity];
   T* fb = cd.f[parity];
-  double movers = 0.0;  // FP32: sum of the stored movers, in FP64
+  float ms = 0.f, me = 0.f;  // FP32: sum of the stored movers as a float pair
   int64_t dst0 = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -106,19 +117,29 @@ __device__ __forceinline__ void init_node(const CaseDev<T>& cd, int x, int y, do
     } else {
       const T gi = (T)(w * lam + R(3) * w * cJ);
       gb[dst] = gi;
-      movers += (double)gi;
+      if (sizeof(R) == 4) {
+        float t, e;
+        two_sum_f(ms, (float)gi, t, e);
+        ms = t;
+        me = __fadd_rn(me, e);
+      }
     }
     // f arriving from a wall carries the moving-wall term on top of the
     // stored value: store f_eq minus that term
     if (fb)
       fb[dst] = (T)(rho * w * (R(3) * cu + R(4.5) * cu * cu - R(1.5) * u2) -
-                    (R)wall_term(cd, i, y, (double)rho));
+                    wall_term_r<T, R>(cd, i, y, rho));
   }
   if (sizeof(R) == 4) {  // FP32: g_0 = phi0 - movers as a float pair (high + low part)
-    const double g0 = p64 - movers;
-    const T hi = (T)g0;
-    gb[dst0] = hi;
-    if (cd.g0lo[parity]) cd.g0lo[parity][k] = (T)(g0 - (double)hi);
+    const float ph = (float)p;                       // p = phi0 rounded to FP32
+    const float pl = (float)(p64 - (double)ph);      // exact remainder, rounded
+    float d, e;
+    two_sum_f(ph, -ms, d, e);                        // ph - ms = d + e exactly
+    const float rest = __fadd_rn(e, __fsub_rn(pl, me));
+    float hi, lo;
+    two_sum_f(d, rest, hi, lo);
+    gb[dst0] = (T)hi;
+    if (cd.g0lo[parity]) cd.g0lo[parity][k] = (T)lo;
   }
   cd.J[parity][k] = (T)Jx;
   cd.J[parity][cd.plane + k] = (T)Jy;
@@ -140,6 +161,10 @@ __global__ void __launch_bounds__(BX) init_items(const CaseDev<T>* __restrict__ 
                                                  double kappa, double lambda, int vortex,
                                                  double vU, int parity) {
   __shared__ double ring[8][BX + 2];
+  // FP32 state: phi0 also rounded to FP32 once per loaded value, for the
+  // arithmetic (the FP64 ring serves the rest population of the own node)
+  constexpr bool kF32 = sizeof(T) == 4;
+  __shared__ T rring[kF32 ? 8 : 1][BX + 2];
   const Item it = items[blockIdx.x];
   const CaseDev<T> cd = cases[it.c];
   const InitSrc sc = src[it.c];
@@ -156,12 +181,34 @@ __global__ void __launch_bounds__(BX) init_items(const CaseDev<T>* __restrict__ 
     if (r >= ny) return cd.walls ? ny - 1 : 0;
     return r;
   };
-  auto load = [&](int r) {
+  // phi0 of row r at this thread's ring slots (own column; thread 0 also the
+  // left halo column, thread BX - 1 the right one), fetched into registers
+  // and stored into the ring two rows later, so that the loads of the
+  // following rows stay in flight while a row is initialised (a load
+  // stored straight into shared memory would stall the thread on it)
+  struct RowV {
+    double c = 0.0, h = 0.0;
+  };
+  auto fetch = [&](int r) -> RowV {
+    RowV v;
+    if (r > yend) return v;  // past the halo row below the item
     const int64_t base = (int64_t)row_of(r) * nx;
+    if (act) v.c = sc.phi[base + x];
+    if (tid == 0) v.h = sc.phi[base + xl];
+    if (tid == BX - 1) v.h = sc.phi[base + xr];
+    return v;
+  };
+  auto stash = [&](int r, const RowV& v) {
+    if (r > yend) return;
     double* dst = ring[r & 7];
-    if (act) dst[tid + 1] = sc.phi[base + x];
-    if (tid == 0) dst[0] = sc.phi[base + xl];
-    if (tid == BX - 1) dst[wact + 1] = sc.phi[base + xr];
+    T* rdst = rring[kF32 ? (r & 7) : 0];
+    auto put = [&](int slot, double val) {
+      dst[slot] = val;
+      if constexpr (kF32) rdst[slot] = (T)val;
+    };
+    if (act) put(tid + 1, v.c);
+    if (tid == 0) put(0, v.h);
+    if (tid == BX - 1) put(wact + 1, v.h);
   };
   // u0 of the own node of row r (rows of this item only)
   const bool has_u = !vortex && sc.u != nullptr;
@@ -172,37 +219,44 @@ __global__ void __launch_bounds__(BX) init_items(const CaseDev<T>* __restrict__ 
       uy = sc.u[(int64_t)nx * ny + k];
     }
   };
+  using R = T;  // arithmetic type of the init, see init_node
+  const R beta4r = (R)beta4, kappar = (R)kappa, lambdar = (R)lambda, vUr = (R)vU;
+  const R rhogr = (R)sc.rho_g, drhor = (R)sc.drho;
   double ux0 = 0.0, uy0 = 0.0, ux1 = 0.0, uy1 = 0.0;
-  load(it.y0 - 1);
-  load(it.y0);
-  load(it.y0 + 1);
+  stash(it.y0 - 1, fetch(it.y0 - 1));
+  stash(it.y0, fetch(it.y0));
+  stash(it.y0 + 1, fetch(it.y0 + 1));
+  RowV pA = fetch(it.y0 + 2), pB = fetch(it.y0 + 3);  // rows in flight
   load_u(it.y0, ux0, uy0);
   load_u(it.y0 + 1, ux1, uy1);
   for (int y = it.y0; y < yend; ++y) {
-    // two rows ahead: phi0 of row y + 2 (slot (y+2) & 7, last read for row
-    // y - 5, long done) and u0 of row y + 2
+    // phi0 of row y + 4 and u0 of row y + 2 start; row y + 2 (fetched two
+    // rows ago) goes into the ring (slot (y+2) & 7, last read for row y - 5)
+    const RowV pC = fetch(y + 4);
     double ux2 = 0.0, uy2 = 0.0;
-    if (y + 2 <= yend) load(y + 2);
     load_u(y + 2, ux2, uy2);
+    stash(y + 2, pA);
+    pA = pB;
+    pB = pC;
     __syncthreads();  // rows up to y + 1 are in the ring
     if (act) {
-      const double* rS = ring[(y - 1) & 7];
-      const double* rC = ring[y & 7];
-      const double* rN = ring[(y + 1) & 7];
       const int c = tid + 1;
-      const double nb[8] = {rC[c + 1], rC[c - 1], rN[c], rS[c],
-                            rN[c + 1], rN[c - 1], rS[c + 1], rS[c - 1]};
-      using R = T;  // arithmetic type of the init, see init_node
+      // arithmetic in R: FP32 values from the rounded ring, FP64 from the FP64 one
+      const R* rS = kF32 ? (const R*)rring[kF32 ? ((y - 1) & 7) : 0] : (const R*)ring[(y - 1) & 7];
+      const R* rC = kF32 ? (const R*)rring[kF32 ? (y & 7) : 0] : (const R*)ring[y & 7];
+      const R* rN = kF32 ? (const R*)rring[kF32 ? ((y + 1) & 7) : 0] : (const R*)ring[(y + 1) & 7];
+      const R nb[8] = {rC[c + 1], rC[c - 1], rN[c], rS[c],
+                       rN[c + 1], rN[c - 1], rS[c + 1], rS[c - 1]};
       R ux = (R)ux0, uy = (R)uy0;
       if (vortex) {
         R sx, cx, sy, cy;
         Num<R>::sincospi_((R(x) + R(0.5)) / R(nx), &sx, &cx);
         Num<R>::sincospi_((R(y) + R(0.5)) / R(ny), &sy, &cy);
-        ux = -(R)vU * sx * sx * (R(2) * sy * cy);
-        uy = (R)vU * sy * sy * (R(2) * sx * cx);
+        ux = -vUr * sx * sx * (R(2) * sy * cy);
+        uy = vUr * sy * sy * (R(2) * sx * cx);
       }
-      init_node<T, R>(cd, x, y, rC[c], nb, ux, uy, (R)beta4, (R)kappa, (R)lambda, (R)sc.rho_g,
-                      (R)sc.drho, parity);
+      init_node<T, R>(cd, x, y, ring[y & 7][c], rC[c], nb, ux, uy, beta4r, kappar, lambdar,
+                      rhogr, drhor, parity);
     }
     ux0 = ux1, uy0 = uy1, ux1 = ux2, uy1 = uy2;
   }
@@ -365,11 +419,17 @@ __global__ void __launch_bounds__(BX) volume_partial(const CaseDev<T>* __restric
 // the partials of items l, l+32, ... in order, then the lanes are combined
 // by a fixed shuffle tree: the result does not depend on timing.
 template <typename T>
+// With a history (slots > 1), the volumes of the state at step t + toff (t
+// the device step clock) go to slot (t + toff) mod slots, `stride` doubles
+// per slot.
 __global__ void volume_final(const CaseDev<T>* __restrict__ cases, int ncases,
-                             const double* __restrict__ part, double* __restrict__ out) {
+                             const double* __restrict__ part, double* __restrict__ out,
+                             const int64_t* __restrict__ t, int64_t toff, int64_t slots,
+                             int64_t stride) {
   const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (c >= ncases) return;
+  if (slots > 1) out += ((*t + toff) % slots) * stride;
   const CaseDev<T>& cd = cases[c];
   for (int r = 0; r < cd.nregions; ++r) {
     double v = 0.0;

@@ -67,7 +67,9 @@ struct lbm_handle {
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[lbmk::kMaxChains - 1] = {};
   std::vector<lbmk::StepGraph> graphs;  // cache, oldest first
-  double* track = nullptr;  // fused volume output (device), or null
+  std::vector<int> seen;                // kinds of run met so far (2 count + parity)
+  double* track = nullptr;  // fused volume output (device address), or null
+  int64_t track_slots = 1;  // steps of volume history in `track`
   bool tma_ok = false;      // every case allows the bulk-copy kernel
   int kernel = 0;           // 0 auto, 1 register-pipelined, 2 bulk-copy staged
   long long wait_cycles = lbmk::kWaitCycles;  // bound of the device waits

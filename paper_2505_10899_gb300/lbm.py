@@ -81,6 +81,7 @@ def _load():
         "lbm_volume_async": ([_H, _VP], ctypes.c_int),
         "lbm_num_regions": ([_H], ctypes.c_int32),
         "lbm_track_volume": ([_H, _VP], ctypes.c_int),
+        "lbm_track_volume_history": ([_H, _VP, ctypes.c_int64], ctypes.c_int),
         "lbm_get_tiling": ([_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                             ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
         "lbm_set_tiling": ([_H, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
@@ -243,6 +244,12 @@ def lbm_set_regions(h, c: int, labels, nregions: int):
 def lbm_track_volume(h, d_out: int):
     return _check(_lib.lbm_track_volume(h, ctypes.c_void_p(d_out) if d_out else None),
                   "lbm_track_volume")
+
+
+def lbm_track_volume_history(h, out: int, nslots: int):
+    """out: address of device or page-locked host memory, nslots * ncases FP64."""
+    return _check(_lib.lbm_track_volume_history(h, ctypes.c_void_p(out) if out else None,
+                                                int(nslots)), "lbm_track_volume_history")
 
 
 def lbm_get_tiling(h):
@@ -485,6 +492,20 @@ class Sim:
         lbm_track_volume(self.h, 0)
         self.vol_track = None
         return None
+
+    def track_volume_history(self, nslots, host=True):
+        """Fused per-step volumes into an [nslots][ncases] FP64 tensor, slot
+        t mod nslots for the state at time t: page-locked host memory that
+        the step kernels write directly (host=True), or device memory."""
+        import torch
+        shape = (int(nslots), len(self.cases))
+        if host:
+            buf = torch.zeros(shape, dtype=torch.float64).pin_memory()
+        else:
+            buf = torch.zeros(shape, dtype=torch.float64, device=self.device)
+        lbm_track_volume_history(self.h, buf.data_ptr(), nslots)
+        self.vol_track = buf
+        return buf
 
     def fields(self, c=0):
         return lbm_fields(self.h, c, self.shape(c))

@@ -331,6 +331,47 @@ def test_fused_volume_tracking(L):
         s.track_volume(True)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("host", [True, False])
+def test_fused_volume_history(L, prec, host):
+    # Slot t mod nslots holds the fused volumes of the state at time t, for
+    # every step, whether the steps ran directly, from a graph, or in chains;
+    # a page-locked host history is written by the kernels themselves.  The
+    # values are those of plain tracking read after every single step, bit
+    # for bit (same tiling, same chains, deterministic reductions).
+    import torch
+    cases, phis, us = _chain_batch()
+    T = 13
+    r = L.Sim(cases, phis, us, precision=prec)
+    r.set_chains(2)
+    vol = r.track_volume(True)
+    rec = []
+    for t in range(T):
+        r.step(1)
+        torch.cuda.synchronize()
+        rec.append(vol.cpu().numpy().copy())
+    r.close()
+    for nslots in (16, 8):
+        s = L.Sim(cases, phis, us, precision=prec)
+        s.set_chains(2)
+        hist = s.track_volume_history(nslots, host=host)
+        for n in (2, 5, 5, 1):  # direct, first-seen chunk direct, then its graph, direct
+            s.step(n)
+        assert s.t == T
+        torch.cuda.synchronize()
+        got = hist.cpu().numpy()
+        for t in range(max(0, T - nslots), T):
+            assert np.array_equal(got[t % nslots], rec[t]), (nslots, t)
+        if nslots > T:
+            assert not got[T:].any()  # slots of later times untouched
+        with pytest.raises(L.LbmError):
+            L.lbm_track_volume_history(s.h, hist.data_ptr(), 0)
+        pageable = np.zeros((nslots, len(cases)))
+        with pytest.raises(L.LbmError):
+            L.lbm_track_volume_history(s.h, pageable.ctypes.data, nslots)
+        s.close()
+
+
 def test_kernel_variants_agree_fp32(L):
     # both load paths feed the same per-node arithmetic: equal to FP32 rounding
     case = W.base_case(160, 72, rho_l=4.0, tau_f_l=0.8, tau_f_g=1.2)
