@@ -51,9 +51,11 @@ struct TmaShape {
   static_assert((SEG * sizeof(T)) % 16 == 0, "plane segment must keep 16-byte alignment");
 };
 
-template <typename T, int BX, bool COUPLED, int MODE, int S>
-__global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
-    step_kernel_tma(const StepArgs<T> a) {
+// The kernel body, for strips that hold a whole row (FROW: x0 = 0 and
+// nx <= BX) or not; the kernel picks one per CTA, so that the strips of wide
+// rows keep compile-time staged positions.
+template <typename T, int BX, bool COUPLED, int MODE, int S, bool FROW>
+__device__ __forceinline__ void tma_body(const StepArgs<T>& a) {
   using SH = TmaShape<T, BX, COUPLED, MODE, S>;
   constexpr int SEG = SH::SEG, NPL = SH::NPL, NJ = SH::NJ, STAGE = SH::STAGE;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -89,6 +91,19 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
   const bool hthr = (tid == 0) || (tid == BX - 1);
   const int hcol = (tid == 0) ? -1 : wact;
   const int hslot = (tid == 0) ? 0 : wact + 1;
+  // A strip that holds the whole row (x0 = 0, nx <= BX) stages the row once,
+  // columns 0..nx-1 at positions 4..nx+3, and reads the periodic neighbours
+  // of its edge columns from the other end of the same copy; other strips
+  // stage global column x0 - 4 + j at position j.  Staged position of local
+  // column c + d, d = -1, 0, +1 (the pull sources of c_x = +1, 0, -1):
+  constexpr bool frow = FROW;
+  auto spos = [&](int c, int d) -> int {
+    int j = c + d;
+    if (frow) j = j < 0 ? j + nx : (j >= nx ? j - nx : j);
+    return j + 4;
+  };
+  const int om = spos(tid, -1), o0 = spos(tid, 0), op = spos(tid, 1);
+  const int hm = spos(hcol, -1), h0 = spos(hcol, 0), hp = spos(hcol, 1);
 
   const T xi = a.ph.xi;
   const bool do_vol = (MODE == kModeStep) && (a.vol_part != nullptr);
@@ -127,7 +142,9 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
     constexpr uint32_t kNeedR = 0x0DDu | (0x0C8u << 9);  // g: c_x <= 0; f: c_x = -1
     const bool lw = (x0 == 0), rw = (x0 + wact >= nx);
     uint32_t elems = (uint32_t)(np * (wact + 8) + nj * wact);
-    if (lw || rw) {  // the wrap columns that no plane reads are not copied
+    if (frow) {  // one copy of the whole row per plane
+      elems = (uint32_t)(np * nx + nj * wact);
+    } else if (lw || rw) {  // the wrap columns that no plane reads are not copied
       const int nwrap = (full && COUPLED) ? 9 : 6;  // 6 g planes, + 3 f planes on full rows
       elems -= (uint32_t)((lw ? 4 * (np - nwrap) : 0) + (rw ? 4 * (np - nwrap) : 0));
     }
@@ -150,20 +167,24 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
       const int64_t row = (int64_t)wrap(r - cy_of(i)) * nx;  // pull: source row r - c_iy
       T* dst = st + lane * SEG;
       int j = 0, g0, len;
-      if (lw) {
-        if ((kNeedL >> lane) & 1u) copy(dst, plane, buf, row + (nx - 4), 4);
-        j = 4;
-        g0 = 0;
-        len = wact;
+      if (frow) {
+        copy(dst + 4, plane, buf, row, (uint32_t)nx);
       } else {
-        g0 = x0 - 4;
-        len = wact + 4;
-      }
-      if (!rw) {
-        copy(dst + j, plane, buf, row + g0, (uint32_t)(len + 4));
-      } else {
-        copy(dst + j, plane, buf, row + g0, (uint32_t)len);
-        if ((kNeedR >> lane) & 1u) copy(dst + j + len, plane, buf, row, 4);
+        if (lw) {
+          if ((kNeedL >> lane) & 1u) copy(dst, plane, buf, row + (nx - 4), 4);
+          j = 4;
+          g0 = 0;
+          len = wact;
+        } else {
+          g0 = x0 - 4;
+          len = wact + 4;
+        }
+        if (!rw) {
+          copy(dst + j, plane, buf, row + g0, (uint32_t)(len + 4));
+        } else {
+          copy(dst + j, plane, buf, row + g0, (uint32_t)len);
+          if ((kNeedR >> lane) & 1u) copy(dst + j + len, plane, buf, row, 4);
+        }
       }
     } else if (lane >= NPL && lane < NPL + nj) {
       const int q = lane - NPL;
@@ -171,10 +192,12 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
     }
   };
 
-  // g of local column c (may be -1 or wact) from a staged row
-  auto staged_g = [&](const T* st, int c, T G[9]) {
+  // g of a local column from a staged row, given the staged positions of
+  // its left, own and right neighbour columns
+  auto staged_g = [&](const T* st, int pm, int p0, int pp, T G[9]) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) G[i] = st[i * SEG + c + 4 - cx_of(i)];
+    for (int i = 0; i < 9; ++i)
+      G[i] = st[i * SEG + (cx_of(i) == 1 ? pm : (cx_of(i) == -1 ? pp : p0))];
   };
 
   // phi and psi of local row k into the ring (row k must have landed)
@@ -183,12 +206,12 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
     const int s = (k + 4) & 3;
     T G[9];
     if (act) {
-      staged_g(st, tid, G);
+      staged_g(st, om, o0, op, G);
       const T phi = sum9(G);
       ring.put(s, tid + 1, phi, psi_of(phi, xi));
     }
     if (hthr) {
-      staged_g(st, hcol, G);
+      staged_g(st, hm, h0, hp, G);
       const T phi = sum9(G);
       ring.put(s, hslot, phi, psi_of(phi, xi));
     }
@@ -250,10 +273,11 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
     if (act) {
       const T* st = stage_of(k);
       T F[9], G[9];
-      staged_g(st, tid, G);
+      staged_g(st, om, o0, op, G);
       if (COUPLED) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) F[i] = st[(9 + i) * SEG + tid + 4 - cx_of(i)];
+        for (int i = 0; i < 9; ++i)
+          F[i] = st[(9 + i) * SEG + (cx_of(i) == 1 ? om : (cx_of(i) == -1 ? op : o0))];
       }
       T jpx = T(0), jpy = T(0);
       if (MODE == kModeStep) {
@@ -290,6 +314,16 @@ __global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
       a.vol_part[(int64_t)blockIdx.x * kMaxRegions] = v;
     }
   }
+}
+
+template <typename T, int BX, bool COUPLED, int MODE, int S>
+__global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
+    step_kernel_tma(const StepArgs<T> a) {
+  const Item it = a.items[blockIdx.x];
+  if (it.x0 == 0 && a.cases[it.c].nx <= BX)
+    tma_body<T, BX, COUPLED, MODE, S, true>(a);
+  else
+    tma_body<T, BX, COUPLED, MODE, S, false>(a);
 }
 
 }  // namespace lbmk

@@ -69,6 +69,37 @@ L_OK = 0
 VARIANTS = pytest.mark.parametrize("variant", [1, 2], ids=["regs", "tma"])
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_full_row_and_edge_strips_match_oracle(L, prec):
+    # Bulk-copy kernel, strips of 128 columns: rows no wider than a strip are
+    # staged whole and read their periodic neighbours from the same copy;
+    # wider rows split into strips whose edge strips copy the wrap columns.
+    # Widths 4 (the narrowest), 12, 100, 128 (one strip) and 132, 260 (a
+    # ragged last strip), several runs of rows each, 40 steps.
+    for nx in (4, 12, 100, 128, 132, 260):
+        ny = 26
+        case = W.base_case(nx, ny, rho_l=3.0, tau_f_l=0.8, tau_f_g=1.1)
+        phi0 = W.tanh_disc(nx, ny, 0.4 * nx, 11.0, min(0.3 * nx, 8.0), 3.0, periodic=True)
+        phi0 = phi0 + W.uniform(nx, phi0.shape, -1e-3, 1e-3)
+        u0 = np.zeros((2, ny, nx))
+        u0[0], u0[1] = 0.013, -0.007
+        o = oracle.Oracle(case, phi0, u0)
+        s = L.Sim(case, phi0, u0, precision=prec)
+        s.set_kernel(2)
+        s.set_tiling(128, 8)
+        o.step(40)
+        s.step(40)
+        if prec == "f64":
+            compare_full(o, s, TOL64, TOL64, TOL64, TOL64)
+        else:
+            phi, ux, uy, p = s.fields(0)
+            ophi, oux, ouy, op = o.fields()
+            assert maxdiff(phi, ophi) <= TOL32_PHI, nx
+            assert maxdiff(ux, oux) <= 1e-6 and maxdiff(uy, ouy) <= 1e-6, nx
+        assert s.status() == L.LBM_OK
+        s.close()
+
+
 @VARIANTS
 @pytest.mark.parametrize("lam", [0.5, 0.0])
 def test_two_droplets_fp64(L, lam, variant):
