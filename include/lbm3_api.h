@@ -116,9 +116,13 @@ int lbm3_set_state(lbm3_handle* h, const double* h_f, const double* h_g,
 int64_t lbm3_time(const lbm3_handle* h);
 
 /* Tiling of the step kernel: CTA tile bx x by columns, marching zc planes.
- * Allowed (bx, by): (32, 4), (32, 8), (32, 16), (64, 4); 8 <= zc <= nz (or
- * zc = nz when nz < 8).  Every tiling gives the same values up to
- * floating-point contraction (see lbm_set_tiling).  n_ctas: CTAs per step. */
+ * Allowed (bx, by): (32, 4), (32, 8), (32, 16), (64, 4) for variants 1-3;
+ * (128, 4) and (256, 2) -- whole rows, nx <= bx -- for variant 4.  Setting a
+ * tile that the variant in use does not run switches to the variant made
+ * for it (LBM_ERR_ARG if none runs it, or if a variant was requested with
+ * lbm3_set_kernel and does not run it).  8 <= zc <= nz (or zc = nz when
+ * nz < 8).  Every tiling gives the same values up to floating-point
+ * contraction (see lbm_set_tiling).  n_ctas: CTAs per step. */
 int lbm3_set_tiling(lbm3_handle* h, int32_t bx, int32_t by, int32_t zc);
 int lbm3_get_tiling(const lbm3_handle* h, int32_t* bx, int32_t* by, int32_t* zc,
                     int32_t* n_ctas);
@@ -127,8 +131,16 @@ int lbm3_get_tiling(const lbm3_handle* h, int32_t* bx, int32_t* by, int32_t* zc,
  * lbm3_autotune picks the fastest), 1 = register-pipelined loads (any
  * precision and tiling), 2 / 3 = asynchronous 4-byte copies (cp.async)
  * through shared memory, 2 / 3 stages deep (LBM3_F32 only; tiles (32, 4),
- * (32, 8), (64, 4)).  All variants run the same per-node arithmetic.
- * lbm3_get_kernel returns the variant in use (1, 2 or 3). */
+ * (32, 8), (64, 4)), 4 = bulk copies (cp.async.bulk) of whole x-rows into
+ * shared memory, one or two planes ahead (LBM3_F32 and LBM3_F16; nx <= 256,
+ * a row of nx stored values and of nx FP32 values a multiple of 16 bytes;
+ * tiles (128, 4) for nx <= 128, (256, 2); selecting it on another tile takes
+ * its own tile; other variants on a tile they do not run: LBM_ERR_ARG).
+ * All variants run the same per-node arithmetic.  Every
+ * wait of variant 4 is bounded: on expiry the step is abandoned and
+ * lbm3_status reports LBM_ERR_TIMEOUT.  lbm3_get_kernel returns the variant
+ * in use (1 to 4).  Errors: LBM_ERR_ARG (variant outside [0, 4], or not
+ * available for this precision or box). */
 int lbm3_set_kernel(lbm3_handle* h, int32_t variant);
 int32_t lbm3_get_kernel(const lbm3_handle* h);
 
@@ -141,7 +153,7 @@ int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* variant, int32_t* bx,
                   int32_t* by, int32_t* zc, double* best_ms);
 
 /* Synchronise and report device error flags (LBM_OK, LBM_ERR_NONFINITE,
- * LBM_ERR_CUDA); clears them. */
+ * LBM_ERR_TIMEOUT, LBM_ERR_CUDA); clears them. */
 int lbm3_status(lbm3_handle* h);
 
 void lbm3_destroy(lbm3_handle* h);

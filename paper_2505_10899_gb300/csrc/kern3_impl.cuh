@@ -4,6 +4,7 @@
 
 #include "launch3.h"
 #include "lbm3_async.cuh"
+#include "lbm3_bulk.cuh"
 #include "lbm3_kernels.cuh"
 
 namespace lbmk3 {
@@ -63,9 +64,35 @@ static cudaError_t launch_async(const Args3<float, float>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <typename T, typename S, int BX, int BY, int NST>
+static cudaError_t launch_bulk(const Args3<T, S>& a, cudaStream_t st) {
+  constexpr size_t bytes = bulk_smem_bytes<T, S, BX, BY, NST>();
+  static bool attr_set = false;  // per instantiation, per process (one device)
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(step3_bulk_kernel<T, S, BX, BY, NST>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (a.nx > BX) return cudaErrorInvalidValue;
+  const dim3 grid(1, (a.ny + BY - 1) / BY, (a.nz + a.zc - 1) / a.zc);
+  step3_bulk_kernel<T, S, BX, BY, NST><<<grid, BX * BY, bytes, st>>>(a, lbmk::kWaitCycles);
+  return cudaGetLastError();
+}
+
 template <typename T, typename S>
 static cudaError_t step_async(const Args3<T, S>& a, int variant, int bx, int by,
                               cudaStream_t st) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (variant == kVarBulk) {
+      // stages: FP16 rows are half the size, so three fit beside the ring
+      constexpr int NST = sizeof(S) == 2 ? 3 : 2;
+      if (bx == 256 && by == 2) return launch_bulk<T, S, 256, 2, NST>(a, st);
+      if (bx == 128 && by == 4) return launch_bulk<T, S, 128, 4, NST>(a, st);
+      return cudaErrorInvalidValue;
+    }
+  }
   if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value) {
     if (variant == kVarAsync2) {
       if (bx == 32 && by == 4) return launch_async<32, 4, 2>(a, st);

@@ -24,22 +24,32 @@ struct Host3 {
   double W;  // interface width (the threshold of the normal scales with it)
 };
 
-inline bool tile_ok(int bx, int by) {
+// Tiles of the register-pipelined and asynchronous-copy kernels.
+inline bool tile_regs_ok(int bx, int by) {
   return (bx == 32 && (by == 4 || by == 8 || by == 16)) || (bx == 64 && by == 4);
 }
+// Tiles of the bulk-copy kernel: whole x-rows, 128 x 4 or 256 x 2.
+inline bool tile_bulk_ok(int bx, int by) { return (bx == 128 && by == 4) || (bx == 256 && by == 2); }
+inline bool tile_ok(int bx, int by) { return tile_regs_ok(bx, by) || tile_bulk_ok(bx, by); }
 
 inline int64_t n_ctas(int nx, int ny, int nz, int bx, int by, int zc) {
   return (int64_t)((nx + bx - 1) / bx) * ((ny + by - 1) / by) * ((nz + zc - 1) / zc);
 }
 
-// Step-kernel variants: register-pipelined loads (any precision), or
-// asynchronous copies through shared memory with 2 or 3 stages (FP32 only).
-enum { kVarRegs = 1, kVarAsync2 = 2, kVarAsync3 = 3 };
+// Step-kernel variants: register-pipelined loads (any precision);
+// asynchronous copies through shared memory with 2 or 3 stages (FP32 only);
+// bulk copies of whole rows into shared memory (FP32 arithmetic, FP32 or
+// FP16 storage; rows of nx <= bx values, nx values a multiple of 16 bytes).
+enum { kVarRegs = 1, kVarAsync2 = 2, kVarAsync3 = 3, kVarBulk = 4 };
 
-inline bool variant_ok(int variant, int precision_is_f32, int bx, int by) {
-  if (variant == kVarRegs) return tile_ok(bx, by);
+// sbytes: bytes of a stored population (8 FP64, 4 FP32, 2 FP16).
+inline bool variant_ok(int variant, int sbytes, int bx, int by, int nx) {
+  if (variant == kVarRegs) return tile_regs_ok(bx, by);
   if (variant == kVarAsync2 || variant == kVarAsync3)
-    return precision_is_f32 && ((bx == 32 && (by == 4 || by == 8)) || (bx == 64 && by == 4));
+    return sbytes == 4 && ((bx == 32 && (by == 4 || by == 8)) || (bx == 64 && by == 4));
+  if (variant == kVarBulk)
+    return sbytes != 8 && tile_bulk_ok(bx, by) && nx <= bx && (nx * sbytes) % 16 == 0 &&
+           (nx * 4) % 16 == 0;
   return false;
 }
 

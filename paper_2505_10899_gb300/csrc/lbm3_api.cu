@@ -215,6 +215,7 @@ int read_flags(lbm3_handle* h) {
   int32_t fl = 0;
   L3_CUDA(cudaMemcpyAsync(&fl, h->flags, sizeof fl, cudaMemcpyDeviceToHost, h->stream));
   L3_CUDA(cudaStreamSynchronize(h->stream));
+  if (fl & lbmk3::kFlagTimeout3) return fail(LBM_ERR_TIMEOUT, "a bounded device wait timed out");
   if (fl & lbmk3::kFlagNonFinite) return fail(LBM_ERR_NONFINITE, "non-finite value in the fields");
   return LBM_OK;
 }
@@ -419,23 +420,37 @@ int lbm3_set_tiling(lbm3_handle* h, int32_t bx, int32_t by, int32_t zc) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
   if (!lbmk3::tile_ok(bx, by)) return fail(LBM_ERR_ARG, "unsupported (bx, by)");
   if (zc < zc_min(h->prm) || zc > h->prm.nz) return fail(LBM_ERR_ARG, "zc out of range");
-  const int f32 = h->prm.precision == LBM3_F32;
-  if (h->variant_req && !lbmk3::variant_ok(h->variant_req, f32, bx, by))
+  const int sb = (int)selem(h->prm.precision), nx = h->prm.nx;
+  if (h->variant_req && !lbmk3::variant_ok(h->variant_req, sb, bx, by, nx))
     return fail(LBM_ERR_ARG, "tiling not available for the requested kernel variant");
+  // keep the variant in use if it runs this tile, else the one made for it
+  int v = h->variant;
+  if (!lbmk3::variant_ok(v, sb, bx, by, nx))
+    v = lbmk3::tile_bulk_ok(bx, by) ? lbmk3::kVarBulk : lbmk3::kVarRegs;
+  if (!lbmk3::variant_ok(v, sb, bx, by, nx))
+    return fail(LBM_ERR_ARG, "tiling not available for this box or precision");
   h->bx = bx, h->by = by, h->zc = zc;
-  if (!lbmk3::variant_ok(h->variant, f32, bx, by)) h->variant = lbmk3::kVarRegs;
+  h->variant = v;
   drop_graph(h);
   return LBM_OK;
 }
 
 int lbm3_set_kernel(lbm3_handle* h, int32_t variant) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
-  if (variant < 0 || variant > lbmk3::kVarAsync3) return fail(LBM_ERR_ARG, "variant in [0, 3]");
-  const int f32 = h->prm.precision == LBM3_F32;
-  if (variant && !lbmk3::variant_ok(variant, f32, h->bx, h->by))
-    return fail(LBM_ERR_ARG, "variant not available for this precision or tiling");
+  if (variant < 0 || variant > lbmk3::kVarBulk) return fail(LBM_ERR_ARG, "variant in [0, 4]");
+  const int sb = (int)selem(h->prm.precision), nx = h->prm.nx;
+  int bx = h->bx, by = h->by;
+  const int v = variant ? variant : lbmk3::kVarRegs;
+  if (v == lbmk3::kVarBulk && !lbmk3::tile_bulk_ok(bx, by)) {
+    // the bulk-copy kernel runs its own tiles only: take the one for nx
+    bx = nx <= 128 ? 128 : 256;
+    by = nx <= 128 ? 4 : 2;
+  }
+  if (!lbmk3::variant_ok(v, sb, bx, by, nx))
+    return fail(LBM_ERR_ARG, "variant not available for this precision or box");
   h->variant_req = variant;
-  h->variant = variant ? variant : lbmk3::kVarRegs;
+  h->variant = v;
+  h->bx = bx, h->by = by;
   drop_graph(h);
   return LBM_OK;
 }
@@ -453,16 +468,16 @@ int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* ovar, int32_t* obx, i
     cudaEventDestroy(e0);
     return fail(LBM_ERR_CUDA, "event create failed");
   }
-  const int f32 = h->prm.precision == LBM3_F32;
+  const int sb = (int)selem(h->prm.precision), nx = h->prm.nx;
   const int kv = h->variant, kb = h->bx, kby = h->by, kz = h->zc;
   double best = 1e300;
   int bv = kv, bb = kb, bby = kby, bz = kz;
   int rc = LBM_OK;
-  const int tiles[4][2] = {{32, 4}, {32, 8}, {32, 16}, {64, 4}};
-  for (int v = lbmk3::kVarRegs; v <= lbmk3::kVarAsync3 && rc == LBM_OK; ++v) {
+  const int tiles[6][2] = {{32, 4}, {32, 8}, {32, 16}, {64, 4}, {128, 4}, {256, 2}};
+  for (int v = lbmk3::kVarRegs; v <= lbmk3::kVarBulk && rc == LBM_OK; ++v) {
     if (h->variant_req && v != h->variant_req) continue;
     for (const auto& tl : tiles) {
-      if (!lbmk3::variant_ok(v, f32, tl[0], tl[1])) continue;
+      if (!lbmk3::variant_ok(v, sb, tl[0], tl[1], nx)) continue;
       for (int zc : {8, 16, 32, 64}) {
         const int z = std::min(std::max(zc, zc_min(h->prm)), h->prm.nz);
         if (zc > 8 && z != zc) continue;  // nz too small for this zc
@@ -509,6 +524,7 @@ int lbm3_status(lbm3_handle* h) {
   int32_t fl = 0;
   L3_CUDA(cudaMemcpy(&fl, h->flags, sizeof fl, cudaMemcpyDeviceToHost));
   L3_CUDA(cudaMemset(h->flags, 0, sizeof fl));
+  if (fl & lbmk3::kFlagTimeout3) return fail(LBM_ERR_TIMEOUT, "a bounded device wait timed out");
   if (fl & lbmk3::kFlagNonFinite) return fail(LBM_ERR_NONFINITE, "non-finite value in the fields");
   return LBM_OK;
 }

@@ -26,7 +26,7 @@ constexpr int kMaxRegions = 8;
 // Weights: D3Q19 1/3, 1/18, 1/36 (c_s^2 = 1/3); D3Q7 1/4, 1/8 (c_s^2 = 1/4).
 
 enum { kModeStep = 0, kModeFields = 1 };
-enum { kFlagNonFinite = 1 };
+enum { kFlagNonFinite = 1, kFlagTimeout3 = 2 };  // device error flags (bits)
 enum { kOutPhi = 0, kOutUx = 1, kOutUy = 2, kOutUz = 3, kOutP = 4 };
 
 // Launch arguments.  T is the arithmetic type, S the storage type.

@@ -138,6 +138,55 @@ def test_fp32_async_copy_variants(L3, variant, tiling):
     assert a.status() == 0
 
 
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("shape,tiling", [((40, 21, 20), (128, 4, 8)),
+                                          ((200, 7, 15), (256, 2, 13)),
+                                          ((8, 3, 5), (128, 4, 5))])
+def test_bulk_row_variant(L3, prec, shape, tiling):
+    # Whole-row bulk copies (variant 4): the same per-node arithmetic as the
+    # register kernel, so equal to it up to FMA contraction, and within the
+    # precision's bar of the oracle; ragged row blocks and z chunks, and a
+    # box thinner than the rows a CTA touches (ny = 3 < 4 + 2, nz = 5).
+    nx, ny, nz = shape
+    case, phi0, u0 = two_phase(nx, ny, nz, rho_l=3.0, tau_f_l=0.7)
+    a = L3.Sim3(case, phi0, u0, precision=prec)
+    a.set_tiling(*tiling)
+    assert a.kernel() == 4  # the tile selects the variant made for it
+    b = L3.Sim3(case, phi0, u0, precision=prec)
+    b.set_kernel(1)
+    tr = a.track_volume(True)
+    a.step(100)
+    b.step(100)
+    assert a.status() == 0 and b.status() == 0
+    fa, fb = a.get_state(), b.get_state()
+    tol = 2e-6 if prec == "f32" else 2e-3
+    for x, y in zip(fa[:3], fb[:3]):
+        assert md(x, y) <= tol
+    o = oracle.Oracle3(case, phi0, u0).step(99)
+    # tracked: the volume of the state entering the last step
+    assert abs(float(tr.cpu().numpy()[0]) / o.volume()[0] - 1) < (1e-6 if prec == "f32" else 1e-5)
+    o.step(1)
+    assert md(a.fields()[0], o.fields()[0]) <= (1e-5 if prec == "f32" else 2e-3)
+
+
+def test_bulk_row_variant_rejected_where_unavailable(L3):
+    case, phi0, u0 = two_phase(40, 24, 20)
+    s = L3.Sim3(case, phi0, u0, precision="f64")
+    with pytest.raises(L3.LbmError):
+        s.set_kernel(4)
+    with pytest.raises(L3.LbmError):
+        s.set_tiling(128, 4, 8)
+    case, phi0, u0 = two_phase(44, 8, 8)  # FP16 rows of 88 bytes: not 16-byte multiples
+    t = L3.Sim3(case, phi0, u0, precision="f16")
+    with pytest.raises(L3.LbmError):
+        t.set_kernel(4)
+    case, phi0, u0 = two_phase(264, 4, 8)  # rows longer than 256
+    t = L3.Sim3(case, phi0, u0, precision="f32")
+    with pytest.raises(L3.LbmError):
+        t.set_kernel(4)
+    t.set_kernel(0)
+
+
 def test_async_variant_rejected_where_unavailable(L3):
     case, phi0, u0 = two_phase(40, 24, 20)
     s = L3.Sim3(case, phi0, u0, precision="f64")
