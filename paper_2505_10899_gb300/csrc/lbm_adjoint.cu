@@ -48,46 +48,63 @@ constexpr int kAdBlocks = 152 * 8;
 // u_wall_top, u_wall_bottom
 constexpr int kNParam = 7;
 
-__device__ __constant__ int kAX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-__device__ __constant__ int kAY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-__device__ __constant__ double kAW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
-                                         1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-__device__ __constant__ int kAOPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+// D2Q9 (Eq. 19): components, weights and opposite directions as
+// compile-time functions of i (constants once the loops over i unroll; a
+// __constant__ table would cost a load per use).
+__host__ __device__ constexpr int kAX(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int kAY(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__host__ __device__ constexpr double kAW(int i) {
+  return i == 0 ? 4.0 / 9 : (i < 5 ? 1.0 / 9 : 1.0 / 36);
+}
+__host__ __device__ constexpr int kAOPP(int i) {
+  return i == 0 ? 0 : (i < 5 ? (i + 1) % 4 + 1 : (i - 5 + 2) % 4 + 5);
+}
+static_assert(kAOPP(1) == 3 && kAOPP(2) == 4 && kAOPP(3) == 1 && kAOPP(4) == 2 &&
+                  kAOPP(5) == 7 && kAOPP(6) == 8 && kAOPP(7) == 5 && kAOPP(8) == 6,
+              "opposite directions");
+static_assert(kAX(5) == 1 && kAY(5) == 1 && kAX(6) == -1 && kAY(6) == 1 && kAX(7) == -1 &&
+                  kAY(7) == -1 && kAX(8) == 1 && kAY(8) == -1,
+              "diagonal directions");
 
 int fail(int code, const std::string& m) { return lbmk::set_last_error(code, m.c_str()); }
 
-__device__ __forceinline__ int64_t shift(int x, int y, int dx, int dy, int nx, int ny) {
+// In-plane offsets are 32-bit: a case has at most 2.3e8 nodes.
+__device__ __forceinline__ int shift(int x, int y, int dx, int dy, int nx, int ny) {
   x += dx;
   y += dy;
   x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
   y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
-  return (int64_t)y * nx + x;
+  return y * nx + x;
 }
 
 // Buffer position of the value population i delivers to node (x, y): the
 // pull source, or with walls the node's own opposite population for a
 // population that would come from beyond a wall (halfway bounce-back).
-__device__ __forceinline__ int64_t ad_src(int i, int x, int y, int nx, int ny, int walls,
+__device__ __forceinline__ int ad_src(int i, int x, int y, int nx, int ny, int walls,
                                           int* pl) {
-  const int ys = y - kAY[i];
+  const int ys = y - kAY(i);
   if (walls && (ys < 0 || ys >= ny)) {
-    *pl = kAOPP[i];
-    return (int64_t)y * nx + x;
+    *pl = kAOPP(i);
+    return y * nx + x;
   }
   *pl = i;
-  return shift(x, y, -kAX[i], -kAY[i], nx, ny);
+  return shift(x, y, -kAX(i), -kAY(i), nx, ny);
 }
 
 // Stencil neighbour (x + dx, y + dy): periodic, or with walls the mirrored
 // ghost row beyond a wall row.
-__device__ __forceinline__ int64_t ad_nb(int x, int y, int dx, int dy, int nx, int ny,
+__device__ __forceinline__ int ad_nb(int x, int y, int dx, int dy, int nx, int ny,
                                          int walls) {
   if (!walls) return shift(x, y, dx, dy, nx, ny);
   x += dx;
   x = x < 0 ? x + nx : (x >= nx ? x - nx : x);
   y += dy;
   y = y < 0 ? 0 : (y >= ny ? ny - 1 : y);
-  return (int64_t)y * nx + x;
+  return y * nx + x;
 }
 
 // Adjoint of phi (lP, [9][n]) and psi (lQ, [8][n]) stencil uses gathered at
@@ -99,18 +116,19 @@ __device__ __forceinline__ void gather_uses(const R* __restrict__ lP, const R* _
                                             int x, int y, int nx, int ny, int walls, R& sp,
                                             R& sq) {
   const int64_t n = (int64_t)nx * ny;
+  #pragma unroll
   for (int j = 1; j < 9; ++j) {
-    const int ys = y - kAY[j];
+    const int ys = y - kAY(j);
     if (!walls || (ys >= 0 && ys < ny)) {
-      const int64_t s = shift(x, y, -kAX[j], -kAY[j], nx, ny);
+      const int s = shift(x, y, -kAX(j), -kAY(j), nx, ny);
       sp += lP[j * n + s];
       if (lQ) sq += lQ[(j - 1) * n + s];
     }
     // a wall row reads its own row through the ghost row beyond the wall
-    if (walls && ((y == 0 && kAY[j] == -1) || (y == ny - 1 && kAY[j] == 1))) {
-      int xs = x - kAX[j];
+    if (walls && ((y == 0 && kAY(j) == -1) || (y == ny - 1 && kAY(j) == 1))) {
+      int xs = x - kAX(j);
       xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-      const int64_t s = (int64_t)y * nx + xs;
+      const int s = y * nx + xs;
       sp += lP[j * n + s];
       if (lQ) sq += lQ[(j - 1) * n + s];
     }
@@ -154,13 +172,13 @@ template <typename R>
 __global__ void ad_phase(const R* __restrict__ gA, int64_t P, int nx, int ny, int walls, R xi,
                          R* __restrict__ phi, R* __restrict__ psi) {
   const int64_t n = (int64_t)nx * ny;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % nx), y = (int)(k / nx);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)n; k += gridDim.x * blockDim.x) {
+    const int y = k / nx, x = k - y * nx;
     R G[9];
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       int pl;
-      const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
+      const int pos = ad_src(i, x, y, nx, ny, walls, &pl);
       G[i] = gA[pl * P + pos];
     }
     const R p = lbmk::sum9(G);
@@ -202,12 +220,12 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
   const int64_t n = (int64_t)nx * ny, P = a.P;
   const Phys<R>& ph = a.ph;
   double gacc[kNParam] = {0, 0, 0, 0, 0, 0, 0};
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % nx), y = (int)(k / nx);
-    int64_t src[9];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)n; k += gridDim.x * blockDim.x) {
+    const int y = k / nx, x = k - y * nx;
+    int src[9];
     int spl[9];
     R F[9], G[9];
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       src[i] = ad_src(i, x, y, nx, ny, a.walls, &spl[i]);
       G[i] = a.gA[spl[i] * P + src[i]];
@@ -215,8 +233,9 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     }
     const R jpx = a.JA[k], jpy = a.JA[P + k];
     R Pv[9], Qv[9];
+    #pragma unroll
     for (int j = 0; j < 9; ++j) {
-      const int64_t s = ad_nb(x, y, kAX[j], kAY[j], nx, ny, a.walls);
+      const int s = ad_nb(x, y, kAX(j), kAY(j), nx, ny, a.walls);
       Pv[j] = a.phi[s];
       Qv[j] = a.psi[s];
     }
@@ -224,13 +243,15 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     const bool wbot = a.walls && y == 0, wtop = a.walls && y == ny - 1;
     if (a.coupled && (wbot || wtop)) {
       const R rw = a.rho_g + Pv[0] * a.drho;
-      if (wbot) {
-        F[5] += rw * a.u_bot / R(6);
-        F[6] -= rw * a.u_bot / R(6);
+      if (wbot) {  // as the forward step forms it
+        const R d = rw * a.u_bot * R(1.0 / 6.0);
+        F[5] += d;
+        F[6] -= d;
       }
       if (wtop) {
-        F[7] -= rw * a.u_top / R(6);
-        F[8] += rw * a.u_top / R(6);
+        const R d = rw * a.u_top * R(1.0 / 6.0);
+        F[7] -= d;
+        F[8] += d;
       }
     }
     // ---------------- forward recompute (as node_update) ----------------
@@ -250,7 +271,7 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     Mom<R> mf{};
     if (a.coupled) {
       rho = a.rho_g + phi * a.drho;
-      irho = R(1) / rho;
+      irho = N::rcp(rho);  // the reciprocal the forward step takes
       mf = lbmk::moments(F);
       ux = (mf.m3 + R(0.5) * Fx) * irho;
       uy = (mf.m5 + R(0.5) * Fy) * irho;
@@ -260,7 +281,7 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
       if (a.var_tau) {
         mu_v = a.mu_g + phi * a.dmu;
         const R tau = R(3) * mu_v * irho + R(0.5);
-        s7 = R(1) / tau;
+        s7 = N::rcp(tau);
         sD7 = R(-0.25) * s7;
         hD7 = R(0.25) - R(0.125) * s7;
       }
@@ -276,13 +297,14 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     const R pc = N::clamp01(phi);
     const R ta = pc + ph.xi, tb = (R(1) - pc) + ph.xi;
     const R q2 = qx * qx + qy * qy;
-    const R iq = (q2 >= ph.qmin2) ? R(1) / sqrt(q2) : R(0);
+    const R iq = (q2 >= ph.qmin2) ? N::rsq(q2) : R(0);
     const R sh = ph.lamW * ph.tfac * ta * tb * iq;
     const R Vx = R(3) * dJx + sh * qx, Vy = R(3) * dJy + sh * qy;
     const Mom<R> mg = lbmk::moments(G);
 
     // ---------------- reverse ----------------
     R aF[9], aG[9];
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       aF[i] = a.ain[i * n + k];
       aG[i] = a.ain[(9 + i) * n + k];
@@ -295,8 +317,10 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     lphi += aG[0];
     R aGp[9];
     aGp[0] = R(0);
+    #pragma unroll
     for (int i = 1; i < 9; ++i) aGp[i] = aG[i] - aG[0];
     R lG[9];
+    #pragma unroll
     for (int i = 0; i < 9; ++i) lG[i] = aGp[i];
     const Mom<R> le = lbmk::moments(aGp);  // lambda_e = M lambda_g*'
     R lmg[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -326,7 +350,7 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     {  // tau_g: s3 = s5 = 1/tau_g; gsD = -s/6, ghD3 = (1 - s/2)/18
       const R lgs = (mg.m3 - Jx) * le.m3 + (mg.m5 - Jy) * le.m5;
       const R lgh = Vx * le.m3 + Vy * le.m5;
-      const R ls = -lgs / R(6) - lgh / R(36);
+      const R ls = -lgs * R(1.0 / 6.0) - lgh * R(1.0 / 36.0);
       const R sg = R(-6) * ph.gsD[3];  // = 1/tau_g
       gacc[3] += (double)(-sg * sg * ls);
     }
@@ -361,8 +385,10 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     luy += phi * lJy;
 
     R lF[9];
+    #pragma unroll
     for (int i = 0; i < 9; ++i) lF[i] = R(0);
     if (a.coupled) {
+      #pragma unroll
       for (int i = 0; i < 9; ++i) lF[i] = aF[i];
       const Mom<R> ld = lbmk::moments(aF);  // lambda_d = M lambda_f*
       R lm[9] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
@@ -451,12 +477,12 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
       lbmk::add_back(lF, lm[0], lm[1], lm[2], lm[3], lm[4], lm[5], lm[6], lm[7], lm[8]);
       // moving-wall term: F_i += rho c_ix u_w / 6, rho = rho_g + phi drho
       if (wbot) {
-        const R l = (lF[5] - lF[6]) / R(6);
+        const R l = (lF[5] - lF[6]) * R(1.0 / 6.0);
         lrho += a.u_bot * l;
         gacc[6] += (double)(rho * l);
       }
       if (wtop) {
-        const R l = (lF[8] - lF[7]) / R(6);
+        const R l = (lF[8] - lF[7]) * R(1.0 / 6.0);
         lrho += a.u_top * l;
         gacc[5] += (double)(rho * l);
       }
@@ -475,8 +501,9 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     gacc[1] += (double)(-lap * lmu);
 
     // stencil adjoints (transpose of the difference forms above)
-    const R gx3 = lgpx / R(3), gy3 = lgpy / R(3), gx12 = lgpx / R(12), gy12 = lgpy / R(12);
-    const R la = R(2.0 / 3.0) * llap, ld6 = llap / R(6);
+    const R gx3 = lgpx * R(1.0 / 3.0), gy3 = lgpy * R(1.0 / 3.0);
+    const R gx12 = lgpx * R(1.0 / 12.0), gy12 = lgpy * R(1.0 / 12.0);
+    const R la = R(2.0 / 3.0) * llap, ld6 = llap * R(1.0 / 6.0);
     a.lP[0 * n + k] = R(-10.0 / 3.0) * llap + lphi;
     a.lP[1 * n + k] = gx3 + la;
     a.lP[3 * n + k] = -gx3 + la;
@@ -497,6 +524,7 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
 
     // transpose of the pull: adjoint of the source positions (a bijection,
     // walls included)
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       a.aout[spl[i] * n + src[i]] = lF[i];
       a.aout[(9 + spl[i]) * n + src[i]] = lG[i];
@@ -518,18 +546,18 @@ __global__ void ad_gather(R* __restrict__ phi, R* __restrict__ psi, const R* __r
                           const R* __restrict__ lQ, int nx, int ny, int walls, R xi,
                           R* __restrict__ aout, const R* __restrict__ gB, int64_t PB) {
   const int64_t n = (int64_t)nx * ny;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % nx), y = (int)(k / nx);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)n; k += gridDim.x * blockDim.x) {
+    const int y = k / nx, x = k - y * nx;
     R sp = lP[k], sq = R(0);
     gather_uses(lP, lQ, x, y, nx, ny, walls, sp, sq);
     const R p = phi[k];
     const R dpsi = (p > R(0) && p < R(1)) ? dpsi_dphi(p, xi) : R(0);
     const R tot = sp + dpsi * sq;
     R G[9];
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       int pl;
-      const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
+      const int pos = ad_src(i, x, y, nx, ny, walls, &pl);
       aout[(9 + pl) * n + pos] += tot;
       if (gB) G[i] = gB[pl * PB + pos];
     }
@@ -569,13 +597,13 @@ __global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs<R> 
   const int64_t n = (int64_t)nx * ny;
   const Phys<double>& ph = a.ph;
   double gacc[kNParam] = {0, 0, 0, 0, 0, 0, 0};
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % nx), y = (int)(k / nx);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)n; k += gridDim.x * blockDim.x) {
+    const int y = k / nx, x = k - y * nx;
     const double p = a.phi0[k];
     double s_ax = 0.0, s_dg = 0.0;
+    #pragma unroll
     for (int j = 1; j < 9; ++j) {
-      const double v = a.phi0[ad_nb(x, y, kAX[j], kAY[j], nx, ny, a.walls)];
+      const double v = a.phi0[ad_nb(x, y, kAX(j), kAY(j), nx, ny, a.walls)];
       if (j < 5) s_ax += v; else s_dg += v;
     }
     const double lap = (2.0 / 3.0) * (s_ax - 4.0 * p) + (1.0 / 6.0) * (s_dg - 4.0 * p);
@@ -594,29 +622,30 @@ __global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs<R> 
     double lLam = 0.0, lphi = 0.0, lJx = a.ain[18 * n + k], lJy = a.ain[19 * n + k], lrho = 0.0;
     const double u2 = ux * ux + uy * uy;
     const double rho = a.rho_g + p * a.drho;
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       int pl;
-      const int64_t s = ad_src(i, x, y, nx, ny, a.walls, &pl);
+      const int s = ad_src(i, x, y, nx, ny, a.walls, &pl);
       const double lg = a.ain[(9 + pl) * n + s];
       if (i == 0) {
         lphi += lg;
-        lLam += (kAW[0] - 1.0) * lg;
+        lLam += (kAW(0) - 1.0) * lg;
       } else {
-        lLam += kAW[i] * lg;
-        lJx += 3.0 * kAW[i] * kAX[i] * lg;
-        lJy += 3.0 * kAW[i] * kAY[i] * lg;
+        lLam += kAW(i) * lg;
+        lJx += 3.0 * kAW(i) * kAX(i) * lg;
+        lJy += 3.0 * kAW(i) * kAY(i) * lg;
       }
       if (a.coupled) {
-        const double cu = kAX[i] * ux + kAY[i] * uy;
+        const double cu = kAX(i) * ux + kAY(i) * uy;
         const double lf = a.ain[pl * n + s];
-        lrho += kAW[i] * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2) * lf;
+        lrho += kAW(i) * (3.0 * cu + 4.5 * cu * cu - 1.5 * u2) * lf;
         // the stored f of a population entering from a wall is f_eq minus the
         // moving-wall term rho c_ix u_w / 6 (added back when it is pulled)
-        if (a.walls && ((y == 0 && kAY[i] == 1) || (y == ny - 1 && kAY[i] == -1))) {
-          const bool bot = y == 0 && kAY[i] == 1;
+        if (a.walls && ((y == 0 && kAY(i) == 1) || (y == ny - 1 && kAY(i) == -1))) {
+          const bool bot = y == 0 && kAY(i) == 1;
           const double uw = bot ? a.u_bot : a.u_top;
-          lrho += -kAX[i] * uw / 6.0 * lf;
-          gacc[bot ? 6 : 5] += -rho * kAX[i] / 6.0 * lf;
+          lrho += -kAX(i) * uw / 6.0 * lf;
+          gacc[bot ? 6 : 5] += -rho * kAX(i) / 6.0 * lf;
         }
       }
     }
@@ -638,18 +667,18 @@ __global__ void __launch_bounds__(kAdThreads) ad_init_local(const AdInitArgs<R> 
 __global__ void ad_init_gather(const double* __restrict__ lphi, const double* __restrict__ llap,
                                int nx, int ny, int walls, double* __restrict__ out) {
   const int64_t n = (int64_t)nx * ny;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % nx), y = (int)(k / nx);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)n; k += gridDim.x * blockDim.x) {
+    const int y = k / nx, x = k - y * nx;
     double v = lphi[k] - (10.0 / 3.0) * llap[k];
+    #pragma unroll
     for (int j = 1; j < 9; ++j) {
       const double w = j < 5 ? 2.0 / 3.0 : 1.0 / 6.0;
-      const int ys = y - kAY[j];
-      if (!walls || (ys >= 0 && ys < ny)) v += w * llap[shift(x, y, -kAX[j], -kAY[j], nx, ny)];
-      if (walls && ((y == 0 && kAY[j] == -1) || (y == ny - 1 && kAY[j] == 1))) {
-        int xs = x - kAX[j];
+      const int ys = y - kAY(j);
+      if (!walls || (ys >= 0 && ys < ny)) v += w * llap[shift(x, y, -kAX(j), -kAY(j), nx, ny)];
+      if (walls && ((y == 0 && kAY(j) == -1) || (y == ny - 1 && kAY(j) == 1))) {
+        int xs = x - kAX(j);
         xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
-        v += w * llap[(int64_t)y * nx + xs];
+        v += w * llap[y * nx + xs];
       }
     }
     out[k] = v;
@@ -663,12 +692,12 @@ template <typename R>
 __global__ void ad_seed_phi(const double* __restrict__ dphi, int nx, int ny, int walls,
                             R* __restrict__ aout) {
   const int64_t n = (int64_t)nx * ny;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
-       k += (int64_t)gridDim.x * blockDim.x) {
-    const int x = (int)(k % nx), y = (int)(k / nx);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)n; k += gridDim.x * blockDim.x) {
+    const int y = k / nx, x = k - y * nx;
+    #pragma unroll
     for (int i = 0; i < 9; ++i) {
       int pl;
-      const int64_t pos = ad_src(i, x, y, nx, ny, walls, &pl);
+      const int pos = ad_src(i, x, y, nx, ny, walls, &pl);
       aout[(9 + pl) * n + pos] = (R)dphi[k];
     }
   }
