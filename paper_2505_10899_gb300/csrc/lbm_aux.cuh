@@ -110,7 +110,8 @@ __device__ __forceinline__ void init_node(const CaseDev<T>& cd, int x, int y, do
     const R cu = R(kCX[i]) * ux + R(kCY[i]) * uy;
     const R cJ = R(kCX[i]) * Jx + R(kCY[i]) * Jy;
     int pl;
-    const int64_t dst = pull_loc(i, x, y, nx, ny, cd.walls, &pl) + (int64_t)pl * cd.plane;
+    const int64_t pos = pull_loc(i, x, y, nx, ny, cd.walls, &pl);  // sets pl
+    const int64_t dst = pos + (int64_t)pl * cd.plane;
     if (i == 0) {
       dst0 = dst;
       if (sizeof(R) == 8) gb[dst] = (T)(p + (w - R(1)) * lam);
