@@ -158,10 +158,27 @@ int lbm_prepare_steps(lbm_handle* h, int64_t nsteps);
  * are captured as a separate branch of the step graph, so that while the
  * last CTAs of one group's step drain, the other group's CTAs keep the SMs
  * busy; the groups are independent, so the results do not change.  Within
- * a group the largest cases are scheduled first.  lbm_set_chains rebuilds
- * the work-item table (synchronises).  Errors: LBM_ERR_ARG. */
+ * a group the largest cases are scheduled first.
+ * lbm_get_chains returns the number of chains in use (up to 8 with
+ * whole-row chains, below).  lbm_set_chains rebuilds the work-item table
+ * (synchronises).  Errors: LBM_ERR_ARG. */
 int lbm_set_chains(lbm_handle* h, int32_t nchains);
 int32_t lbm_get_chains(const lbm_handle* h);
+
+/* Whole-row chains (on = 1; off by default; lbm_autotune tries both): with
+ * the bulk-copy kernel in FP32 and strips of 128 columns, a case whose row
+ * fits a width of 64, 96, 192 or 256 columns (the smallest that holds it,
+ * 128 included, decides) runs each row as one strip of that width, in one
+ * extra chain per width.  A whole-row strip copies its row once per plane and
+ * needs no periodic-wrap pieces, so batches of such cases step faster (192-
+ * wide cases: 0.81 of the HBM roofline instead of 0.69 with 128-column
+ * strips); in a batch that mixes them with wide cases the chains of different
+ * widths share the SMs less well.  The other cases form the nchains groups.
+ * Results are those of any tiling (see lbm_set_tiling).  lbm_get_row_chains
+ * reports whether they are in use (1) or not (0).  Rebuilds the work-item
+ * table (synchronises).  Errors: LBM_ERR_ARG. */
+int lbm_set_row_chains(lbm_handle* h, int32_t on);
+int32_t lbm_get_row_chains(const lbm_handle* h);
 
 /* Bound of the device waits, in SM clock cycles: the bulk-copy kernel's
  * waits for its staged rows and the persistent kernel's grid barrier.  A
@@ -213,7 +230,8 @@ int lbm_track_volume(lbm_handle* h, double* d_out);
 int lbm_track_volume_history(lbm_handle* h, double* out, int64_t nslots);
 
 /* Work tiling of the step kernel: each CTA owns a strip of bx columns
- * (bx in {32, 64, 128}) and marches down runs of `rows` rows (2..1024).
+ * (bx in {32, 64, 128}; whole-row chains, see lbm_set_chains, take their own
+ * width) and marches down runs of `rows` rows (2..1024).
  * lbm_init picks a default from the batch size; lbm_set_tiling replaces it
  * (results agree for every tiling up to floating-point rounding: the
  * per-node operations are the same, but different kernel instantiations
@@ -238,7 +256,9 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel,
  * grid), 2 = bulk-copy (TMA) staged loads through shared memory (needs every
  * case to have nx >= 4 and nx a multiple of 4 in FP32, of 2 in FP64).  Both
  * run the same per-node arithmetic (equal up to rounding, see
- * lbm_set_tiling).  lbm_get_kernel returns the variant in use (1 or 2). */
+ * lbm_set_tiling).  lbm_get_kernel returns the variant in use (1 or 2).
+ * Changing the variant rebuilds the work-item table (whole-row chains run
+ * the bulk-copy kernel only; synchronises). */
 int lbm_set_kernel(lbm_handle* h, int32_t variant);
 int32_t lbm_get_kernel(const lbm_handle* h);
 

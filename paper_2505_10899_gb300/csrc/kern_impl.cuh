@@ -57,6 +57,9 @@ cudaError_t step_bx(const StepArgs<LBM_T>& a, bool coupled, int mode, bool tma, 
     return mode == kModeStep ? step_tma<BX, false, kModeStep>(a, n, s)
                              : step_tma<BX, false, kModeFields>(a, n, s);
   }
+  if constexpr (BX != 32 && BX != 64 && BX != 128) {
+    return cudaErrorInvalidValue;  // whole-row widths: bulk-copy kernel only
+  } else {
   if (coupled) {
     if (mode == kModeStep)
       step_kernel<LBM_T, BX, true, kModeStep><<<n, BX, 0, s>>>(a);
@@ -69,6 +72,7 @@ cudaError_t step_bx(const StepArgs<LBM_T>& a, bool coupled, int mode, bool tma, 
       step_kernel<LBM_T, BX, false, kModeFields><<<n, BX, 0, s>>>(a);
   }
   return cudaGetLastError();
+  }
 }
 }  // namespace
 
@@ -80,6 +84,9 @@ cudaError_t launch_step<LBM_T>(const StepArgs<LBM_T>& a, int bx, bool coupled, i
     case 32: return step_bx<32>(a, coupled, mode, tma, n_items, s);
     case 64: return step_bx<64>(a, coupled, mode, tma, n_items, s);
     case 128: return step_bx<128>(a, coupled, mode, tma, n_items, s);
+    case 96: return step_bx<96>(a, coupled, mode, tma, n_items, s);
+    case 192: return step_bx<192>(a, coupled, mode, tma, n_items, s);
+    case 256: return step_bx<256>(a, coupled, mode, tma, n_items, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -123,6 +130,9 @@ cudaError_t prepare_tma<LBM_T>() {
   cudaError_t e;
   if ((e = prep_bx<32>()) != cudaSuccess) return e;
   if ((e = prep_bx<64>()) != cudaSuccess) return e;
+  if ((e = prep_bx<96>()) != cudaSuccess) return e;
+  if ((e = prep_bx<192>()) != cudaSuccess) return e;
+  if ((e = prep_bx<256>()) != cudaSuccess) return e;
   return prep_bx<128>();
 }
 
@@ -141,6 +151,9 @@ size_t tma_smem_bytes<LBM_T>(int bx, bool coupled, int mode) {
     case 32: return pick(std::integral_constant<int, 32>{});
     case 64: return pick(std::integral_constant<int, 64>{});
     case 128: return pick(std::integral_constant<int, 128>{});
+    case 96: return pick(std::integral_constant<int, 96>{});
+    case 192: return pick(std::integral_constant<int, 192>{});
+    case 256: return pick(std::integral_constant<int, 256>{});
     default: return 0;
   }
 }
@@ -160,9 +173,24 @@ cudaError_t launch_init_items<LBM_T>(const CaseDev<LBM_T>* cases, const Item* it
       init_items<LBM_T, 64><<<n_items, 64, 0, s>>>(cases, items, src, beta4, kappa, lambda,
                                                     vortex, vU, parity);
       break;
-    default:
+    case 96:
+      init_items<LBM_T, 96><<<n_items, 96, 0, s>>>(cases, items, src, beta4, kappa, lambda,
+                                                    vortex, vU, parity);
+      break;
+    case 128:
       init_items<LBM_T, 128><<<n_items, 128, 0, s>>>(cases, items, src, beta4, kappa, lambda,
                                                       vortex, vU, parity);
+      break;
+    case 192:
+      init_items<LBM_T, 192><<<n_items, 192, 0, s>>>(cases, items, src, beta4, kappa, lambda,
+                                                      vortex, vU, parity);
+      break;
+    case 256:
+      init_items<LBM_T, 256><<<n_items, 256, 0, s>>>(cases, items, src, beta4, kappa, lambda,
+                                                      vortex, vU, parity);
+      break;
+    default:
+      return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
@@ -227,32 +255,31 @@ cudaError_t launch_lo_from_f64<LBM_T>(LBM_T* lo, const LBM_T* hi, const double* 
 }
 
 template <>
-cudaError_t launch_volume<LBM_T>(const CaseDev<LBM_T>* cases, int ncases,
-                                 const Item* items, int n_items, int bx, int parity,
-                                 double* part, double* out, cudaStream_t s) {
+cudaError_t launch_volume_partial<LBM_T>(const CaseDev<LBM_T>* cases, const Item* items,
+                                         int n_items, int bx, int parity, double* part,
+                                         cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
   switch (bx) {
     case 32: volume_partial<LBM_T, 32><<<n_items, 32, 0, s>>>(cases, items, parity, part); break;
     case 64: volume_partial<LBM_T, 64><<<n_items, 64, 0, s>>>(cases, items, parity, part); break;
+    case 96: volume_partial<LBM_T, 96><<<n_items, 96, 0, s>>>(cases, items, parity, part); break;
     case 128: volume_partial<LBM_T, 128><<<n_items, 128, 0, s>>>(cases, items, parity, part); break;
+    case 192: volume_partial<LBM_T, 192><<<n_items, 192, 0, s>>>(cases, items, parity, part); break;
+    case 256: volume_partial<LBM_T, 256><<<n_items, 256, 0, s>>>(cases, items, parity, part); break;
     default: return cudaErrorInvalidValue;
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int warps = 4;
-  volume_final<LBM_T><<<(ncases + warps - 1) / warps, 32 * warps, 0, s>>>(cases, ncases, part, out,
-                                                                         nullptr, 0, 0, 0);
   return cudaGetLastError();
 }
 
 template <>
-cudaError_t launch_volume_final<LBM_T>(const CaseDev<LBM_T>* cases, int ncases,
-                                       const double* part, double* out, const int64_t* t,
-                                       int64_t toff, int64_t slots, int64_t stride,
-                                       cudaStream_t s) {
+cudaError_t launch_volume_final<LBM_T>(const CaseDev<LBM_T>* cases, const int* case_ids,
+                                       int ncases, const double* part, double* out,
+                                       const int64_t* t, int64_t toff, int64_t slots,
+                                       int64_t stride, cudaStream_t s) {
+  if (ncases <= 0) return cudaSuccess;
   const int warps = 4;
-  volume_final<LBM_T><<<(ncases + warps - 1) / warps, 32 * warps, 0, s>>>(cases, ncases, part, out,
-                                                                         t, toff, slots, stride);
+  volume_final<LBM_T><<<(ncases + warps - 1) / warps, 32 * warps, 0, s>>>(
+      cases, case_ids, ncases, part, out, t, toff, slots, stride);
   return cudaGetLastError();
 }
 

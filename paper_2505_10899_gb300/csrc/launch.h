@@ -8,8 +8,12 @@
 
 namespace lbmk {
 
-// Supported strip widths (threads per CTA of the step kernel).
+// Strip widths of a tiling (threads per CTA of the step kernels).
 inline bool valid_bx(int bx) { return bx == 32 || bx == 64 || bx == 128; }
+
+// Strip widths the bulk-copy kernel also runs, for cases whose whole row is
+// one strip of that width (their own chains, see lbm_api.cu).
+inline bool row_bx(int bx) { return bx == 96 || bx == 192 || bx == 256; }
 
 // tma: use the bulk-copy staged kernel (every case must have nx a multiple
 // of 16 bytes of T and nx >= 4), else the register-pipelined kernel.
@@ -65,16 +69,18 @@ cudaError_t launch_add_lo_f64(double* v, const T* lo, int64_t n, cudaStream_t s)
 template <typename T>
 cudaError_t launch_lo_from_f64(T* lo, const T* hi, const double* v, int64_t n, cudaStream_t s);
 
+// Per-item partial volumes (labelled regions) of the state in buffer parity.
 template <typename T>
-cudaError_t launch_volume(const CaseDev<T>* cases, int ncases,
-                          const Item* items, int n_items, int bx, int parity,
-                          double* part, double* out, cudaStream_t s);
+cudaError_t launch_volume_partial(const CaseDev<T>* cases, const Item* items, int n_items,
+                                  int bx, int parity, double* part, cudaStream_t s);
 
-// Per-case sums of the partials written by the step kernel (vol_part).
+// Per-case sums of the item partials (written by the step kernel's fused
+// volume or by launch_volume_partial): the cases case_ids[0..ncases), or
+// cases 0..ncases-1 with case_ids null.
 template <typename T>
-cudaError_t launch_volume_final(const CaseDev<T>* cases, int ncases, const double* part,
-                                double* out, const int64_t* t, int64_t toff, int64_t slots,
-                                int64_t stride, cudaStream_t s);
+cudaError_t launch_volume_final(const CaseDev<T>* cases, const int* case_ids, int ncases,
+                                const double* part, double* out, const int64_t* t, int64_t toff,
+                                int64_t slots, int64_t stride, cudaStream_t s);
 
 cudaError_t launch_clock(int64_t* t, int64_t n, cudaStream_t s);
 cudaError_t launch_set_clock(int64_t* t, int64_t value, cudaStream_t s);

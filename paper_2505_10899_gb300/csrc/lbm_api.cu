@@ -113,53 +113,100 @@ int check_params(const lbm_params* c, int n) {
 
 size_t elem_size(int precision) { return precision == LBM_F64 ? 8 : 4; }
 
-// Chains: contiguous case ranges of nearly equal node counts.
-std::vector<int> split_chains(const lbm_params* c, int n, int nchains) {
+// Chains: contiguous ranges of the given cases of nearly equal node counts.
+std::vector<int> split_chains(const lbm_params* c, const std::vector<int>& ids, int nchains) {
+  const int n = (int)ids.size();
   nchains = std::max(1, std::min(nchains, n));
   int64_t total = 0;
-  for (int k = 0; k < n; ++k) total += (int64_t)c[k].nx * c[k].ny;
+  for (int k : ids) total += (int64_t)c[k].nx * c[k].ny;
   std::vector<int> b(nchains + 1, 0);
   b[nchains] = n;
   int64_t acc = 0;
   int k = 0;
   for (int ch = 1; ch < nchains; ++ch) {
     const int64_t want = total * ch / nchains;
-    while (k < n - (nchains - ch) && (k < b[ch - 1] + 1 || acc + (int64_t)c[k].nx * c[k].ny / 2 < want))
-      acc += (int64_t)c[k].nx * c[k].ny, ++k;
+    while (k < n - (nchains - ch) &&
+           (k < b[ch - 1] + 1 || acc + (int64_t)c[ids[k]].nx * c[ids[k]].ny / 2 < want))
+      acc += (int64_t)c[ids[k]].nx * c[ids[k]].ny, ++k;
     b[ch] = k;
   }
   return b;
 }
 
-// Work items: strips of bx columns, runs of `rows` rows.  Items are grouped
-// by chain; within a chain the cases go largest first (their items are the
-// slowest), so the small ones fill the end of the step.  The items of one
-// case stay contiguous: [beg[k], end[k]).
-std::vector<Item> make_items(const lbm_params* c, int n, const Tiling& t,
-                             const std::vector<int>& chain_case, std::vector<int>* beg,
-                             std::vector<int>* end, std::vector<int>* chain_item) {
-  std::vector<Item> it;
-  beg->assign(n, 0);
-  end->assign(n, 0);
-  const int nch = (int)chain_case.size() - 1;
-  chain_item->assign(nch + 1, 0);
+// Whole-row strip width of a case when the tiling's strips are 128 wide: a
+// case whose row fits one of the widths 64, 96, 192 or 256 (the smallest that
+// holds it, 128 included) runs its rows as single strips of that width in a
+// chain of its own, which copies each row once per plane and needs no
+// periodic-wrap pieces; 0: the case runs the tiling's strips.
+int row_width(int nx) {
+  for (int w : {64, 96, 128, 192, 256})
+    if (nx <= w) return w == 128 ? 0 : w;
+  return 0;
+}
+
+// The chains and work items of a tiling.  Work items are strips of the
+// chain's width, runs of `rows` rows.  Items are grouped by chain; within a
+// chain the cases go largest first (their items are the slowest), so the
+// small ones fill the end of the step.  The items of one case stay
+// contiguous: [beg[k], end[k]).  Without whole rows (rowmode false, or a
+// tiling other than 128-wide strips) the chains are nreq contiguous case
+// ranges of nearly equal node counts; with them, the cases of the tiling's
+// strips form up to nreq such chains and each whole-row width one more.
+struct Plan {
+  std::vector<int> chain_case, chain_cases, chain_bx, chain_item, beg, end, case_chain;
+  std::vector<Item> items;
+};
+
+Plan make_plan(const lbm_params* c, int n, const Tiling& t, int nreq, bool rowmode) {
+  Plan pl;
+  std::vector<int> generic;
+  std::vector<int> byw[4];
+  const int widths[4] = {64, 96, 192, 256};
+  rowmode = rowmode && t.bx == 128;
+  for (int k = 0; k < n; ++k) {
+    const int w = rowmode ? row_width(c[k].nx) : 0;
+    int q = -1;
+    for (int j = 0; j < 4; ++j)
+      if (widths[j] == w) q = j;
+    if (q < 0) generic.push_back(k);
+    else byw[q].push_back(k);
+  }
+  auto add_chain = [&](const std::vector<int>& ids, int beg_i, int end_i, int bx) {
+    pl.chain_case.push_back((int)pl.chain_cases.size());
+    for (int r = beg_i; r < end_i; ++r) pl.chain_cases.push_back(ids[r]);
+    pl.chain_bx.push_back(bx);
+  };
+  if (!generic.empty()) {
+    const std::vector<int> b = split_chains(c, generic, nreq);
+    for (size_t ch = 0; ch + 1 < b.size(); ++ch) add_chain(generic, b[ch], b[ch + 1], t.bx);
+  }
+  for (int j = 0; j < 4; ++j)
+    if (!byw[j].empty()) add_chain(byw[j], 0, (int)byw[j].size(), widths[j]);
+  pl.chain_case.push_back((int)pl.chain_cases.size());
+  const int nch = (int)pl.chain_bx.size();
+  pl.beg.assign(n, 0);
+  pl.end.assign(n, 0);
+  pl.case_chain.assign(n, 0);
+  pl.chain_item.assign(nch + 1, 0);
   for (int ch = 0; ch < nch; ++ch) {
-    (*chain_item)[ch] = (int)it.size();
-    std::vector<int> order;
-    for (int k = chain_case[ch]; k < chain_case[ch + 1]; ++k) order.push_back(k);
+    pl.chain_item[ch] = (int)pl.items.size();
+    std::vector<int> order(pl.chain_cases.begin() + pl.chain_case[ch],
+                           pl.chain_cases.begin() + pl.chain_case[ch + 1]);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
       return (int64_t)c[a].nx * c[a].ny > (int64_t)c[b].nx * c[b].ny;
     });
+    const int bx = pl.chain_bx[ch];
     for (int k : order) {
-      (*beg)[k] = (int)it.size();
+      pl.case_chain[k] = ch;
+      pl.beg[k] = (int)pl.items.size();
       for (int y0 = 0; y0 < c[k].ny; y0 += t.rows)
-        for (int x0 = 0; x0 < c[k].nx; x0 += t.bx)
-          it.push_back(Item{k, x0, y0, std::min(t.rows, c[k].ny - y0)});
-      (*end)[k] = (int)it.size();
+        for (int x0 = 0; x0 < c[k].nx; x0 += bx)
+          pl.items.push_back(Item{k, x0, y0, std::min(t.rows, c[k].ny - y0)});
+      pl.end[k] = (int)pl.items.size();
     }
   }
-  (*chain_item)[nch] = (int)it.size();
-  return it;
+  pl.chain_item[nch] = (int)pl.items.size();
+  return pl;
 }
 
 // Default tiling: the widest strip that leaves at most 15% of the threads idle
@@ -214,6 +261,8 @@ Layout make_layout(const lbm_params* c, int n, int n_items, int total_regions) {
   off = align_up(off + (size_t)std::max(total_regions, n * lbmk::kMaxRegions) * sizeof(double));
   L.init = off;
   off = align_up(off + (size_t)n * sizeof(lbmk::InitSrc));
+  L.chainc = off;  // case indices, chain by chain
+  off = align_up(off + (size_t)n * sizeof(int));
   int64_t maxp = 0;
   for (int k = 0; k < n; ++k) maxp = std::max<int64_t>(maxp, (int64_t)c[k].nx * c[k].ny);
   L.staging = off;
@@ -413,7 +462,8 @@ int enqueue_steps(lbm_handle* h, cudaStream_t s, int parity, int count, bool fli
   for (int c = 0; c < nch; ++c) {
     cudaStream_t sc = c == 0 ? s : h->aux[c - 1];
     const int i0 = h->chain_item[c], ni = h->chain_item[c + 1] - i0;
-    const int c0 = h->chain_case[c], nc = h->chain_case[c + 1] - c0;
+    const int q0 = h->chain_case[c], nc = h->chain_case[c + 1] - q0;
+    const int bx = h->chain_bx[c];
     for (int j = 0; j < count; ++j) {
       const int par = flip ? (parity + j) & 1 : parity;
       const int64_t toff = flip ? j : 0;
@@ -422,20 +472,22 @@ int enqueue_steps(lbm_handle* h, cudaStream_t s, int parity, int count, bool fli
         StepArgs<float> a = step_args<float>(h, par, toff);
         a.items = h->items_dev + i0;
         a.vol_part = (vol && h->track) ? h->part + (int64_t)i0 * lbmk::kMaxRegions : nullptr;
-        e = lbmk::launch_step<float>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), ni, sc);
+        e = lbmk::launch_step<float>(a, bx, coupled, lbmk::kModeStep, use_tma(h), ni, sc);
         if (e == cudaSuccess && vol && h->track)
-          e = lbmk::launch_volume_final<float>((const CaseDev<float>*)h->cases_dev + c0, nc,
-                                               h->part, h->track, h->t_dev, toff,
-                                               h->track_slots, h->total_regions, sc);
+          e = lbmk::launch_volume_final<float>((const CaseDev<float>*)h->cases_dev,
+                                               h->chain_cases_dev + q0, nc, h->part, h->track,
+                                               h->t_dev, toff, h->track_slots,
+                                               h->total_regions, sc);
       } else {
         StepArgs<double> a = step_args<double>(h, par, toff);
         a.items = h->items_dev + i0;
         a.vol_part = (vol && h->track) ? h->part + (int64_t)i0 * lbmk::kMaxRegions : nullptr;
-        e = lbmk::launch_step<double>(a, h->tile.bx, coupled, lbmk::kModeStep, use_tma(h), ni, sc);
+        e = lbmk::launch_step<double>(a, bx, coupled, lbmk::kModeStep, use_tma(h), ni, sc);
         if (e == cudaSuccess && vol && h->track)
-          e = lbmk::launch_volume_final<double>((const CaseDev<double>*)h->cases_dev + c0, nc,
-                                               h->part, h->track, h->t_dev, toff,
-                                               h->track_slots, h->total_regions, sc);
+          e = lbmk::launch_volume_final<double>((const CaseDev<double>*)h->cases_dev,
+                                               h->chain_cases_dev + q0, nc, h->part, h->track,
+                                               h->t_dev, toff, h->track_slots,
+                                               h->total_regions, sc);
       }
       if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
     }
@@ -549,7 +601,7 @@ int do_fields(lbm_handle* h, int c, double* phi, double* ux, double* uy, double*
   a.out_ux = st + n;
   a.out_uy = st + 2 * n;
   a.out_p = st + 3 * n;
-  cudaError_t e = lbmk::launch_step<T>(a, h->tile.bx, h->flow == LBM_FLOW_COUPLED,
+  cudaError_t e = lbmk::launch_step<T>(a, h->chain_bx[h->case_chain[c]], h->flow == LBM_FLOW_COUPLED,
                                        lbmk::kModeFields, use_tma(h),
                                        h->item_end[c] - h->item_begin[c], h->stream);
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("fields: ") + cudaGetErrorString(e));
@@ -651,25 +703,44 @@ size_t state_bytes_case(const lbm_handle* h, int k) {
 }
 
 // New tiling or chain count: rebuild the item table and the case table.
+// Whole-row chains need the bulk-copy kernel (FP32; the FP64 kernels are
+// bound by the FP64 pipe, where the strip layout hardly matters).
+bool rowmode(const lbm_handle* h) {
+  return h->row_chains && use_tma(h) && h->precision == LBM_F32;
+}
+
+void apply_plan(lbm_handle* h, Plan& pl) {
+  h->nchains = (int)pl.chain_bx.size();
+  h->chain_case.swap(pl.chain_case);
+  h->chain_cases.swap(pl.chain_cases);
+  h->chain_bx.swap(pl.chain_bx);
+  h->chain_item.swap(pl.chain_item);
+  h->case_chain.swap(pl.case_chain);
+  h->items.swap(pl.items);
+  h->item_begin.swap(pl.beg);
+  h->item_end.swap(pl.end);
+}
+
+int upload_plan(lbm_handle* h) {
+  LBM_CUDA(cudaMemcpyAsync(h->items_dev, h->items.data(), h->items.size() * sizeof(Item),
+                           cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(h->chain_cases_dev, h->chain_cases.data(),
+                           h->chain_cases.size() * sizeof(int), cudaMemcpyHostToDevice,
+                           h->stream));
+  return upload_cases(h);
+}
+
 int retile(lbm_handle* h, const Tiling& t, int nchains) {
-  std::vector<int> b, e, ci;
-  std::vector<int> cc = split_chains(h->params.data(), h->ncases, nchains);
-  std::vector<Item> it = make_items(h->params.data(), h->ncases, t, cc, &b, &e, &ci);
-  if ((int64_t)it.size() > max_items(h->params.data(), h->ncases))
+  Plan pl = make_plan(h->params.data(), h->ncases, t, nchains, rowmode(h));
+  if ((int64_t)pl.items.size() > max_items(h->params.data(), h->ncases))
     return fail(LBM_ERR_ARG, "tiling needs more work items than the workspace holds");
   drop_graph(h);
   // the previous step's kernels may still read the item table
   LBM_CUDA(cudaStreamSynchronize(h->stream));
   h->tile = t;
-  h->nchains = (int)cc.size() - 1;
-  h->chain_case.swap(cc);
-  h->chain_item.swap(ci);
-  h->items.swap(it);
-  h->item_begin.swap(b);
-  h->item_end.swap(e);
-  LBM_CUDA(cudaMemcpyAsync(h->items_dev, h->items.data(), h->items.size() * sizeof(Item),
-                           cudaMemcpyHostToDevice, h->stream));
-  return upload_cases(h);
+  h->chains_req = nchains;
+  apply_plan(h, pl);
+  return upload_plan(h);
 }
 
 }  // namespace
@@ -727,10 +798,7 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   h->flow = cases[0].flow;
   h->stream = (cudaStream_t)stream;
   h->tile = choose_tiling(cases, ncases);
-  h->nchains = std::min(2, ncases);
-  h->chain_case = split_chains(cases, ncases, h->nchains);
-  h->items = make_items(cases, ncases, h->tile, h->chain_case, &h->item_begin, &h->item_end,
-                        &h->chain_item);
+  h->chains_req = std::min(2, ncases);
   h->nregions.assign(ncases, 1);
   h->vol_base.resize(ncases);
   for (int k = 0; k < ncases; ++k) h->vol_base[k] = k;
@@ -762,6 +830,11 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
     for (int k = 0; k < ncases; ++k)
       if (cases[k].walls) h->tma_ok = false;
   }
+  h->chain_cases_dev = (int*)(h->ws + h->L.chainc);
+  {
+    Plan pl = make_plan(cases, ncases, h->tile, h->chains_req, rowmode(h));
+    apply_plan(h, pl);
+  }
 
   auto cleanup = [&](int code) {
     lbm_destroy(h);
@@ -782,12 +855,11 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
     if (e != cudaSuccess)
       return cleanup(fail(LBM_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e)));
   }
-  if (cudaMemsetAsync(h->ws + h->L.hdr, 0, 64, h->stream) != cudaSuccess ||
-      cudaMemcpyAsync(h->items_dev, h->items.data(), h->items.size() * sizeof(Item),
-                      cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+  if (cudaMemsetAsync(h->ws + h->L.hdr, 0, 64, h->stream) != cudaSuccess)
     return cleanup(fail(LBM_ERR_CUDA, "header upload failed"));
-  // labels planes: zero (region 0 everywhere) until lbm_set_regions
-  rc = upload_cases(h);
+  // items, chains and cases; labels planes: zero (region 0 everywhere)
+  // until lbm_set_regions
+  rc = upload_plan(h);
   if (rc) return cleanup(rc);
 
   // Initial fields.  Where the device can read the caller's arrays itself
@@ -844,16 +916,18 @@ int lbm_init(const lbm_params* cases, int32_t ncases, void* d_workspace, size_t 
   {
     const lbm_params& p = cases[0];  // launch-uniform physics
     const double beta4 = 4.0 * (12.0 * p.sigma / p.W), kappa = 1.5 * p.sigma * p.W;
-    const int ni = (int)h->items.size();
-    cudaError_t e;
-    if (h->precision == LBM_F32)
-      e = lbmk::launch_init_items<float>((const CaseDev<float>*)h->cases_dev, h->items_dev, ni,
-                                         h->tile.bx, src_dev, beta4, kappa, p.lambda, vortex,
-                                         p.vortex_U, 0, h->stream);
-    else
-      e = lbmk::launch_init_items<double>((const CaseDev<double>*)h->cases_dev, h->items_dev, ni,
-                                          h->tile.bx, src_dev, beta4, kappa, p.lambda, vortex,
-                                          p.vortex_U, 0, h->stream);
+    cudaError_t e = cudaSuccess;
+    for (int c = 0; c < h->nchains && e == cudaSuccess; ++c) {  // one launch per strip width
+      const int i0 = h->chain_item[c], ni = h->chain_item[c + 1] - i0;
+      if (h->precision == LBM_F32)
+        e = lbmk::launch_init_items<float>((const CaseDev<float>*)h->cases_dev, h->items_dev + i0,
+                                           ni, h->chain_bx[c], src_dev, beta4, kappa, p.lambda,
+                                           vortex, p.vortex_U, 0, h->stream);
+      else
+        e = lbmk::launch_init_items<double>((const CaseDev<double>*)h->cases_dev,
+                                            h->items_dev + i0, ni, h->chain_bx[c], src_dev, beta4,
+                                            kappa, p.lambda, vortex, p.vortex_U, 0, h->stream);
+    }
     if (e != cudaSuccess) return cleanup(fail(LBM_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e)));
   }
   if (cudaStreamSynchronize(h->stream) != cudaSuccess)
@@ -967,9 +1041,12 @@ int lbm_set_kernel(lbm_handle* h, int32_t variant) {
     return fail(LBM_ERR_ARG, "bulk-copy kernel needs nx a multiple of 16 bytes and nx >= 4");
   if (variant == 3 && total_nodes(h) > kPersistMaxNodes)
     return fail(LBM_ERR_ARG, "persistent kernel is for batches of at most 4 Mi nodes");
-  if (variant != h->kernel) drop_graph(h);
+  if (variant == h->kernel) return LBM_OK;
+  const int keep = h->kernel;
   h->kernel = variant;
-  return LBM_OK;
+  const int rc = retile(h, h->tile, h->chains_req);  // whole-row chains follow the kernel
+  if (rc != LBM_OK) h->kernel = keep;
+  return rc;
 }
 
 int32_t lbm_get_kernel(const lbm_handle* h) {
@@ -1001,49 +1078,59 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel, int32_t* b
   const int n_trial = trials < 8 ? 8 : trials;
   const Tiling keep_tile = h->tile;
   const int keep_kernel = h->kernel;
+  const bool keep_rows = h->row_chains;
   double best = 1e300;
   Tiling best_t = keep_tile;
   int best_k = use_tma(h) ? 2 : 1;
+  bool best_rc = keep_rows;
   int rc = LBM_OK;
   for (int kv : {2, 1, 3}) {
     if (kv == 2 && !h->tma_ok) continue;
     if (kv == 3 && total_nodes(h) > kPersistMaxNodes) continue;
     for (int bx : {128, 64, 32}) {
       for (int rows : {2, 4, 8, 16, 32, 64, 128}) {
-        h->kernel = kv;
-        rc = lbm_set_tiling(h, bx, rows);
+        // whole-row chains exist for the FP32 bulk-copy kernel on 128-wide
+        // strips only: try them on and off there
+        const int nrc = (kv == 2 && bx == 128 && h->precision == LBM_F32) ? 2 : 1;
+        for (int rcv = 0; rcv < nrc; ++rcv) {
+          h->kernel = kv;
+          h->row_chains = rcv == 1;
+          rc = lbm_set_tiling(h, bx, rows);
+          if (rc != LBM_OK) break;
+          cudaError_t e = cudaSuccess;
+          if (kv == 3) {  // one launch of n_trial steps without flipping buffers
+            rc = launch_persist(h, h->stream, h->parity, 1, 0);
+            if (rc == LBM_OK) e = cudaEventRecord(e0, h->stream);
+            if (rc == LBM_OK && e == cudaSuccess) rc = launch_persist(h, h->stream, h->parity, n_trial, 0);
+            if (rc != LBM_OK) break;
+          } else {
+            cudaGraphExec_t gx = nullptr;
+            rc = capture_steps(h, h->parity, n_trial, false, false, false, &gx);
+            if (rc != LBM_OK) break;
+            e = cudaGraphLaunch(gx, h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+            if (e == cudaSuccess) e = cudaGraphLaunch(gx, h->stream);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (gx) cudaGraphExecDestroy(gx);
+          }
+          if (kv == 3 && e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+          if (kv == 3 && e == cudaSuccess) e = cudaEventSynchronize(e1);
+          float ms = 0.f;
+          if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+          if (e != cudaSuccess) {
+            rc = fail(LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+            break;
+          }
+          if (ms / n_trial < best) {
+            best = ms / n_trial;
+            best_t.bx = bx;
+            best_t.rows = rows;
+            best_k = kv;
+            best_rc = rcv == 1;
+          }
+        }
         if (rc != LBM_OK) break;
-        cudaError_t e = cudaSuccess;
-        if (kv == 3) {  // one launch of n_trial steps without flipping buffers
-          rc = launch_persist(h, h->stream, h->parity, 1, 0);
-          if (rc == LBM_OK) e = cudaEventRecord(e0, h->stream);
-          if (rc == LBM_OK && e == cudaSuccess) rc = launch_persist(h, h->stream, h->parity, n_trial, 0);
-          if (rc != LBM_OK) break;
-        } else {
-          cudaGraphExec_t gx = nullptr;
-          rc = capture_steps(h, h->parity, n_trial, false, false, false, &gx);
-          if (rc != LBM_OK) break;
-          e = cudaGraphLaunch(gx, h->stream);
-          if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-          if (e == cudaSuccess) e = cudaGraphLaunch(gx, h->stream);
-          if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-          if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-          if (gx) cudaGraphExecDestroy(gx);
-        }
-        if (kv == 3 && e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-        if (kv == 3 && e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-          rc = fail(LBM_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-          break;
-        }
-        if (ms / n_trial < best) {
-          best = ms / n_trial;
-          best_t.bx = bx;
-          best_t.rows = rows;
-          best_k = kv;
-        }
       }
       if (rc != LBM_OK) break;
     }
@@ -1053,10 +1140,12 @@ int lbm_autotune(lbm_handle* h, int32_t trials, int32_t* best_kernel, int32_t* b
   cudaEventDestroy(e1);
   if (rc != LBM_OK) {
     h->kernel = keep_kernel;
+    h->row_chains = keep_rows;
     lbm_set_tiling(h, keep_tile.bx, keep_tile.rows);
     return rc;
   }
   h->kernel = best_k;
+  h->row_chains = best_rc;
   rc = lbm_set_tiling(h, best_t.bx, best_t.rows);
   if (rc != LBM_OK) return rc;
   if (best_kernel) *best_kernel = best_k;
@@ -1081,7 +1170,7 @@ int lbm_set_tiling(lbm_handle* h, int32_t bx, int32_t rows) {
   Tiling t;
   t.bx = bx;
   t.rows = rows;
-  return retile(h, t, h->nchains);
+  return retile(h, t, h->chains_req);
 }
 
 int lbm_set_wait_limit(lbm_handle* h, int64_t cycles) {
@@ -1094,12 +1183,23 @@ int lbm_set_wait_limit(lbm_handle* h, int64_t cycles) {
 
 int lbm_set_chains(lbm_handle* h, int32_t nchains) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
-  if (nchains < 1 || nchains > lbmk::kMaxChains)
-    return fail(LBM_ERR_ARG, "nchains must lie in [1, 4]");
+  if (nchains < 1 || nchains > 4) return fail(LBM_ERR_ARG, "nchains must lie in [1, 4]");
   return retile(h, h->tile, std::min<int>(nchains, h->ncases));
 }
 
 int32_t lbm_get_chains(const lbm_handle* h) { return h ? h->nchains : 0; }
+
+int lbm_set_row_chains(lbm_handle* h, int32_t on) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  if (on != 0 && on != 1) return fail(LBM_ERR_ARG, "on must be 0 or 1");
+  if ((on != 0) == h->row_chains) return LBM_OK;
+  h->row_chains = on != 0;
+  const int rc = retile(h, h->tile, h->chains_req);
+  if (rc != LBM_OK) h->row_chains = !h->row_chains;
+  return rc;
+}
+
+int32_t lbm_get_row_chains(const lbm_handle* h) { return h && rowmode(h) ? 1 : 0; }
 
 int lbm_track_volume_history(lbm_handle* h, double* out, int64_t nslots) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
@@ -1131,14 +1231,27 @@ int lbm_track_volume(lbm_handle* h, double* d_out) {
 int lbm_volume_async(lbm_handle* h, double* d_out) {
   lbmk::TraceRange trace("lbm_volume");
   if (!h || !d_out) return fail(LBM_ERR_ARG, "null argument");
-  cudaError_t e;
-  const int n = (int)h->items.size();
-  if (h->precision == LBM_F32)
-    e = lbmk::launch_volume<float>((const CaseDev<float>*)h->cases_dev, h->ncases, h->items_dev, n,
-                                   h->tile.bx, h->parity, h->part, d_out, h->stream);
-  else
-    e = lbmk::launch_volume<double>((const CaseDev<double>*)h->cases_dev, h->ncases, h->items_dev, n,
-                                    h->tile.bx, h->parity, h->part, d_out, h->stream);
+  cudaError_t e = cudaSuccess;
+  // item partials chain by chain (each chain's strip width), then the cases
+  for (int c = 0; c < h->nchains && e == cudaSuccess; ++c) {
+    const int i0 = h->chain_item[c], ni = h->chain_item[c + 1] - i0;
+    double* part = h->part + (int64_t)i0 * lbmk::kMaxRegions;
+    if (h->precision == LBM_F32)
+      e = lbmk::launch_volume_partial<float>((const CaseDev<float>*)h->cases_dev, h->items_dev + i0,
+                                             ni, h->chain_bx[c], h->parity, part, h->stream);
+    else
+      e = lbmk::launch_volume_partial<double>((const CaseDev<double>*)h->cases_dev,
+                                              h->items_dev + i0, ni, h->chain_bx[c], h->parity,
+                                              part, h->stream);
+  }
+  if (e == cudaSuccess) {
+    if (h->precision == LBM_F32)
+      e = lbmk::launch_volume_final<float>((const CaseDev<float>*)h->cases_dev, nullptr, h->ncases,
+                                           h->part, d_out, nullptr, 0, 0, 0, h->stream);
+    else
+      e = lbmk::launch_volume_final<double>((const CaseDev<double>*)h->cases_dev, nullptr,
+                                            h->ncases, h->part, d_out, nullptr, 0, 0, 0, h->stream);
+  }
   if (e != cudaSuccess) return fail(LBM_ERR_CUDA, std::string("volume: ") + cudaGetErrorString(e));
   return LBM_OK;
 }

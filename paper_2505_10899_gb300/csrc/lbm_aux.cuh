@@ -423,13 +423,15 @@ template <typename T>
 // With a history (slots > 1), the volumes of the state at step t + toff (t
 // the device step clock) go to slot (t + toff) mod slots, `stride` doubles
 // per slot.
-__global__ void volume_final(const CaseDev<T>* __restrict__ cases, int ncases,
+__global__ void volume_final(const CaseDev<T>* __restrict__ cases,
+                             const int* __restrict__ case_ids, int ncases,
                              const double* __restrict__ part, double* __restrict__ out,
                              const int64_t* __restrict__ t, int64_t toff, int64_t slots,
                              int64_t stride) {
-  const int c = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (c >= ncases) return;
+  if (w >= ncases) return;
+  const int c = case_ids ? case_ids[w] : w;
   if (slots > 1) out += ((*t + toff) % slots) * stride;
   const CaseDev<T>& cd = cases[c];
   for (int r = 0; r < cd.nregions; ++r) {

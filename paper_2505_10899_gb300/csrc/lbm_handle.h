@@ -14,7 +14,7 @@
 namespace lbmk {
 
 struct Layout {
-  size_t hdr = 0, cases = 0, items = 0, part = 0, vol = 0, init = 0, staging = 0;
+  size_t hdr = 0, cases = 0, items = 0, part = 0, vol = 0, init = 0, chainc = 0, staging = 0;
   std::vector<size_t> f, g, J, lab;  // per-case offsets (f: 2 buffers back to back)
   std::vector<size_t> glo;           // FP32: low part of g_0, 2 planes per case
   std::vector<int64_t> plane;
@@ -29,7 +29,7 @@ struct Tiling {
 // Independent case groups ("chains") whose steps are captured as parallel
 // branches of one CUDA graph, so that the last CTAs of one group's step run
 // beside the next group's work instead of leaving SMs idle.
-constexpr int kMaxChains = 4;
+constexpr int kMaxChains = 8;  // 4 of the tiling's strips + 4 whole-row widths
 
 // A captured and instantiated sequence of `count` steps starting from source
 // buffer `parity`.
@@ -60,9 +60,15 @@ struct lbm_handle {
   lbmk::Phys<double> pd{};
   std::vector<lbmk::CaseDev<float>> cf;
   std::vector<lbmk::CaseDev<double>> cd;
-  int nchains = 1;
-  std::vector<int> chain_case;  // chain c: cases [chain_case[c], chain_case[c+1])
+  int nchains = 1;              // chains of the current plan
+  int chains_req = 2;           // chains requested for the tiling's strips
+  bool row_chains = false;      // whole-row chains requested (lbm_set_row_chains)
+  std::vector<int> chain_case;  // chain c: its cases chain_cases[chain_case[c] .. chain_case[c+1])
+  std::vector<int> chain_cases; //   (case indices, chain by chain)
   std::vector<int> chain_item;  //          items [chain_item[c], chain_item[c+1])
+  std::vector<int> chain_bx;    //          strip width of its CTAs
+  std::vector<int> case_chain;  // chain of each case
+  int* chain_cases_dev = nullptr;  // chain_cases on the device (per-chain volume sums)
   cudaStream_t aux[lbmk::kMaxChains - 1] = {};  // capture streams of chains 1..
   cudaEvent_t fork_ev = nullptr;
   cudaEvent_t join_ev[lbmk::kMaxChains - 1] = {};

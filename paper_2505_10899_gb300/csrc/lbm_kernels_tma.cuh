@@ -316,8 +316,20 @@ __device__ __forceinline__ void tma_body(const StepArgs<T>& a) {
   }
 }
 
+// CTAs per SM the FP32 kernel is register-capped for (its shared memory
+// allows about as many): about 80 registers a thread in every width.
+template <typename T, int BX>
+constexpr int tma_min_blocks() {
+  return sizeof(T) != 4 ? 1
+         : BX == 128    ? 6
+         : BX == 96     ? 6
+         : BX == 192    ? 4
+         : BX == 256    ? 3
+                        : 1;
+}
+
 template <typename T, int BX, bool COUPLED, int MODE, int S>
-__global__ void __launch_bounds__(BX, (sizeof(T) == 4 && BX == 128) ? 6 : 1)
+__global__ void __launch_bounds__(BX, (tma_min_blocks<T, BX>()))
     step_kernel_tma(const StepArgs<T> a) {
   const Item it = a.items[blockIdx.x];
   if (it.x0 == 0 && a.cases[it.c].nx <= BX)

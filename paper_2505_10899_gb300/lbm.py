@@ -70,6 +70,8 @@ def _load():
         "lbm_prepare_steps": ([_H, ctypes.c_int64], ctypes.c_int),
         "lbm_set_chains": ([_H, ctypes.c_int32], ctypes.c_int),
         "lbm_get_chains": ([_H], ctypes.c_int32),
+        "lbm_set_row_chains": ([_H, ctypes.c_int32], ctypes.c_int),
+        "lbm_get_row_chains": ([_H], ctypes.c_int32),
         "lbm_set_wait_limit": ([_H, ctypes.c_int64], ctypes.c_int),
         "lbm_fp64_fma_rate": ([ctypes.c_int64, ctypes.c_int32, _D, _D], ctypes.c_int),
         "lbm_record_steps": ([_H, ctypes.c_int64, _VP, ctypes.c_int64], ctypes.c_int),
@@ -457,6 +459,13 @@ class Sim:
 
     def set_chains(self, n):
         lbm_set_chains(self.h, n)
+
+    def set_row_chains(self, on=True):
+        """Whole-row chains for cases whose rows fit 64, 96, 192 or 256 columns."""
+        _check(_lib.lbm_set_row_chains(self.h, 1 if on else 0), "lbm_set_row_chains")
+
+    def row_chains(self):
+        return bool(_lib.lbm_get_row_chains(self.h))
 
     def chains(self):
         return lbm_get_chains(self.h)

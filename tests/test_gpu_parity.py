@@ -261,6 +261,67 @@ def test_chains_do_not_change_results(L):
         s.set_chains(5)
 
 
+def test_whole_row_chains_fp32(L):
+    # FP32, bulk-copy kernel, 128-column strips: cases whose row fits 64, 96,
+    # 192 or 256 columns run whole-row strips in chains of their own (four
+    # here); the others form the requested chains.  Every case matches the
+    # oracle, the states agree with the same batch on 64-column strips (no
+    # whole-row chains) up to FMA contraction, and the fused volumes with
+    # lbm_volume.
+    import torch
+    widths = [(64, 40), (96, 36), (100, 30), (128, 33), (192, 28), (200, 26), (256, 24), (384, 20)]
+    cases, phis, us = [], [], []
+    for k, (nx, ny) in enumerate(widths):
+        cases.append(W.base_case(nx, ny, rho_l=1.0 + k, tau_f_l=0.8, tau_f_g=0.9))
+        phi = W.tanh_disc(nx, ny, 0.45 * nx, 0.5 * ny, min(nx, ny) / 4, 4.0, periodic=True)
+        phis.append(phi + W.uniform(40 + k, phi.shape, -1e-3, 1e-3))
+        u = np.zeros((2, ny, nx))
+        u[k % 2] = 0.01 * (-1) ** k
+        us.append(u)
+    a = L.Sim(cases, phis, us, precision="f32")
+    a.set_kernel(2)
+    a.set_tiling(128, 16)
+    a.set_chains(2)
+    assert a.chains() == 2 and not a.row_chains()  # off by default
+    a.set_row_chains(True)
+    assert a.row_chains()
+    assert a.chains() == 2 + 4  # widths 64, 96, 192 and 256 (the 200-wide row included)
+    vol = a.track_volume(True)
+    b = L.Sim(cases, phis, us, precision="f32")
+    b.set_kernel(2)
+    b.set_tiling(64, 16)
+    assert b.chains() == 2
+    a.step(50)
+    b.step(50)
+    assert a.status() == L.LBM_OK and b.status() == L.LBM_OK
+    torch.cuda.synchronize()
+    fused = vol.cpu().numpy().copy()
+    for k, (c, p0, u0) in enumerate(zip(cases, phis, us)):
+        o = oracle.Oracle(c, p0, u0).step(50)
+        phi, ux, uy, p = a.fields(k)
+        ophi, oux, ouy, op = o.fields()
+        assert maxdiff(phi, ophi) <= TOL32_PHI, k
+        assert maxdiff(ux, oux) <= 1e-6 and maxdiff(uy, ouy) <= 1e-6, k
+        for x, y in zip(a.get_state(k)[:3], b.get_state(k)[:3]):
+            assert maxdiff(x, y) <= 2e-6, k
+    # the fused volumes of the last step: the state at t = 49, up to the low
+    # part of g_0 that the fused FP32 sum leaves out
+    r = L.Sim(cases, phis, us, precision="f32")
+    r.set_kernel(2)
+    r.set_tiling(128, 16)
+    r.set_row_chains(True)
+    r.step(49)
+    assert np.abs(fused / r.volume() - 1).max() < 1e-7
+    # the register kernel runs no whole-row chains; the request comes back
+    # with the bulk-copy kernel
+    r.set_kernel(1)
+    assert not r.row_chains() and r.chains() == 2
+    r.set_kernel(2)
+    assert r.row_chains() and r.chains() == 6
+    for s in (a, b, r):
+        s.close()
+
+
 def test_three_chains_match_oracle_fp64(L):
     cases, phis, us = _chain_batch()
     oracles = [oracle.Oracle(c, p, u).step(30) for c, p, u in zip(cases, phis, us)]
