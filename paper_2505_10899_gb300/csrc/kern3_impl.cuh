@@ -6,6 +6,7 @@
 #include "lbm3_async.cuh"
 #include "lbm3_bulk.cuh"
 #include "lbm3_kernels.cuh"
+#include "lbm3_strip.cuh"
 
 namespace lbmk3 {
 
@@ -81,6 +82,23 @@ static cudaError_t launch_bulk(const Args3<T, S>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <typename T, typename S, int BX, int BY, int NST, int MINB>
+static cudaError_t launch_strip(const Args3<T, S>& a, cudaStream_t st) {
+  constexpr size_t bytes = strip_smem_bytes<T, S, BX, BY, NST>();
+  static bool attr_set = false;  // per instantiation, per process (one device)
+  if (!attr_set) {
+    const cudaError_t e = cudaFuncSetAttribute(step3_strip_kernel<T, S, BX, BY, NST, MINB>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)bytes);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (a.nx % BX != 0) return cudaErrorInvalidValue;
+  const dim3 grid(a.nx / BX, (a.ny + BY - 1) / BY, (a.nz + a.zc - 1) / a.zc);
+  step3_strip_kernel<T, S, BX, BY, NST, MINB><<<grid, BX * BY, bytes, st>>>(a, lbmk::kWaitCycles);
+  return cudaGetLastError();
+}
+
 template <typename T, typename S>
 static cudaError_t step_async(const Args3<T, S>& a, int variant, int bx, int by,
                               cudaStream_t st) {
@@ -90,6 +108,14 @@ static cudaError_t step_async(const Args3<T, S>& a, int variant, int bx, int by,
       constexpr int NST = sizeof(S) == 2 ? 3 : 2;
       if (bx == 256 && by == 2) return launch_bulk<T, S, 256, 2, NST>(a, st);
       if (bx == 128 && by == 4) return launch_bulk<T, S, 128, 4, NST>(a, st);
+      return cudaErrorInvalidValue;
+    }
+    if (variant == kVarStrip) {
+      // about 90 KB per CTA of 256 threads: two CTAs per SM, with three FP16
+      // stages or two FP32 ones per CTA
+      constexpr int NST = sizeof(S) == 2 ? 3 : 2;
+      if (bx == 32 && by == 8) return launch_strip<T, S, 32, 8, NST, 2>(a, st);
+      if (bx == 64 && by == 4) return launch_strip<T, S, 64, 4, NST, 2>(a, st);
       return cudaErrorInvalidValue;
     }
   }

@@ -30,6 +30,8 @@ inline bool tile_regs_ok(int bx, int by) {
 }
 // Tiles of the bulk-copy kernel: whole x-rows, 128 x 4 or 256 x 2.
 inline bool tile_bulk_ok(int bx, int by) { return (bx == 128 && by == 4) || (bx == 256 && by == 2); }
+// Tiles of the strip bulk-copy kernel (nx a multiple of bx, nx >= 2 bx).
+inline bool tile_strip_ok(int bx, int by) { return (bx == 32 && by == 8) || (bx == 64 && by == 4); }
 inline bool tile_ok(int bx, int by) { return tile_regs_ok(bx, by) || tile_bulk_ok(bx, by); }
 
 inline int64_t n_ctas(int nx, int ny, int nz, int bx, int by, int zc) {
@@ -39,8 +41,10 @@ inline int64_t n_ctas(int nx, int ny, int nz, int bx, int by, int zc) {
 // Step-kernel variants: register-pipelined loads (any precision);
 // asynchronous copies through shared memory with 2 or 3 stages (FP32 only);
 // bulk copies of whole rows into shared memory (FP32 arithmetic, FP32 or
-// FP16 storage; rows of nx <= bx values, nx values a multiple of 16 bytes).
-enum { kVarRegs = 1, kVarAsync2 = 2, kVarAsync3 = 3, kVarBulk = 4 };
+// FP16 storage; rows of nx <= bx values, nx values a multiple of 16 bytes);
+// bulk copies of padded strip-row segments (FP32 arithmetic, FP32 or FP16
+// storage; nx a multiple of bx and at least two strips).
+enum { kVarRegs = 1, kVarAsync2 = 2, kVarAsync3 = 3, kVarBulk = 4, kVarStrip = 5 };
 
 // sbytes: bytes of a stored population (8 FP64, 4 FP32, 2 FP16).
 inline bool variant_ok(int variant, int sbytes, int bx, int by, int nx) {
@@ -50,6 +54,8 @@ inline bool variant_ok(int variant, int sbytes, int bx, int by, int nx) {
   if (variant == kVarBulk)
     return sbytes != 8 && tile_bulk_ok(bx, by) && nx <= bx && (nx * sbytes) % 16 == 0 &&
            (nx * 4) % 16 == 0;
+  if (variant == kVarStrip)
+    return sbytes != 8 && tile_strip_ok(bx, by) && nx % bx == 0 && nx >= 2 * bx;
   return false;
 }
 

@@ -437,7 +437,7 @@ int lbm3_set_tiling(lbm3_handle* h, int32_t bx, int32_t by, int32_t zc) {
 
 int lbm3_set_kernel(lbm3_handle* h, int32_t variant) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
-  if (variant < 0 || variant > lbmk3::kVarBulk) return fail(LBM_ERR_ARG, "variant in [0, 4]");
+  if (variant < 0 || variant > lbmk3::kVarStrip) return fail(LBM_ERR_ARG, "variant in [0, 5]");
   const int sb = (int)selem(h->prm.precision), nx = h->prm.nx;
   int bx = h->bx, by = h->by;
   const int v = variant ? variant : lbmk3::kVarRegs;
@@ -445,6 +445,12 @@ int lbm3_set_kernel(lbm3_handle* h, int32_t variant) {
     // the bulk-copy kernel runs its own tiles only: take the one for nx
     bx = nx <= 128 ? 128 : 256;
     by = nx <= 128 ? 4 : 2;
+  }
+  if (v == lbmk3::kVarStrip && !(lbmk3::tile_strip_ok(bx, by) && nx % bx == 0 && nx >= 2 * bx)) {
+    // the strip kernel runs its own tiles only: 64 x 4 where nx allows, else 32 x 8
+    const bool wide = nx % 64 == 0 && nx >= 128;
+    bx = wide ? 64 : 32;
+    by = wide ? 4 : 8;
   }
   if (!lbmk3::variant_ok(v, sb, bx, by, nx))
     return fail(LBM_ERR_ARG, "variant not available for this precision or box");
@@ -474,7 +480,7 @@ int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* ovar, int32_t* obx, i
   int bv = kv, bb = kb, bby = kby, bz = kz;
   int rc = LBM_OK;
   const int tiles[6][2] = {{32, 4}, {32, 8}, {32, 16}, {64, 4}, {128, 4}, {256, 2}};
-  for (int v = lbmk3::kVarRegs; v <= lbmk3::kVarBulk && rc == LBM_OK; ++v) {
+  for (int v = lbmk3::kVarRegs; v <= lbmk3::kVarStrip && rc == LBM_OK; ++v) {
     if (h->variant_req && v != h->variant_req) continue;
     for (const auto& tl : tiles) {
       if (!lbmk3::variant_ok(v, sb, tl[0], tl[1], nx)) continue;

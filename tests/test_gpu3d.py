@@ -169,6 +169,55 @@ def test_bulk_row_variant(L3, prec, shape, tiling):
     assert md(a.fields()[0], o.fields()[0]) <= (1e-5 if prec == "f32" else 2e-3)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+@pytest.mark.parametrize("shape,tiling", [((64, 21, 20), (32, 8, 8)),
+                                          ((128, 10, 13), (64, 4, 8)),
+                                          ((192, 17, 9), (64, 4, 9)),
+                                          ((64, 3, 5), (32, 8, 5))])
+def test_strip_bulk_variant(L3, prec, shape, tiling):
+    # Strip-row bulk copies (variant 5): the same per-node arithmetic as the
+    # register kernel, so equal to it up to FMA contraction, and within the
+    # precision's bar of the oracle.  Several strips with periodic wrap pieces
+    # at x = 0 and x = nx, ragged row blocks and z chunks, and a box of two
+    # strips thinner than the rows a CTA touches (ny = 3).
+    nx, ny, nz = shape
+    case, phi0, u0 = two_phase(nx, ny, nz, rho_l=3.0, tau_f_l=0.7)
+    a = L3.Sim3(case, phi0, u0, precision=prec)
+    a.set_tiling(*tiling)
+    a.set_kernel(5)
+    assert a.kernel() == 5 and a.tiling()[:3] == tiling
+    b = L3.Sim3(case, phi0, u0, precision=prec)
+    b.set_kernel(1)
+    tr = a.track_volume(True)
+    a.step(100)
+    b.step(100)
+    assert a.status() == 0 and b.status() == 0
+    fa, fb = a.get_state(), b.get_state()
+    tol = 2e-6 if prec == "f32" else 2e-3
+    for x, y in zip(fa[:3], fb[:3]):
+        assert md(x, y) <= tol
+    o = oracle.Oracle3(case, phi0, u0).step(99)
+    assert abs(float(tr.cpu().numpy()[0]) / o.volume()[0] - 1) < (1e-6 if prec == "f32" else 1e-5)
+    o.step(1)
+    assert md(a.fields()[0], o.fields()[0]) <= (1e-5 if prec == "f32" else 2e-3)
+
+
+def test_strip_variant_rejected_where_unavailable(L3):
+    case, phi0, u0 = two_phase(64, 8, 8)
+    s = L3.Sim3(case, phi0, u0, precision="f64")
+    with pytest.raises(L3.LbmError):
+        s.set_kernel(5)
+    case, phi0, u0 = two_phase(40, 8, 8)  # nx not a multiple of the strip width
+    t = L3.Sim3(case, phi0, u0, precision="f16")
+    with pytest.raises(L3.LbmError):
+        t.set_kernel(5)
+    t.set_kernel(0)
+    case, phi0, u0 = two_phase(32, 8, 8)  # one strip: both pads would wrap
+    t = L3.Sim3(case, phi0, u0, precision="f32")
+    with pytest.raises(L3.LbmError):
+        t.set_kernel(5)
+
+
 def test_bulk_row_variant_rejected_where_unavailable(L3):
     case, phi0, u0 = two_phase(40, 24, 20)
     s = L3.Sim3(case, phi0, u0, precision="f64")
