@@ -118,9 +118,9 @@ int64_t lbm3_time(const lbm3_handle* h);
 /* Tiling of the step kernel: CTA tile bx x by columns, marching zc planes.
  * Allowed (bx, by): (32, 4), (32, 8), (32, 16), (64, 4) for variants 1-3;
  * (128, 4) and (256, 2) -- whole rows, nx <= bx -- for variant 4; (32, 8)
- * and (64, 4) with nx a multiple of bx and nx >= 2 bx for variant 5.  Setting a
- * tile that the variant in use does not run switches to the variant made
- * for it (LBM_ERR_ARG if none runs it, or if a variant was requested with
+ * and (64, 4) with nx a multiple of bx and nx >= 2 bx for variant 5.
+ * Setting a tile that the variant in use does not run switches to the
+ * variant made for it (LBM_ERR_ARG if none runs it, or if a variant was requested with
  * lbm3_set_kernel and does not run it).  8 <= zc <= nz (or zc = nz when
  * nz < 8).  Every tiling gives the same values up to floating-point
  * contraction (see lbm_set_tiling).  n_ctas: CTAs per step. */
@@ -129,8 +129,9 @@ int lbm3_get_tiling(const lbm3_handle* h, int32_t* bx, int32_t* by, int32_t* zc,
                     int32_t* n_ctas);
 
 /* Step-kernel variant: 0 = automatic (the register kernel until
- * lbm3_autotune picks the fastest), 1 = register-pipelined loads (any
- * precision and tiling), 2 / 3 = asynchronous 4-byte copies (cp.async)
+ * lbm3_autotune picks the fastest; on a tile the register kernel does not
+ * run, with the default tile (32, 8)), 1 = register-pipelined loads (any
+ * precision; tiles of variants 1-3, others switch to (32, 8)), 2 / 3 = asynchronous 4-byte copies (cp.async)
  * through shared memory, 2 / 3 stages deep (LBM3_F32 only; tiles (32, 4),
  * (32, 8), (64, 4)), 4 = bulk copies (cp.async.bulk) of whole x-rows into
  * shared memory, one or two planes ahead (LBM3_F32 and LBM3_F16; nx <= 256,

@@ -32,7 +32,9 @@ inline bool tile_regs_ok(int bx, int by) {
 inline bool tile_bulk_ok(int bx, int by) { return (bx == 128 && by == 4) || (bx == 256 && by == 2); }
 // Tiles of the strip bulk-copy kernel (nx a multiple of bx, nx >= 2 bx).
 inline bool tile_strip_ok(int bx, int by) { return (bx == 32 && by == 8) || (bx == 64 && by == 4); }
-inline bool tile_ok(int bx, int by) { return tile_regs_ok(bx, by) || tile_bulk_ok(bx, by); }
+inline bool tile_ok(int bx, int by) {
+  return tile_regs_ok(bx, by) || tile_bulk_ok(bx, by) || tile_strip_ok(bx, by);
+}
 
 inline int64_t n_ctas(int nx, int ny, int nz, int bx, int by, int zc) {
   return (int64_t)((nx + bx - 1) / bx) * ((ny + by - 1) / by) * ((nz + zc - 1) / zc);

@@ -426,7 +426,9 @@ int lbm3_set_tiling(lbm3_handle* h, int32_t bx, int32_t by, int32_t zc) {
   // keep the variant in use if it runs this tile, else the one made for it
   int v = h->variant;
   if (!lbmk3::variant_ok(v, sb, bx, by, nx))
-    v = lbmk3::tile_bulk_ok(bx, by) ? lbmk3::kVarBulk : lbmk3::kVarRegs;
+    v = lbmk3::tile_bulk_ok(bx, by)   ? lbmk3::kVarBulk
+        : lbmk3::tile_regs_ok(bx, by) ? lbmk3::kVarRegs
+                                      : lbmk3::kVarStrip;
   if (!lbmk3::variant_ok(v, sb, bx, by, nx))
     return fail(LBM_ERR_ARG, "tiling not available for this box or precision");
   h->bx = bx, h->by = by, h->zc = zc;
@@ -441,6 +443,11 @@ int lbm3_set_kernel(lbm3_handle* h, int32_t variant) {
   const int sb = (int)selem(h->prm.precision), nx = h->prm.nx;
   int bx = h->bx, by = h->by;
   const int v = variant ? variant : lbmk3::kVarRegs;
+  if (v == lbmk3::kVarRegs && !lbmk3::tile_regs_ok(bx, by)) {
+    // automatic or register kernel on a tile it does not run: the default tile
+    bx = 32;
+    by = 8;
+  }
   if (v == lbmk3::kVarBulk && !lbmk3::tile_bulk_ok(bx, by)) {
     // the bulk-copy kernel runs its own tiles only: take the one for nx
     bx = nx <= 128 ? 128 : 256;

@@ -1,8 +1,8 @@
 // Strip-tiled bulk-copy variant of the three-dimensional step kernel (FP32
 // arithmetic, FP32 or FP16 population storage) for boxes whose nx is a
-// multiple of the strip width BX and at least 2 BX.  Same per-node arithmetic as step3_kernel
-// (node3, the same stencils and phase-A sums); the difference is how the
-// pulled values reach the threads.
+// multiple of the strip width BX and at least 2 BX.  Same per-node
+// arithmetic as step3_kernel (node3, the same stencils and phase-A sums); the
+// difference is how the pulled values reach the threads.
 //
 // A CTA owns a BX x BY column tile (x0 .. x0+BX-1, y0 .. y0+BY-1) and marches
 // along z over `zc` planes, like step3_kernel, so several CTAs share an SM.
@@ -69,7 +69,6 @@ struct StripShape {
   static_assert(STAGE_BYTES % 16 == 0 && GM_OFF % 16 == 0 && J_OFF % 16 == 0 &&
                     G0_OFF % 16 == 0 && (WS * sizeof(S)) % 16 == 0 && (WT * sizeof(T)) % 16 == 0,
                 "stage regions and rows must keep 16-byte alignment");
-  static_assert(NH <= BX * BY, "tile too small for its halo");
 };
 
 template <typename T, typename S, int BX, int BY, int NST>
@@ -232,20 +231,20 @@ __global__ void __launch_bounds__(BX* BY, MINB)
     ring[slot][r][xl + 1] = v;
   };
 
-  // halo slot of this thread (tile coordinates -1..BX, -1..BY), as in step3_kernel
-  int hx = 0, hy = 0;
-  const bool has_h = tid < SH::NH;
-  if (has_h) {
-    if (tid < RW) {
-      hx = tid - 1, hy = -1;
-    } else if (tid < 2 * RW) {
-      hx = tid - RW - 1, hy = BY;
-    } else if (tid < 2 * RW + BY) {
-      hx = -1, hy = tid - 2 * RW;
+  // Halo position h of the tile (tile coordinates -1..BX, -1..BY): the rows
+  // above and below, then the columns left and right.  Thread tid takes
+  // positions tid, tid + NT, ... (one at most where NH <= NT).
+  auto halo_xy = [&](int h, int& hx, int& hy) {
+    if (h < RW) {
+      hx = h - 1, hy = -1;
+    } else if (h < 2 * RW) {
+      hx = h - RW - 1, hy = BY;
+    } else if (h < 2 * RW + BY) {
+      hx = -1, hy = h - 2 * RW;
     } else {
-      hx = BX, hy = tid - 2 * RW - BY;
+      hx = BX, hy = h - 2 * RW - BY;
     }
-  }
+  };
 
   for (int k = 0; k < NST - 1 && k < nplanes; ++k) issue(k);
   int issued_last = min(NST - 1, nplanes) - 1;
@@ -255,9 +254,8 @@ __global__ void __launch_bounds__(BX* BY, MINB)
   T Gc[7], Gn[7], Gcl = T(0), Gnl = T(0);
   {
     const uint32_t nxy = (uint32_t)nx * (uint32_t)ny;
-    Offs own, hal;
+    Offs own;
     set_xy(own, x0 + tx, wrapy(y0 + ty), nx, ny);
-    if (has_h) set_xy(hal, (x0 + hx + nx) % nx, wrapy(y0 + hy), nx, ny);
     for (int q = 0; q < 2; ++q) {
       const int zl = wrapz(zb - 1 + q);
       set_z(own, zl, nz, nxy);
@@ -267,7 +265,11 @@ __global__ void __launch_bounds__(BX* BY, MINB)
 #pragma unroll
       for (int i = 0; i < 7; ++i) (q == 0 ? Gn : Gc)[i] = G[i];
       (q == 0 ? Gnl : Gcl) = gl;
-      if (has_h) {
+      for (int h = tid; h < SH::NH; h += NT) {
+        int hx, hy;
+        halo_xy(h, hx, hy);
+        Offs hal;
+        set_xy(hal, (x0 + hx + nx) % nx, wrapy(y0 + hy), nx, ny);
         set_z(hal, zl, nz, nxy);
         pull_g(g0s, g0ls, gms, P, hal, G, gl);
         put((zb - 1 + q) & 3, hy + 1, hx, G, gl);
@@ -286,7 +288,9 @@ __global__ void __launch_bounds__(BX* BY, MINB)
       // phase A of plane z + 1 from the staged g rows
       staged_g(st, ty + 1, tx, Gn, Gnl);
       put((z + 1) & 3, ty + 1, tx, Gn, Gnl);
-      if (has_h) {
+      for (int h = tid; h < SH::NH; h += NT) {
+        int hx, hy;
+        halo_xy(h, hx, hy);
         T H[7], hl;
         staged_g(st, hy + 1, hx, H, hl);
         put((z + 1) & 3, hy + 1, hx, H, hl);

@@ -216,6 +216,18 @@ def test_strip_variant_rejected_where_unavailable(L3):
     t = L3.Sim3(case, phi0, u0, precision="f32")
     with pytest.raises(L3.LbmError):
         t.set_kernel(5)
+    # automatic selection keeps a tile the register kernel runs, and leaves a
+    # tile only the whole-row kernel runs for the default tile
+    case, phi0, u0 = two_phase(128, 8, 8)
+    u = L3.Sim3(case, phi0, u0, precision="f32")
+    u.set_tiling(64, 4, 8)
+    u.set_kernel(5)
+    u.set_kernel(0)
+    assert u.kernel() == 1 and u.tiling()[:2] == (64, 4)
+    u.set_tiling(128, 4, 8)
+    assert u.kernel() == 4
+    u.set_kernel(0)
+    assert u.kernel() == 1 and u.tiling()[:2] == (32, 8)
 
 
 def test_bulk_row_variant_rejected_where_unavailable(L3):
