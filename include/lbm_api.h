@@ -124,6 +124,10 @@ size_t lbm_workspace_bytes(const lbm_params* cases, int32_t ncases);
  *   f = f_eq(p = 0, rho(phi0), u0) (Eq. 22); phi*u at t-1 := phi0 u0.
  * rho(phi) = rho_g + phi (rho_l - rho_g) and mu(phi) linear likewise;
  * tau_f(x) = mu/(rho c_s^2) + 1/2 (Eq. 27).  In vortex mode u0 is ignored.
+ * The arrays may lie in pageable host memory (copied through the workspace's
+ * staging planes), or in page-locked host or device memory (read in place by
+ * the init kernel).  The call synchronises the stream: on return no array
+ * is read any more.
  * d_workspace: device pointer, >= lbm_workspace_bytes(), 256-byte aligned.
  * stream: a cudaStream_t (NULL = legacy default stream).
  * Errors: LBM_ERR_ARG, LBM_ERR_WORKSPACE, LBM_ERR_CUDA. */

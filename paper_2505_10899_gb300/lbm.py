@@ -181,14 +181,26 @@ def lbm_workspace_bytes(params) -> int:
     return int(_lib.lbm_workspace_bytes(arr, len(params)))
 
 
+def _init_ptr(a):
+    """An initial field for lbm_init: a host array (FP64, [ny][nx] or
+    [2][ny][nx]), or an int, the address of such an array in device or
+    page-locked host memory that the caller keeps alive until lbm_init
+    returns."""
+    if isinstance(a, (int, np.integer)):
+        return ctypes.cast(ctypes.c_void_p(int(a)), _D)
+    return _dp(np.ascontiguousarray(a, dtype=np.float64))
+
+
 def lbm_init(params, d_workspace: int, ws_bytes: int, phi0s, u0s=None, stream: int = 0):
     n = len(params)
     arr = (lbm_params * n)(*params)
-    phis = [np.ascontiguousarray(p, dtype=np.float64) for p in phi0s]
-    us = [None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+    phis = [p if isinstance(p, (int, np.integer)) else np.ascontiguousarray(p, dtype=np.float64)
+            for p in phi0s]
+    us = [None if u is None else (u if isinstance(u, (int, np.integer))
+                                  else np.ascontiguousarray(u, dtype=np.float64))
           for u in (u0s if u0s is not None else [None] * n)]
-    phi_ptrs = (_D * n)(*[_dp(p) for p in phis])
-    u_ptrs = (_D * n)(*[_dp(u) if u is not None else _D() for u in us])
+    phi_ptrs = (_D * n)(*[_init_ptr(p) for p in phis])
+    u_ptrs = (_D * n)(*[_init_ptr(u) if u is not None else _D() for u in us])
     h = _H()
     _check(_lib.lbm_init(arr, n, ctypes.c_void_p(d_workspace), ws_bytes, phi_ptrs, u_ptrs,
                          ctypes.c_void_p(stream), ctypes.byref(h)), "lbm_init")
