@@ -192,14 +192,15 @@ __global__ void ad_phase(const R* __restrict__ gA, int64_t P, int nx, int ny, in
 // order over a fixed grid), so the slots accumulate over the adjoint steps in
 // a fixed order without atomics, and one final sum over the CTAs (at
 // take_grads) gives the same bits on every run.
+template <typename A>
 __device__ __forceinline__ void ad_block_partials(double (&red)[kAdThreads / 32][kNParam],
-                                                  const double (&gacc)[kNParam],
+                                                  const A (&gacc)[kNParam],
                                                   double* __restrict__ part) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int q = 0; q < kNParam; ++q) {
-    double v = gacc[q];
+    A v = gacc[q];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[warp][q] = v;
+    if (lane == 0) red[warp][q] = (double)v;
   }
   __syncthreads();
   if (threadIdx.x < kNParam) {
@@ -219,7 +220,13 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
   const int nx = a.nx, ny = a.ny;
   const int64_t n = (int64_t)nx * ny, P = a.P;
   const Phys<R>& ph = a.ph;
-  double gacc[kNParam] = {0, 0, 0, 0, 0, 0, 0};
+  // Parameter terms: each thread sums its nodes' terms and each warp its
+  // threads' sums in R; the warp sums enter the FP64 block and CTA partials.
+  // Under FP32 a 32-term FP32 partial adds rounding of the order of the
+  // terms' own FP32 arithmetic, and keeps the work off GB300's narrow FP64
+  // pipe (FP64 conversions and a double shuffle tree per node took two
+  // thirds of its cycles in this kernel).
+  R gacc[kNParam] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)n; k += gridDim.x * blockDim.x) {
     const int y = k / nx, x = k - y * nx;
     int src[9];
@@ -352,14 +359,14 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
       const R lgh = Vx * le.m3 + Vy * le.m5;
       const R ls = -lgs * R(1.0 / 6.0) - lgh * R(1.0 / 36.0);
       const R sg = R(-6) * ph.gsD[3];  // = 1/tau_g
-      gacc[3] += (double)(-sg * sg * ls);
+      gacc[3] += -sg * sg * ls;
     }
     // mg = M G
     lbmk::add_back(lG, lmg[0], lmg[1], lmg[2], lmg[3], lmg[4], lmg[5], lmg[6], lmg[7], lmg[8]);
     // Lam = mu + lambda phi
     lmu += lLam;
     lphi += ph.lambda * lLam;
-    gacc[2] += (double)(phi * lLam);
+    gacc[2] += phi * lLam;
     // V = 3 dJ + sh q
     const R ldJx = R(3) * lVx, ldJy = R(3) * lVy;
     const R lsh = qx * lVx + qy * lVy;
@@ -368,7 +375,7 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     // sh = lamW tfac ta tb iq
     const R c0 = ph.lamW * ph.tfac;
     const R lta = c0 * tb * iq * lsh, ltb = c0 * ta * iq * lsh, liq = c0 * ta * tb * lsh;
-    gacc[2] += (double)(ph.tfac * ta * tb * iq * lsh * a.invW);  // lamW = lambda / W
+    gacc[2] += ph.tfac * ta * tb * iq * lsh * a.invW;  // lamW = lambda / W
     if (q2 >= ph.qmin2) {  // below the threshold n = 0: no derivative
       const R lq2 = R(-0.5) * iq * iq * iq * liq;
       lqx += R(2) * qx * lq2;
@@ -443,7 +450,7 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
         lirho += R(3) * mu_v * ltau;
         lphi += a.dmu * lmuv;
       } else {
-        gacc[4] += (double)(-s7 * s7 * ls7);  // s7 = 1/tau_f
+        gacc[4] += -s7 * s7 * ls7;  // s7 = 1/tau_f
       }
       // jx = rho ux, jy = rho uy
       lrho += ux * ljx + uy * ljy;
@@ -479,12 +486,12 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
       if (wbot) {
         const R l = (lF[5] - lF[6]) * R(1.0 / 6.0);
         lrho += a.u_bot * l;
-        gacc[6] += (double)(rho * l);
+        gacc[6] += rho * l;
       }
       if (wtop) {
         const R l = (lF[8] - lF[7]) * R(1.0 / 6.0);
         lrho += a.u_top * l;
-        gacc[5] += (double)(rho * l);
+        gacc[5] += rho * l;
       }
       // irho = 1/rho, rho = rho_g + phi drho
       lrho += -irho * irho * lirho;
@@ -497,8 +504,8 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
     // mu = beta4 poly - kappa lap
     lphi += ph.beta4 * (R(3) * phi * phi - R(3) * phi + R(0.5)) * lmu;
     llap += -ph.kappa * lmu;
-    gacc[0] += (double)(poly * lmu);
-    gacc[1] += (double)(-lap * lmu);
+    gacc[0] += poly * lmu;
+    gacc[1] += -lap * lmu;
 
     // stencil adjoints (transpose of the difference forms above)
     const R gx3 = lgpx * R(1.0 / 3.0), gy3 = lgpy * R(1.0 / 3.0);
@@ -542,25 +549,33 @@ __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(co
 // ad_node reads them.  Each node reads its own phi before it overwrites it,
 // and no other node reads it in this launch, so the two share the planes.
 template <typename R>
-__global__ void ad_gather(R* __restrict__ phi, R* __restrict__ psi, const R* __restrict__ lP,
+__global__ void __launch_bounds__(kAdThreads, 4) ad_gather(R* __restrict__ phi, R* __restrict__ psi, const R* __restrict__ lP,
                           const R* __restrict__ lQ, int nx, int ny, int walls, R xi,
                           R* __restrict__ aout, const R* __restrict__ gB, int64_t PB) {
   const int64_t n = (int64_t)nx * ny;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < (int)n; k += gridDim.x * blockDim.x) {
     const int y = k / nx, x = k - y * nx;
+    // The adjoints of the node's 9 pulled g sit at 9 distinct positions (the
+    // pull is a bijection): read them all before any write, so that the
+    // reads need not wait for the writes of the same array.  Offsets are
+    // below 18 n < 2^32 (a case has at most 2.3e8 nodes).
+    uint32_t at[9];
+    R cur[9], G[9];
+    #pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      int pl;
+      const int pos = ad_src(i, x, y, nx, ny, walls, &pl);
+      at[i] = (uint32_t)(9 + pl) * (uint32_t)n + (uint32_t)pos;
+      cur[i] = aout[at[i]];
+      if (gB) G[i] = gB[pl * PB + pos];
+    }
     R sp = lP[k], sq = R(0);
     gather_uses(lP, lQ, x, y, nx, ny, walls, sp, sq);
     const R p = phi[k];
     const R dpsi = (p > R(0) && p < R(1)) ? dpsi_dphi(p, xi) : R(0);
     const R tot = sp + dpsi * sq;
-    R G[9];
     #pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      int pl;
-      const int pos = ad_src(i, x, y, nx, ny, walls, &pl);
-      aout[(9 + pl) * n + pos] += tot;
-      if (gB) G[i] = gB[pl * PB + pos];
-    }
+    for (int i = 0; i < 9; ++i) aout[at[i]] = cur[i] + tot;
     if (gB) {  // phi (Eq. 35) and psi (Eq. 37) of the next state, as ad_phase
       const R q = lbmk::sum9(G);
       phi[k] = q;
