@@ -1033,7 +1033,8 @@ def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
                "backward_over_plain_forward": round((t2 - t1) / plain_s, 3),
                f"plain_{prec}_forward_s": round(plain_s, 3),
                "adjoint_arithmetic": "fp64" if prec == "f64" else
-                                     "fp32 (parameter derivatives accumulated in fp64)"}
+                                     ("fp32 (parameter terms summed per warp in fp32, "
+                                      "then accumulated in fp64)")}
         if prec == "f32":
             ref = out["gradient_f64"]
             res["rel_diff_vs_f64_gradient"] = {

@@ -328,8 +328,8 @@ int lbm_record_steps(lbm_handle* h, int64_t count, void* d_states, int64_t strid
  * FP64 or FP32).  An adjoint state has the first 20 planes of the snapshot
  * layout above, in the handle's precision: the derivative of a scalar
  * objective with respect to each stored value.  An FP32 handle runs the
- * adjoint arithmetic in FP32 and accumulates the parameter derivatives in
- * FP64; it differentiates the FP32 step at its stored states (g_0 taken as
+ * adjoint arithmetic in FP32, sums the parameter terms of each warp in FP32
+ * and accumulates those sums in FP64; it differentiates the FP32 step at its stored states (g_0 taken as
  * the high part of its float pair, a difference of at most half an FP32 ulp
  * of g_0 in phi).
  *   lbm_adjoint_attach: device scratch of lbm_adjoint_workspace_bytes()

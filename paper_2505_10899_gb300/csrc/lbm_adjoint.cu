@@ -212,7 +212,7 @@ __device__ __forceinline__ void ad_block_partials(double (&red)[kAdThreads / 32]
 
 // The per-node reverse sweep.  R is the arithmetic and storage type of the
 // states and adjoints (the handle's precision); the parameter partials are
-// accumulated in FP64.
+// summed per thread and per warp in R and accumulated in FP64 above that.
 template <typename R>
 __global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(const AdArgs<R> a) {
   __shared__ double red[kAdThreads / 32][kNParam];
