@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--only-batching", action="store_true",
                     help="only the batched-vs-separate-handles comparison")
     ap.add_argument("--only-adjoint", action="store_true",
-                    help="print the reverse-mode timing only (profiling aid)")
+                    help="print the reverse-mode timings only (profiling aid)")
     return ap.parse_args()
 
 
@@ -485,6 +485,10 @@ def headline_ratios(ex):
         "batching", "speedup_vs_launch_per_case_per_step")
     out["batching_speedup_vs_graph_per_case"] = get("batching", "speedup_vs_graph_per_case")
     out["adjoint_step_over_forward"] = get("adjoint", "vjp_over_forward")
+    out["adjoint_step_over_forward_f32"] = get("adjoint_sweep_shear", "f32",
+                                               "adjoint_over_forward")
+    out["adjoint_step_over_forward_f64"] = get("adjoint_sweep_shear", "f64",
+                                               "adjoint_over_forward")
     out["adjoint_backward_over_forward_recorded"] = get(
         "adjoint", "backward_states_recorded", "backward_over_forward_step")
     out["gradient_over_forward_f64"] = get("shear_droplet", "gradient_f64",
@@ -683,6 +687,7 @@ def run_extras(args, cases, dev):
     out["batching"] = batching_timing(cases, dev)
     out["droplet_lattice_16384x8192"] = lattice_timing(dev)
     out["adjoint"] = adjoint_timing(dev)
+    out["adjoint_sweep_shear"] = adjoint_sweep_timing(dev)
     out["rayleigh_plateau_3d"] = rp3d_timing(dev, steps=args.steps3, peak64=out["fp64_peak"])
     out["shear_droplet"] = shear_timing(dev)
     return out
@@ -943,6 +948,55 @@ def adjoint_timing(dev, nx=512, ny=256, nsteps=32, ckpt=8):
             "backward_states_recomputed": res["recomputed"]}
 
 
+def adjoint_sweep_timing(dev, precisions=("f32", "f64"), nrec=256):
+    """Reverse-mode step against the forward step on the sheared droplet in
+    a 512 x 256 channel (walls at -U and +U = 0.01, R = 40, Ca = 0.1,
+    Re = 0.1), per precision: the forward step autotuned and replayed from
+    graphs, then lbm_record_steps of nrec states and one lbm_adjoint_sweep
+    over them (two launches per step), both timed with CUDA events."""
+    import torch
+    from paper_2505_10899_gb300 import adjoint as A
+    from paper_2505_10899_gb300 import lbm
+
+    case, phi0, u0 = W.shear_droplet(512, 256, R=40.0, U=0.01, Ca=0.1, Re=0.1)
+    out = {"grid": "512x256", "walls_u": 0.01, "steps": nrec}
+    for prec in precisions:
+        a = A.AdjointSim(case, phi0, u0, prec)
+        a.sim.autotune(1)
+        a.step(300)
+        st = a.sim.stream
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        a.step(nrec)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        fwd = e0.elapsed_time(e1) / nrec
+        rec = torch.empty((nrec, a.planes) + a.shape, dtype=a.dtype, device=a.dev)
+        stride = rec[0].numel() * rec.element_size()
+        lbm.lbm_record_steps(a.h, nrec, rec.data_ptr(), stride)
+        adj = a.seed_phi(torch.ones(a.shape, dtype=torch.float64))
+        spare = torch.empty_like(adj)
+        t0 = a.t - nrec
+        for _ in range(2):  # the first sweep loads the kernels; the second is timed
+            torch.cuda.synchronize(dev)
+            e0.record(st)
+            lbm.lbm_adjoint_sweep(a.h, rec.data_ptr(), stride, t0, nrec, adj.data_ptr(),
+                                  spare.data_ptr())
+            e1.record(st)
+            torch.cuda.synchronize(dev)
+        adj_ms = e0.elapsed_time(e1) / nrec
+        out[prec] = {"forward_us_per_step": round(fwd * 1e3, 2),
+                     "adjoint_us_per_step": round(adj_ms * 1e3, 2),
+                     "adjoint_over_forward": round(adj_ms / fwd, 3),
+                     "forward_kernel": a.sim.kernel(), "forward_tiling": list(a.sim.tiling()),
+                     "status": a.sim.status()}
+        a.close()
+        del rec, adj, spare
+        torch.cuda.empty_cache()
+    return out
+
+
 def shear_timing(dev, nsteps=20000, ckpt=256, grad_steps=20000):
     """The sheared droplet in a 512 x 256 channel (walls at -U and
     +U = 0.01, R = 40, W = 4, Ca = 0.1, Re = 0.1): FP32 forward MLUPS over
@@ -1133,7 +1187,9 @@ def main():
     args = parse()
     if args.only_adjoint:
         import torch
-        print(json.dumps({"adjoint": adjoint_timing(torch.device("cuda", 0))}), flush=True)
+        dev = torch.device("cuda", 0)
+        print(json.dumps({"adjoint": adjoint_timing(dev),
+                          "adjoint_sweep_shear": adjoint_sweep_timing(dev)}), flush=True)
         return
     if args.only_lattice:
         import torch
