@@ -151,6 +151,15 @@ int lbm3_get_tiling(const lbm3_handle* h, int32_t* bx, int32_t* by, int32_t* zc,
 int lbm3_set_kernel(lbm3_handle* h, int32_t variant);
 int32_t lbm3_get_kernel(const lbm3_handle* h);
 
+/* Bound of the device waits of the bulk-copy variants (4 and 5), in SM clock
+ * cycles: the waits for their staged planes.  A wait that gives up makes
+ * lbm3_status report LBM_ERR_TIMEOUT; the CTA first waits, with the default
+ * bound, for the copies it issued, then returns, and the step's results are
+ * not valid.  cycles < 0 restores the default, about 2 s (4e9 cycles); 0
+ * gives up at the first poll that finds the data missing (used to test the
+ * timeout path).  Variants 1-3 do not wait on data.  Errors: LBM_ERR_ARG. */
+int lbm3_set_wait_limit(lbm3_handle* h, int64_t cycles);
+
 /* Time every allowed (variant, bx, by) with a few zc choices (`trials`
  * launches each, CUDA events) and keep the fastest; with a variant set by
  * lbm3_set_kernel only that variant is tried.  Trial launches write only the

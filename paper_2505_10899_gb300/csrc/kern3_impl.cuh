@@ -33,6 +33,7 @@ static Args3<T, S> make_args(const Bufs& b, const Host3& h, int parity) {
   }
   a.wg = (T)h.wg, a.hg = (T)h.hg, a.wf = (T)h.wf, a.hf = (T)h.hf;
   a.rho_g = (T)h.rho_g, a.drho = (T)h.drho, a.mu_g = (T)h.mu_g, a.dmu = (T)h.dmu;
+  a.wait = h.wait_cycles;
   return a;
 }
 
@@ -78,7 +79,7 @@ static cudaError_t launch_bulk(const Args3<T, S>& a, cudaStream_t st) {
   }
   if (a.nx > BX) return cudaErrorInvalidValue;
   const dim3 grid(1, (a.ny + BY - 1) / BY, (a.nz + a.zc - 1) / a.zc);
-  step3_bulk_kernel<T, S, BX, BY, NST><<<grid, BX * BY, bytes, st>>>(a, lbmk::kWaitCycles);
+  step3_bulk_kernel<T, S, BX, BY, NST><<<grid, BX * BY, bytes, st>>>(a, a.wait);
   return cudaGetLastError();
 }
 
@@ -95,7 +96,7 @@ static cudaError_t launch_strip(const Args3<T, S>& a, cudaStream_t st) {
   }
   if (a.nx % BX != 0) return cudaErrorInvalidValue;
   const dim3 grid(a.nx / BX, (a.ny + BY - 1) / BY, (a.nz + a.zc - 1) / a.zc);
-  step3_strip_kernel<T, S, BX, BY, NST, MINB><<<grid, BX * BY, bytes, st>>>(a, lbmk::kWaitCycles);
+  step3_strip_kernel<T, S, BX, BY, NST, MINB><<<grid, BX * BY, bytes, st>>>(a, a.wait);
   return cudaGetLastError();
 }
 

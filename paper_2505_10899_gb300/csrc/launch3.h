@@ -6,6 +6,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "lbm3_layout.h"
+
 namespace lbmk3 {
 
 struct Bufs {
@@ -22,6 +24,7 @@ struct Host3 {
   int64_t plane;
   double beta4, kappa, lambda, lamW, xi, tfac, wg, hg, wf, hf, rho_g, drho, mu_g, dmu;
   double W;  // interface width (the threshold of the normal scales with it)
+  long long wait_cycles = lbmk::kWaitCycles;  // bound of the bulk-copy kernels' waits
 };
 
 // Tiles of the register-pipelined and asynchronous-copy kernels.

@@ -470,6 +470,13 @@ int lbm3_set_kernel(lbm3_handle* h, int32_t variant) {
 
 int32_t lbm3_get_kernel(const lbm3_handle* h) { return h ? h->variant : -1; }
 
+int lbm3_set_wait_limit(lbm3_handle* h, int64_t cycles) {
+  if (!h) return fail(LBM_ERR_ARG, "null handle");
+  h->hp.wait_cycles = cycles < 0 ? lbmk::kWaitCycles : (long long)cycles;
+  drop_graph(h);  // captured launches hold the old bound
+  return LBM_OK;
+}
+
 int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* ovar, int32_t* obx, int32_t* oby,
                   int32_t* ozc, double* best_ms) {
   lbmk::TraceRange trace("lbm3_autotune");

@@ -52,6 +52,7 @@ struct Args3 {
   double* vol_part;        // kModeStep: per-CTA FP64 sum of phi, or null
   double* out;             // kModeFields: FP64 field [z][y][x]
   int32_t out_which;       // kOut*
+  long long wait;          // bound of the bulk-copy kernels' waits, SM cycles (0: one poll)
 };
 
 }  // namespace lbmk3

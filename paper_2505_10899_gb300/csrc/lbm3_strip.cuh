@@ -16,8 +16,9 @@
 //     y0+BY of plane z+1 over the BX + 2 columns x0-1 .. x0+BX, for phase A
 //     (phi = sum g, Eq. 35; psi, Eq. 37) into a 4-plane ring of (phi, psi)
 //     from which the D3Q19 stencils of Sec. 3.2 are read.
-// A staged row starts one 16-byte chunk (E elements) left of x0 and ends one
-// chunk right of x0+BX-1, so that the pull's one-column shift and the halo
+// A staged row starts one 16-byte chunk (ES stored values, or ET values of
+// the arithmetic type for the g_0 rows) left of x0 and ends one chunk right
+// of x0+BX-1, so that the pull's one-column shift and the halo
 // columns are index offsets inside it; a segment copies only the chunks its
 // population reads (no left chunk for c_x = -1 rows of f, and so on).  Where a
 // segment crosses the periodic edge x = 0 or x = nx it is split there (nx is

@@ -50,6 +50,7 @@ for _name, (_args, _res) in {
     "lbm3_get_tiling": ([_H, _I32P, _I32P, _I32P, _I32P], ctypes.c_int),
     "lbm3_autotune": ([_H, ctypes.c_int32, _I32P, _I32P, _I32P, _I32P, _D], ctypes.c_int),
     "lbm3_set_kernel": ([_H, ctypes.c_int32], ctypes.c_int),
+    "lbm3_set_wait_limit": ([_H, ctypes.c_int64], ctypes.c_int),
     "lbm3_get_kernel": ([_H], ctypes.c_int32),
     "lbm3_status": ([_H], ctypes.c_int),
     "lbm3_destroy": ([_H], None),
@@ -176,6 +177,10 @@ def lbm3_set_kernel(h, variant: int):
     return _check(_lib.lbm3_set_kernel(h, int(variant)), "lbm3_set_kernel")
 
 
+def lbm3_set_wait_limit(h, cycles: int):
+    return _check(_lib.lbm3_set_wait_limit(h, int(cycles)), "lbm3_set_wait_limit")
+
+
 def lbm3_get_kernel(h) -> int:
     return int(_lib.lbm3_get_kernel(h))
 
@@ -257,6 +262,9 @@ class Sim3:
 
     def kernel(self):
         return lbm3_get_kernel(self.h)
+
+    def set_wait_limit(self, cycles):
+        lbm3_set_wait_limit(self.h, cycles)
 
     @property
     def t(self):
