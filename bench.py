@@ -853,7 +853,7 @@ def rp3d_timing(dev, grid=(256, 256, 1024), precisions=("f32", "f16", "f64"), st
         achieved = bpn * n / (ms * 1e-3) / 1e9
         var = {1: "step3_kernel", 2: "step3_async_kernel<2 stages>",
                3: "step3_async_kernel<3 stages>", 4: "step3_bulk_kernel",
-               5: "step3_strip_kernel"}[s.kernel()]
+               5: "step3_strip_kernel", 6: "step3_strip_kernel (two stages, 3-5 CTAs per SM)"}[s.kernel()]
         out[prec] = {
             "mlups": round(n / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 4),
             "steps": K, "kernel": var, "tiling": dict(zip(("bx", "by", "zc", "ctas"), s.tiling())),

@@ -118,9 +118,10 @@ int64_t lbm3_time(const lbm3_handle* h);
 /* Tiling of the step kernel: CTA tile bx x by columns, marching zc planes.
  * Allowed (bx, by): (32, 4), (32, 8), (32, 16), (64, 4) for variants 1-3;
  * (128, 4) and (256, 2) -- whole rows, nx <= bx -- for variant 4; (32, 8)
- * and (64, 4) with nx a multiple of bx and nx >= 2 bx for variant 5.
- * Setting a tile that the variant in use does not run switches to the
- * variant made for it (LBM_ERR_ARG if none runs it, or if a variant was requested with
+ * and (64, 4) with nx a multiple of bx and nx >= 2 bx for variant 5; (64, 4)
+ * and (64, 2), with the same conditions, for variant 6.  Setting a tile
+ * that the variant in use does not run switches to the variant made for it
+ * (LBM_ERR_ARG if none runs it, or if a variant was requested with
  * lbm3_set_kernel and does not run it).  8 <= zc <= nz (or zc = nz when
  * nz < 8).  Every tiling gives the same values up to floating-point
  * contraction (see lbm_set_tiling).  n_ctas: CTAs per step. */
@@ -128,30 +129,38 @@ int lbm3_set_tiling(lbm3_handle* h, int32_t bx, int32_t by, int32_t zc);
 int lbm3_get_tiling(const lbm3_handle* h, int32_t* bx, int32_t* by, int32_t* zc,
                     int32_t* n_ctas);
 
-/* Step-kernel variant: 0 = automatic (the register kernel until
- * lbm3_autotune picks the fastest; on a tile the register kernel does not
- * run, with the default tile (32, 8)), 1 = register-pipelined loads (any
- * precision; tiles of variants 1-3, others switch to (32, 8)), 2 / 3 = asynchronous 4-byte copies (cp.async)
- * through shared memory, 2 / 3 stages deep (LBM3_F32 only; tiles (32, 4),
- * (32, 8), (64, 4)), 4 = bulk copies (cp.async.bulk) of whole x-rows into
- * shared memory, one or two planes ahead (LBM3_F32 and LBM3_F16; nx <= 256,
- * a row of nx stored values and of nx FP32 values a multiple of 16 bytes;
- * tiles (128, 4) for nx <= 128, (256, 2); selecting it on another tile takes
- * its own tile), 5 = bulk copies of padded row segments of a bx-column strip
- * (one 16-byte chunk each side for the pull's shift and the halo column;
- * split where they cross the periodic edge) into shared memory, two (FP32)
- * or three (FP16) stages deep, two CTAs per SM (LBM3_F32 and LBM3_F16;
- * nx a multiple of bx and nx >= 2 bx; tiles (32, 8), (64, 4); selecting it
- * on another tile takes (64, 4) where nx allows, else (32, 8)).  Other variants on a tile they do not run:
- * LBM_ERR_ARG.  All variants run the same per-node arithmetic.  Every
- * wait of variants 4 and 5 is bounded: on expiry the step is abandoned and
+/* Step-kernel variant.  All variants run the same per-node arithmetic.
+ *   0: automatic -- the register kernel until lbm3_autotune picks the
+ *      fastest (on a tile the register kernel does not run, with the
+ *      default tile (32, 8));
+ *   1: register-pipelined loads (any precision; tiles of variants 1-3,
+ *      others switch to (32, 8));
+ *   2 / 3: asynchronous 4-byte copies (cp.async) through shared memory,
+ *      2 / 3 stages deep (LBM3_F32 only; tiles (32, 4), (32, 8), (64, 4));
+ *   4: bulk copies (cp.async.bulk) of whole x-rows into shared memory, one
+ *      or two planes ahead (LBM3_F32 and LBM3_F16; nx <= 256, a row of nx
+ *      stored values and of nx FP32 values a multiple of 16 bytes; tiles
+ *      (128, 4) for nx <= 128, (256, 2); selecting it on another tile takes
+ *      its own tile);
+ *   5: bulk copies of padded row segments of a bx-column strip (one 16-byte
+ *      chunk each side for the pull's shift and the halo column; split where
+ *      they cross the periodic edge), two (FP32) or three (FP16) stages
+ *      deep, two CTAs per SM (LBM3_F32 and LBM3_F16; nx a multiple of bx and
+ *      nx >= 2 bx; tiles (32, 8), (64, 4); selecting it on another tile takes
+ *      (64, 4) where nx allows, else (32, 8));
+ *   6: the strip kernel of 5 with two stages and three (64, 4) or five
+ *      (64, 2) CTAs per SM at fewer registers: more warps, less look-ahead
+ *      (same precisions and box conditions; selecting it on another tile
+ *      takes (64, 4)).
+ * Other variants on a tile they do not run: LBM_ERR_ARG.  Every wait of
+ * variants 4 to 6 is bounded: on expiry the step is abandoned and
  * lbm3_status reports LBM_ERR_TIMEOUT.  lbm3_get_kernel returns the variant
- * in use (1 to 5).  Errors: LBM_ERR_ARG (variant outside [0, 5], or not
+ * in use (1 to 6).  Errors: LBM_ERR_ARG (variant outside [0, 6], or not
  * available for this precision or box). */
 int lbm3_set_kernel(lbm3_handle* h, int32_t variant);
 int32_t lbm3_get_kernel(const lbm3_handle* h);
 
-/* Bound of the device waits of the bulk-copy variants (4 and 5), in SM clock
+/* Bound of the device waits of the bulk-copy variants (4 to 6), in SM clock
  * cycles: the waits for their staged planes.  A wait that gives up makes
  * lbm3_status report LBM_ERR_TIMEOUT; the CTA first waits, with the default
  * bound, for the copies it issued, then returns, and the step's results are

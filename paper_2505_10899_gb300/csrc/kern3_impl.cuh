@@ -119,6 +119,13 @@ static cudaError_t step_async(const Args3<T, S>& a, int variant, int bx, int by,
       if (bx == 64 && by == 4) return launch_strip<T, S, 64, 4, NST, 2>(a, st);
       return cudaErrorInvalidValue;
     }
+    if (variant == kVarStripOcc) {
+      // two stages per CTA and at most 80 (64 x 4) or 96 (64 x 2) registers:
+      // three or five CTAs per SM where shared memory allows (FP16 storage)
+      if (bx == 64 && by == 4) return launch_strip<T, S, 64, 4, 2, 3>(a, st);
+      if (bx == 64 && by == 2) return launch_strip<T, S, 64, 2, 2, 5>(a, st);
+      return cudaErrorInvalidValue;
+    }
   }
   if constexpr (std::is_same<T, float>::value && std::is_same<S, float>::value) {
     if (variant == kVarAsync2) {

@@ -35,8 +35,11 @@ inline bool tile_regs_ok(int bx, int by) {
 inline bool tile_bulk_ok(int bx, int by) { return (bx == 128 && by == 4) || (bx == 256 && by == 2); }
 // Tiles of the strip bulk-copy kernel (nx a multiple of bx, nx >= 2 bx).
 inline bool tile_strip_ok(int bx, int by) { return (bx == 32 && by == 8) || (bx == 64 && by == 4); }
+// Tiles of the strip kernel's occupancy form (two stages, more CTAs per SM).
+inline bool tile_strip_occ_ok(int bx, int by) { return bx == 64 && (by == 4 || by == 2); }
 inline bool tile_ok(int bx, int by) {
-  return tile_regs_ok(bx, by) || tile_bulk_ok(bx, by) || tile_strip_ok(bx, by);
+  return tile_regs_ok(bx, by) || tile_bulk_ok(bx, by) || tile_strip_ok(bx, by) ||
+         tile_strip_occ_ok(bx, by);
 }
 
 inline int64_t n_ctas(int nx, int ny, int nz, int bx, int by, int zc) {
@@ -48,8 +51,11 @@ inline int64_t n_ctas(int nx, int ny, int nz, int bx, int by, int zc) {
 // bulk copies of whole rows into shared memory (FP32 arithmetic, FP32 or
 // FP16 storage; rows of nx <= bx values, nx values a multiple of 16 bytes);
 // bulk copies of padded strip-row segments (FP32 arithmetic, FP32 or FP16
-// storage; nx a multiple of bx and at least two strips).
-enum { kVarRegs = 1, kVarAsync2 = 2, kVarAsync3 = 3, kVarBulk = 4, kVarStrip = 5 };
+// storage; nx a multiple of bx and at least two strips), with two or three
+// stages and two CTAs per SM (5), or two stages and three (64 x 4) or five
+// (64 x 2) CTAs per SM at fewer registers (6).
+enum { kVarRegs = 1, kVarAsync2 = 2, kVarAsync3 = 3, kVarBulk = 4, kVarStrip = 5,
+       kVarStripOcc = 6 };
 
 // sbytes: bytes of a stored population (8 FP64, 4 FP32, 2 FP16).
 inline bool variant_ok(int variant, int sbytes, int bx, int by, int nx) {
@@ -61,6 +67,8 @@ inline bool variant_ok(int variant, int sbytes, int bx, int by, int nx) {
            (nx * 4) % 16 == 0;
   if (variant == kVarStrip)
     return sbytes != 8 && tile_strip_ok(bx, by) && nx % bx == 0 && nx >= 2 * bx;
+  if (variant == kVarStripOcc)
+    return sbytes != 8 && tile_strip_occ_ok(bx, by) && nx % bx == 0 && nx >= 2 * bx;
   return false;
 }
 

@@ -426,9 +426,10 @@ int lbm3_set_tiling(lbm3_handle* h, int32_t bx, int32_t by, int32_t zc) {
   // keep the variant in use if it runs this tile, else the one made for it
   int v = h->variant;
   if (!lbmk3::variant_ok(v, sb, bx, by, nx))
-    v = lbmk3::tile_bulk_ok(bx, by)   ? lbmk3::kVarBulk
-        : lbmk3::tile_regs_ok(bx, by) ? lbmk3::kVarRegs
-                                      : lbmk3::kVarStrip;
+    v = lbmk3::tile_bulk_ok(bx, by)    ? lbmk3::kVarBulk
+        : lbmk3::tile_regs_ok(bx, by)  ? lbmk3::kVarRegs
+        : lbmk3::tile_strip_ok(bx, by) ? lbmk3::kVarStrip
+                                       : lbmk3::kVarStripOcc;
   if (!lbmk3::variant_ok(v, sb, bx, by, nx))
     return fail(LBM_ERR_ARG, "tiling not available for this box or precision");
   h->bx = bx, h->by = by, h->zc = zc;
@@ -439,7 +440,7 @@ int lbm3_set_tiling(lbm3_handle* h, int32_t bx, int32_t by, int32_t zc) {
 
 int lbm3_set_kernel(lbm3_handle* h, int32_t variant) {
   if (!h) return fail(LBM_ERR_ARG, "null handle");
-  if (variant < 0 || variant > lbmk3::kVarStrip) return fail(LBM_ERR_ARG, "variant in [0, 5]");
+  if (variant < 0 || variant > lbmk3::kVarStripOcc) return fail(LBM_ERR_ARG, "variant in [0, 6]");
   const int sb = (int)selem(h->prm.precision), nx = h->prm.nx;
   int bx = h->bx, by = h->by;
   const int v = variant ? variant : lbmk3::kVarRegs;
@@ -458,6 +459,10 @@ int lbm3_set_kernel(lbm3_handle* h, int32_t variant) {
     const bool wide = nx % 64 == 0 && nx >= 128;
     bx = wide ? 64 : 32;
     by = wide ? 4 : 8;
+  }
+  if (v == lbmk3::kVarStripOcc && !lbmk3::tile_strip_occ_ok(bx, by)) {
+    bx = 64;  // the occupancy form runs 64-column tiles only
+    by = 4;
   }
   if (!lbmk3::variant_ok(v, sb, bx, by, nx))
     return fail(LBM_ERR_ARG, "variant not available for this precision or box");
@@ -493,8 +498,8 @@ int lbm3_autotune(lbm3_handle* h, int32_t trials, int32_t* ovar, int32_t* obx, i
   double best = 1e300;
   int bv = kv, bb = kb, bby = kby, bz = kz;
   int rc = LBM_OK;
-  const int tiles[6][2] = {{32, 4}, {32, 8}, {32, 16}, {64, 4}, {128, 4}, {256, 2}};
-  for (int v = lbmk3::kVarRegs; v <= lbmk3::kVarStrip && rc == LBM_OK; ++v) {
+  const int tiles[7][2] = {{32, 4}, {32, 8}, {32, 16}, {64, 4}, {128, 4}, {256, 2}, {64, 2}};
+  for (int v = lbmk3::kVarRegs; v <= lbmk3::kVarStripOcc && rc == LBM_OK; ++v) {
     if (h->variant_req && v != h->variant_req) continue;
     for (const auto& tl : tiles) {
       if (!lbmk3::variant_ok(v, sb, tl[0], tl[1], nx)) continue;

@@ -170,12 +170,16 @@ def test_bulk_row_variant(L3, prec, shape, tiling):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f16"])
-@pytest.mark.parametrize("shape,tiling", [((64, 21, 20), (32, 8, 8)),
-                                          ((128, 10, 13), (64, 4, 8)),
-                                          ((192, 17, 9), (64, 4, 9)),
-                                          ((64, 3, 5), (32, 8, 5))])
-def test_strip_bulk_variant(L3, prec, shape, tiling):
-    # Strip-row bulk copies (variant 5): the same per-node arithmetic as the
+@pytest.mark.parametrize("variant,shape,tiling", [(5, (64, 21, 20), (32, 8, 8)),
+                                                  (5, (128, 10, 13), (64, 4, 8)),
+                                                  (5, (192, 17, 9), (64, 4, 9)),
+                                                  (5, (64, 3, 5), (32, 8, 5)),
+                                                  (6, (128, 21, 20), (64, 4, 8)),
+                                                  (6, (192, 9, 13), (64, 2, 8)),
+                                                  (6, (128, 3, 5), (64, 2, 5))])
+def test_strip_bulk_variant(L3, prec, variant, shape, tiling):
+    # Strip-row bulk copies (variants 5 and 6, the second with two stages and
+    # more CTAs per SM): the same per-node arithmetic as the
     # register kernel, so equal to it up to FMA contraction, and within the
     # precision's bar of the oracle.  Several strips with periodic wrap pieces
     # at x = 0 and x = nx, ragged row blocks and z chunks, and a box of two
@@ -184,8 +188,8 @@ def test_strip_bulk_variant(L3, prec, shape, tiling):
     case, phi0, u0 = two_phase(nx, ny, nz, rho_l=3.0, tau_f_l=0.7)
     a = L3.Sim3(case, phi0, u0, precision=prec)
     a.set_tiling(*tiling)
-    a.set_kernel(5)
-    assert a.kernel() == 5 and a.tiling()[:3] == tiling
+    a.set_kernel(variant)
+    assert a.kernel() == variant and a.tiling()[:3] == tiling
     b = L3.Sim3(case, phi0, u0, precision=prec)
     b.set_kernel(1)
     tr = a.track_volume(True)
