@@ -214,7 +214,7 @@ __device__ __forceinline__ void ad_block_partials(double (&red)[kAdThreads / 32]
 // states and adjoints (the handle's precision); the parameter partials are
 // summed per thread and per warp in R and accumulated in FP64 above that.
 template <typename R>
-__global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 2 : 1) ad_node(const AdArgs<R> a) {
+__global__ void __launch_bounds__(kAdThreads, sizeof(R) == 4 ? 3 : 1) ad_node(const AdArgs<R> a) {
   __shared__ double red[kAdThreads / 32][kNParam];
   using N = lbmk::Num<R>;
   const int nx = a.nx, ny = a.ny;
